@@ -1,0 +1,770 @@
+/*
+ * FliX CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg load this library.  The
+ * product (the CUDA library and its Python binding) never calls it and shares no code with it.
+ *
+ * It is deliberately plain and slow: sorted arrays, qsort, binary searches and linear merges, each
+ * step written to be checked against the paper by eye.  Two parts:
+ *
+ *  1. The semantic ordered map (om_map_*): the result every FliX batch must reach.  A FliX batch is
+ *     applied with snapshot semantics: lookups, successor and range queries see the state before the
+ *     batch; then the batch's inserts and deletes are applied in submission order.  An insert of a
+ *     present key leaves its value unchanged (Sec. 3.2: a key is inserted only if not already
+ *     present); a delete removes the key physically (Sec. 3.2, no tombstones).  Successor is the
+ *     smallest stored key k' >= k (Sec. 6.5).  A miss returns the all-ones "none" value (Sec. 3.3).
+ *     Range [lo, hi] is inclusive and ascending; the paper names but does not define it (Sec. 2.1,
+ *     Sec. 3.3), so this is the reading used throughout.
+ *
+ *  2. The structural model (om_model_*) of FliX's data layer, following Sec. 3.2-3.5 and Sec. 4:
+ *     buckets are chains of fixed-capacity nodes (NS slots, metadata maxKey and size, a node-link);
+ *     the MKBA holds each bucket's maxBucket; the initial build cuts the sorted keys into groups of
+ *     p = fill * NS; each bucket pulls its sublist from the sorted update list by a binary search for
+ *     maxBucket_{i-1} (Sec. 3.3, Sec. 4.1); an update goes to the first node of the chain whose
+ *     maxKey >= k (Sec. 4.1); deletes compact the node by shifting survivors left by the number of
+ *     earlier deletions (Sec. 4.4, Tab. 4); inserts merge the sublist into the node in key order
+ *     (Sec. 4.3.2, Tab. 3); a node that overflows is split into halves (Sec. 3.2, Sec. 5.3.1);
+ *     emptied nodes leave the chain and are reused (Sec. 4.4); restructuring flattens every chain
+ *     into half-full single-node buckets and resets the MKBA (Sec. 3.5, Sec. 6.6).
+ *
+ *     Where the paper leaves the node layout after a multi-key overflow open, the model uses one
+ *     canonical layout: a merged run of t keys stays one node if t <= NS; otherwise it becomes
+ *     q = floor(t / s) nodes (s = NS/2, the even half of Sec. 5.3.1): q-1 nodes of s keys and a last
+ *     node of the remaining t-(q-1)s keys.  Every piece but the last takes its own largest key as
+ *     maxKey; the last keeps the old node's maxKey.  This reproduces Tab. 3.  An emptied node is
+ *     unlinked unless the whole chain emptied, in which case the chain's first node stays as an empty
+ *     node; when the chain's last node leaves, its maxKey (= maxBucket) passes to the new last node.
+ *
+ * Keys and values are held as uint64 for both key widths kw in {32, 64}; KEY_MAX = 2^kw - 1 is not a
+ * storable key (it is the last bucket's maxBucket and the successor "none" key) and VAL_NONE is
+ * the all-ones value of the same width.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OP_NOP = 0, OP_LOOKUP = 1, OP_SUCC = 2, OP_RANGE = 3, OP_INSERT = 4, OP_DELETE = 5 };
+/* Net effect of a key's update run (composition of its inserts and deletes in submission order). */
+enum { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
+
+#define NIL (-1)
+
+static uint64_t width_max(int kw) { return kw == 64 ? ~(uint64_t)0 : (((uint64_t)1 << kw) - 1); }
+
+/* ------------------------------------------------------------------------------------------------
+ * Small helpers
+ * ---------------------------------------------------------------------------------------------- */
+
+typedef struct {
+    uint64_t key, val, pos;
+    uint8_t op;
+} orec;
+
+static int cmp_key_pos(const void* a, const void* b)
+{
+    const orec* x = (const orec*)a;
+    const orec* y = (const orec*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+/* first i in [0, n) with a[i] >= x, or n */
+static size_t lower_bound_u64(const uint64_t* a, size_t n, uint64_t x)
+{
+    size_t lo = 0, hi = n;
+    while (lo < hi) {
+        size_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* first i in [0, n) with a[i] > x, or n */
+static size_t upper_bound_u64(const uint64_t* a, size_t n, uint64_t x)
+{
+    size_t lo = 0, hi = n;
+    while (lo < hi) {
+        size_t mid = lo + (hi - lo) / 2;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* Apply one key's update ops, in submission order, to its state (present, val). */
+static void apply_run(const orec* r, size_t m, int* present, uint64_t* val)
+{
+    for (size_t i = 0; i < m; i++) {
+        if (r[i].op == OP_INSERT) {
+            if (!*present) { *present = 1; *val = r[i].val; }
+        } else if (r[i].op == OP_DELETE) {
+            *present = 0;
+        }
+    }
+}
+
+/* Net effect of a key's update run, whatever the key's prior state:
+ *   ends absent                       -> EFF_DEL
+ *   ends present, no delete in the run -> EFF_INS (first insert's value; a no-op if present)
+ *   ends present after a delete        -> EFF_UPS (the value inserted after the last delete) */
+static int run_effect(const orec* r, size_t m, uint64_t* val)
+{
+    int present = 0, deleted = 0;
+    uint64_t v = 0;
+    apply_run(r, m, &present, &v);          /* replayed from the absent state */
+    for (size_t i = 0; i < m; i++)
+        if (r[i].op == OP_DELETE) deleted = 1;
+    if (!present) return EFF_DEL;
+    *val = v;
+    return deleted ? EFF_UPS : EFF_INS;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * 1. Semantic ordered map
+ * ---------------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int kw;
+    uint64_t kmax;
+    uint64_t* k;
+    uint64_t* v;
+    size_t n;
+} om_map;
+
+om_map* om_map_create(int kw)
+{
+    if (kw != 32 && kw != 64) return NULL;
+    om_map* m = (om_map*)calloc(1, sizeof(om_map));
+    m->kw = kw;
+    m->kmax = width_max(kw);
+    return m;
+}
+
+void om_map_destroy(om_map* m)
+{
+    if (!m) return;
+    free(m->k);
+    free(m->v);
+    free(m);
+}
+
+size_t om_map_size(const om_map* m) { return m->n; }
+
+void om_map_export(const om_map* m, uint64_t* keys, uint64_t* vals)
+{
+    memcpy(keys, m->k, m->n * sizeof(uint64_t));
+    memcpy(vals, m->v, m->n * sizeof(uint64_t));
+}
+
+/* Build from pairs: duplicates keep the first occurrence.  Returns -1 (unchanged) on KEY_MAX. */
+int om_map_bulk_load(om_map* m, const uint64_t* keys, const uint64_t* vals, size_t n)
+{
+    for (size_t i = 0; i < n; i++)
+        if (keys[i] >= m->kmax) return -1;
+    orec* r = (orec*)malloc((n ? n : 1) * sizeof(orec));
+    for (size_t i = 0; i < n; i++) { r[i].key = keys[i]; r[i].val = vals[i]; r[i].pos = i; r[i].op = OP_INSERT; }
+    qsort(r, n, sizeof(orec), cmp_key_pos);
+    free(m->k);
+    free(m->v);
+    m->k = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    m->v = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    size_t c = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (i > 0 && r[i].key == r[i - 1].key) continue;
+        m->k[c] = r[i].key;
+        m->v[c] = r[i].val;
+        c++;
+    }
+    m->n = c;
+    free(r);
+    return 0;
+}
+
+/* Reads of one batch against the current state.  Per op i (all outputs defined for every op):
+ *   LOOKUP: out_val = value or VAL_NONE, out_found = hit, out_key = key if hit else KEY_MAX
+ *   SUCC  : out_key = smallest stored key >= key (KEY_MAX if none), out_val its value (VAL_NONE),
+ *           out_found = exists
+ *   other : out_key = KEY_MAX, out_val = VAL_NONE, out_found = 0
+ * range_off[n+1] (if non-NULL): exclusive prefix of the per-op range counts |{k : lo <= k <= hi}|
+ * for RANGE ops (lo = key, hi = aux; empty when lo > hi) and 0 for all other ops. */
+void om_map_read(const om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys,
+                 const uint64_t* aux, uint64_t* out_val, uint8_t* out_found, uint64_t* out_key,
+                 uint64_t* range_off)
+{
+    const uint64_t none = m->kmax;
+    uint64_t acc = 0;
+    if (range_off) range_off[0] = 0;
+    for (size_t i = 0; i < n; i++) {
+        uint64_t ok = none, ov = none;
+        uint8_t of = 0;
+        uint64_t cnt = 0;
+        if (ops[i] == OP_LOOKUP) {
+            size_t p = lower_bound_u64(m->k, m->n, keys[i]);
+            if (p < m->n && m->k[p] == keys[i]) { ok = keys[i]; ov = m->v[p]; of = 1; }
+        } else if (ops[i] == OP_SUCC) {
+            size_t p = lower_bound_u64(m->k, m->n, keys[i]);
+            if (p < m->n) { ok = m->k[p]; ov = m->v[p]; of = 1; }
+        } else if (ops[i] == OP_RANGE) {
+            if (keys[i] <= aux[i]) {
+                size_t a = lower_bound_u64(m->k, m->n, keys[i]);
+                size_t b = upper_bound_u64(m->k, m->n, aux[i]);
+                cnt = b - a;
+            }
+        }
+        if (out_key) out_key[i] = ok;
+        if (out_val) out_val[i] = ov;
+        if (out_found) out_found[i] = of;
+        acc += cnt;
+        if (range_off) range_off[i + 1] = acc;
+    }
+}
+
+/* Range pairs of a batch, concatenated in op order at the offsets om_map_read produced. */
+void om_map_range_fill(const om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys,
+                       const uint64_t* aux, const uint64_t* range_off, uint64_t* rkeys, uint64_t* rvals)
+{
+    for (size_t i = 0; i < n; i++) {
+        if (ops[i] != OP_RANGE || keys[i] > aux[i]) continue;
+        size_t a = lower_bound_u64(m->k, m->n, keys[i]);
+        size_t b = upper_bound_u64(m->k, m->n, aux[i]);
+        uint64_t o = range_off[i];
+        for (size_t j = a; j < b; j++, o++) { rkeys[o] = m->k[j]; rvals[o] = m->v[j]; }
+    }
+}
+
+/* Inserts and deletes of one batch, applied in submission order.  Returns -1 (unchanged) if an
+ * insert carries KEY_MAX.  Keys are independent, so the ops are grouped by key (stable, keeping
+ * submission order inside a key) and each key's ops are replayed on that key's state. */
+int om_map_update(om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux)
+{
+    size_t u = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (ops[i] == OP_INSERT && keys[i] >= m->kmax) return -1;
+        if (ops[i] == OP_INSERT || ops[i] == OP_DELETE) u++;
+    }
+    orec* r = (orec*)malloc((u ? u : 1) * sizeof(orec));
+    u = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (ops[i] != OP_INSERT && ops[i] != OP_DELETE) continue;
+        r[u].key = keys[i];
+        r[u].val = ops[i] == OP_INSERT ? aux[i] : 0;
+        r[u].pos = i;
+        r[u].op = ops[i];
+        u++;
+    }
+    qsort(r, u, sizeof(orec), cmp_key_pos);
+    uint64_t* nk = (uint64_t*)malloc((m->n + u + 1) * sizeof(uint64_t));
+    uint64_t* nv = (uint64_t*)malloc((m->n + u + 1) * sizeof(uint64_t));
+    size_t i = 0, j = 0, c = 0;
+    while (i < m->n || j < u) {
+        if (j >= u || (i < m->n && m->k[i] < r[j].key)) {
+            nk[c] = m->k[i]; nv[c] = m->v[i]; c++; i++;
+            continue;
+        }
+        size_t e = j;
+        while (e < u && r[e].key == r[j].key) e++;
+        int present = 0;
+        uint64_t val = 0;
+        if (i < m->n && m->k[i] == r[j].key) { present = 1; val = m->v[i]; i++; }
+        apply_run(r + j, e - j, &present, &val);
+        if (present) { nk[c] = r[j].key; nv[c] = val; c++; }
+        j = e;
+    }
+    free(m->k);
+    free(m->v);
+    m->k = nk;
+    m->v = nv;
+    m->n = c;
+    free(r);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * 2. Structural model
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Sec. 4.4 / Tab. 4: each node key is compared with the delete keys and marked; a survivor moves
+ * left by the number of deletions among the slots before it.  shift[i] = -1 for a deleted slot.
+ * Returns the new size. */
+uint32_t om_delete_compact(const uint64_t* keys, uint32_t n, const uint64_t* dk, uint32_t m,
+                           uint64_t* out, int32_t* shift)
+{
+    uint32_t del_count = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        int marked = 0;
+        for (uint32_t d = 0; d < m; d++)
+            if (dk[d] == keys[i]) marked = 1;
+        if (marked) {
+            if (shift) shift[i] = -1;
+            del_count++;
+            continue;
+        }
+        if (shift) shift[i] = (int32_t)del_count;
+        out[i - del_count] = keys[i];
+    }
+    return n - del_count;
+}
+
+/* Sec. 4.3.2 / Tab. 3: the sorted insert sublist is merged into the node's sorted keys; a key
+ * already present is not inserted again.  Returns the merged size. */
+uint32_t om_merge_insert(const uint64_t* keys, uint32_t n, const uint64_t* ins, uint32_t m, uint64_t* out)
+{
+    uint32_t i = 0, j = 0, c = 0;
+    while (i < n || j < m) {
+        if (j >= m || (i < n && keys[i] < ins[j])) out[c++] = keys[i++];
+        else if (i < n && keys[i] == ins[j]) { out[c++] = keys[i++]; j++; }
+        else out[c++] = ins[j++];
+    }
+    return c;
+}
+
+/* Canonical node layout of a merged run of t keys (see the header).  Writes the piece sizes and
+ * returns the number of pieces q (0 when t == 0). */
+uint32_t om_canonical_layout(uint64_t t, uint32_t NS, uint32_t* piece_sizes)
+{
+    if (t == 0) return 0;
+    if (t <= NS) { if (piece_sizes) piece_sizes[0] = (uint32_t)t; return 1; }
+    uint32_t s = NS / 2;
+    uint64_t q = t / s;
+    if (piece_sizes) {
+        for (uint64_t r = 0; r + 1 < q; r++) piece_sizes[r] = s;
+        piece_sizes[q - 1] = (uint32_t)(t - (q - 1) * s);
+    }
+    return (uint32_t)q;
+}
+
+typedef struct {
+    int kw;
+    uint64_t kmax;
+    uint32_t NS, p;
+    /* node pool */
+    uint64_t cap, hw;
+    uint64_t *keys, *vals;
+    uint32_t* size;
+    uint64_t* bound;
+    int64_t* next;
+    int64_t* free_stack;
+    uint64_t nfree;
+    /* buckets */
+    uint64_t nb, nb_cap;
+    uint64_t* mkba;
+    int64_t* head;
+} om_model;
+
+static void model_grow(om_model* m, uint64_t want)
+{
+    if (want <= m->cap) return;
+    uint64_t c = m->cap ? m->cap : 16;
+    while (c < want) c *= 2;
+    m->keys = (uint64_t*)realloc(m->keys, c * m->NS * sizeof(uint64_t));
+    m->vals = (uint64_t*)realloc(m->vals, c * m->NS * sizeof(uint64_t));
+    m->size = (uint32_t*)realloc(m->size, c * sizeof(uint32_t));
+    m->bound = (uint64_t*)realloc(m->bound, c * sizeof(uint64_t));
+    m->next = (int64_t*)realloc(m->next, c * sizeof(int64_t));
+    m->free_stack = (int64_t*)realloc(m->free_stack, c * sizeof(int64_t));
+    m->cap = c;
+}
+
+static int64_t node_alloc(om_model* m)
+{
+    if (m->nfree) return m->free_stack[--m->nfree];
+    model_grow(m, m->hw + 1);
+    return (int64_t)m->hw++;
+}
+
+static void node_free(om_model* m, int64_t id) { m->free_stack[m->nfree++] = id; }
+
+static void buckets_resize(om_model* m, uint64_t nb)
+{
+    if (nb > m->nb_cap) {
+        m->mkba = (uint64_t*)realloc(m->mkba, nb * sizeof(uint64_t));
+        m->head = (int64_t*)realloc(m->head, nb * sizeof(int64_t));
+        m->nb_cap = nb;
+    }
+    m->nb = nb;
+}
+
+om_model* om_model_create(int kw, uint32_t NS, uint32_t fill_pct)
+{
+    if ((kw != 32 && kw != 64) || NS < 2 || (NS & 1) || fill_pct == 0 || fill_pct > 100) return NULL;
+    om_model* m = (om_model*)calloc(1, sizeof(om_model));
+    m->kw = kw;
+    m->kmax = width_max(kw);
+    m->NS = NS;
+    m->p = (uint32_t)(((uint64_t)NS * fill_pct) / 100);
+    if (m->p < 1) m->p = 1;
+    return m;
+}
+
+void om_model_destroy(om_model* m)
+{
+    if (!m) return;
+    free(m->keys); free(m->vals); free(m->size); free(m->bound); free(m->next);
+    free(m->free_stack); free(m->mkba); free(m->head);
+    free(m);
+}
+
+/* Sec. 3.2: cut the sorted distinct pairs into groups of p keys, one single-node bucket per group;
+ * maxBucket is the group's largest key, except the last bucket's, which is KEY_MAX so that keys
+ * above the largest build key also have a bucket.  n == 0 gives one bucket with one empty node. */
+static void model_cut(om_model* m, const uint64_t* k, const uint64_t* v, uint64_t n)
+{
+    m->hw = 0;
+    m->nfree = 0;
+    uint64_t nb = n ? (n + m->p - 1) / m->p : 1;
+    buckets_resize(m, nb);
+    model_grow(m, nb);
+    for (uint64_t b = 0; b < nb; b++) {
+        int64_t id = node_alloc(m);
+        uint64_t lo = b * m->p, hi = lo + m->p < n ? lo + m->p : n;
+        uint32_t sz = (uint32_t)(hi - lo);
+        for (uint32_t s = 0; s < sz; s++) {
+            m->keys[id * m->NS + s] = k[lo + s];
+            m->vals[id * m->NS + s] = v[lo + s];
+        }
+        m->size[id] = sz;
+        m->mkba[b] = (b + 1 == nb) ? m->kmax : k[hi - 1];
+        m->bound[id] = m->mkba[b];
+        m->next[id] = NIL;
+        m->head[b] = id;
+    }
+}
+
+int om_model_bulk_load(om_model* m, const uint64_t* keys, const uint64_t* vals, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; i++)
+        if (keys[i] >= m->kmax) return -1;
+    orec* r = (orec*)malloc((n ? n : 1) * sizeof(orec));
+    for (uint64_t i = 0; i < n; i++) { r[i].key = keys[i]; r[i].val = vals[i]; r[i].pos = i; r[i].op = 0; }
+    qsort(r, n, sizeof(orec), cmp_key_pos);
+    uint64_t* k = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint64_t* v = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint64_t c = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (i > 0 && r[i].key == r[i - 1].key) continue;
+        k[c] = r[i].key; v[c] = r[i].val; c++;
+    }
+    model_cut(m, k, v, c);
+    free(r); free(k); free(v);
+    return 0;
+}
+
+/* Apply one node's routed updates (sorted, distinct keys, net effects) and lay the result out.
+ * Returns the number of output keys t; pieces are linked after `node`, the last piece's next is the
+ * node's old next.  *tail receives the last piece (or NIL when t == 0). */
+static uint64_t model_apply_node(om_model* m, int64_t node, const uint64_t* uk, const int* ue,
+                                 const uint64_t* uv, uint64_t cnt, int64_t* tail)
+{
+    const uint32_t NS = m->NS;
+    uint32_t sz = m->size[node];
+    const uint64_t* nk = m->keys + node * NS;
+    const uint64_t* nv = m->vals + node * NS;
+
+    /* (i) deletes compact the node (Sec. 4.4); an upsert of a present key replaces its value. */
+    uint64_t* dk = (uint64_t*)malloc((cnt + 1) * sizeof(uint64_t));
+    uint32_t nd = 0;
+    for (uint64_t j = 0; j < cnt; j++) if (ue[j] == EFF_DEL) dk[nd++] = uk[j];
+    uint64_t* ck = (uint64_t*)malloc((NS + 1) * sizeof(uint64_t));
+    uint64_t* cv = (uint64_t*)malloc((NS + 1) * sizeof(uint64_t));
+    int32_t* shift = (int32_t*)malloc((NS + 1) * sizeof(int32_t));
+    uint32_t c = om_delete_compact(nk, sz, dk, nd, ck, shift);
+    for (uint32_t i = 0; i < sz; i++) if (shift[i] >= 0) cv[i - shift[i]] = nv[i];
+    for (uint64_t j = 0; j < cnt; j++) {
+        if (ue[j] != EFF_UPS) continue;
+        for (uint32_t i = 0; i < c; i++) if (ck[i] == uk[j]) cv[i] = uv[j];
+    }
+
+    /* (ii) inserts (and upserts of absent keys) merge into the node in key order (Sec. 4.3.2). */
+    uint64_t* ik = (uint64_t*)malloc((cnt + 1) * sizeof(uint64_t));
+    uint64_t* iv = (uint64_t*)malloc((cnt + 1) * sizeof(uint64_t));
+    uint32_t ni = 0;
+    for (uint64_t j = 0; j < cnt; j++) {
+        if (ue[j] != EFF_INS && ue[j] != EFF_UPS) continue;
+        ik[ni] = uk[j]; iv[ni] = uv[j]; ni++;
+    }
+    uint64_t* rk = (uint64_t*)malloc((c + ni + 1) * sizeof(uint64_t));
+    uint64_t* rv = (uint64_t*)malloc((c + ni + 1) * sizeof(uint64_t));
+    uint64_t t = om_merge_insert(ck, c, ik, ni, rk);
+    {   /* carry the values along the merge */
+        uint32_t a = 0, b = 0;
+        for (uint64_t o = 0; o < t; o++) {
+            if (a < c && ck[a] == rk[o]) { rv[o] = cv[a]; a++; if (b < ni && ik[b] == rk[o]) b++; }
+            else { rv[o] = iv[b]; b++; }
+        }
+    }
+
+    /* (iii) canonical layout: the node keeps piece 0, new nodes take the rest. */
+    uint64_t old_bound = m->bound[node];
+    int64_t old_next = m->next[node];
+    uint32_t* ps = (uint32_t*)malloc(((t / (NS / 2)) + 2) * sizeof(uint32_t));
+    uint32_t q = om_canonical_layout(t, NS, ps);
+    int64_t cur = node;
+    uint64_t o = 0;
+    for (uint32_t r = 0; r < q; r++) {
+        if (r > 0) {
+            int64_t nn = node_alloc(m);
+            m->next[cur] = nn;
+            cur = nn;
+        }
+        for (uint32_t s = 0; s < ps[r]; s++, o++) {
+            m->keys[cur * NS + s] = rk[o];
+            m->vals[cur * NS + s] = rv[o];
+        }
+        m->size[cur] = ps[r];
+        m->bound[cur] = (r + 1 < q) ? rk[o - 1] : old_bound;
+    }
+    if (q > 0) m->next[cur] = old_next;
+    *tail = q > 0 ? cur : NIL;
+    if (q == 0) m->size[node] = 0;
+    free(dk); free(ck); free(cv); free(shift); free(ik); free(iv); free(rk); free(rv); free(ps);
+    return t;
+}
+
+/* One bucket applies its sublist (Sec. 4.1: walk node-links to the first node with k <= maxKey). */
+static void model_apply_bucket(om_model* m, uint64_t b, const uint64_t* uk, const int* ue,
+                               const uint64_t* uv, uint64_t cnt)
+{
+    int64_t node = m->head[b];
+    int64_t prev = NIL;           /* last node kept so far in chain order */
+    int64_t* dropped = (int64_t*)malloc((cnt + 2) * sizeof(int64_t));
+    uint64_t nd = 0;
+    int last_dropped = 0;
+    uint64_t j = 0;
+    while (j < cnt && node != NIL) {
+        int64_t nx = m->next[node];
+        uint64_t k = j;
+        while (k < cnt && uk[k] <= m->bound[node]) k++;
+        if (k == j) { prev = node; node = nx; continue; }
+        int64_t tail;
+        uint64_t t = model_apply_node(m, node, uk + j, ue + j, uv + j, k - j, &tail);
+        if (t == 0) {
+            if (prev == NIL) m->head[b] = nx; else m->next[prev] = nx;
+            dropped[nd++] = node;
+            last_dropped = (nx == NIL);
+        } else {
+            if (prev == NIL) m->head[b] = node; else m->next[prev] = node;
+            prev = tail;
+            last_dropped = 0;
+        }
+        j = k;
+        node = nx;
+    }
+    if (m->head[b] == NIL) {
+        /* the whole chain emptied: its first node stays as the bucket's only, empty node */
+        int64_t keep = dropped[0];
+        m->size[keep] = 0;
+        m->bound[keep] = m->mkba[b];
+        m->next[keep] = NIL;
+        m->head[b] = keep;
+        for (uint64_t i = 1; i < nd; i++) node_free(m, dropped[i]);
+    } else {
+        if (last_dropped) m->bound[prev] = m->mkba[b];   /* maxBucket passes to the new last node */
+        for (uint64_t i = 0; i < nd; i++) node_free(m, dropped[i]);
+    }
+    free(dropped);
+}
+
+/* Inserts and deletes of one batch: sort the update list, reduce each key's run to its net effect,
+ * then every bucket pulls its sublist by binary search (Sec. 3.3, Sec. 4.1).  Returns -1
+ * (unchanged) if an insert carries KEY_MAX. */
+int om_model_update(om_model* m, uint64_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux)
+{
+    uint64_t u = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (ops[i] == OP_INSERT && keys[i] >= m->kmax) return -1;
+        if (ops[i] == OP_INSERT || ops[i] == OP_DELETE) u++;
+    }
+    orec* r = (orec*)malloc((u ? u : 1) * sizeof(orec));
+    u = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (ops[i] != OP_INSERT && ops[i] != OP_DELETE) continue;
+        r[u].key = keys[i]; r[u].val = ops[i] == OP_INSERT ? aux[i] : 0; r[u].pos = i; r[u].op = ops[i];
+        u++;
+    }
+    qsort(r, u, sizeof(orec), cmp_key_pos);
+    uint64_t* uk = (uint64_t*)malloc((u + 1) * sizeof(uint64_t));
+    uint64_t* uv = (uint64_t*)malloc((u + 1) * sizeof(uint64_t));
+    int* ue = (int*)malloc((u + 1) * sizeof(int));
+    uint64_t U = 0;
+    for (uint64_t j = 0; j < u;) {
+        uint64_t e = j;
+        while (e < u && r[e].key == r[j].key) e++;
+        uint64_t val = 0;
+        int eff = run_effect(r + j, e - j, &val);
+        uk[U] = r[j].key; uv[U] = val; ue[U] = eff; U++;
+        j = e;
+    }
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint64_t start = b == 0 ? 0 : upper_bound_u64(uk, U, m->mkba[b - 1]);
+        uint64_t end = upper_bound_u64(uk, U, m->mkba[b]);
+        if (start < end) model_apply_bucket(m, b, uk + start, ue + start, uv + start, end - start);
+    }
+    free(r); free(uk); free(uv); free(ue);
+    return 0;
+}
+
+uint64_t om_model_live_keys(const om_model* m)
+{
+    uint64_t n = 0;
+    for (uint64_t b = 0; b < m->nb; b++)
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x]) n += m->size[x];
+    return n;
+}
+
+uint64_t om_model_nodes_used(const om_model* m) { return m->hw - m->nfree; }
+uint64_t om_model_buckets(const om_model* m) { return m->nb; }
+
+uint64_t om_model_max_chain(const om_model* m)
+{
+    uint64_t mx = 0;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint64_t c = 0;
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x]) c++;
+        if (c > mx) mx = c;
+    }
+    return mx;
+}
+
+/* Sec. 3.5: flatten every chain into single-node buckets at the build fill and reset the MKBA.
+ * Returns the number of nodes recovered (used before minus used after). */
+int64_t om_model_restructure(om_model* m)
+{
+    uint64_t before = om_model_nodes_used(m);
+    uint64_t n = om_model_live_keys(m);
+    uint64_t* k = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+    uint64_t* v = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+    uint64_t c = 0;
+    for (uint64_t b = 0; b < m->nb; b++)
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x])
+            for (uint32_t s = 0; s < m->size[x]; s++) {
+                k[c] = m->keys[x * m->NS + s];
+                v[c] = m->vals[x * m->NS + s];
+                c++;
+            }
+    model_cut(m, k, v, c);
+    free(k); free(v);
+    return (int64_t)before - (int64_t)om_model_nodes_used(m);
+}
+
+/* Reads through the structure.  Queries are sorted by key and each bucket pulls its sublist by a
+ * binary search for maxBucket_{i-1} (Sec. 3.3); each query walks to the first node with
+ * k <= maxKey.  Output conventions match om_map_read (LOOKUP and SUCC only). */
+void om_model_read(const om_model* m, uint64_t n, const uint8_t* ops, const uint64_t* keys,
+                   uint64_t* out_val, uint8_t* out_found, uint64_t* out_key)
+{
+    const uint64_t none = m->kmax;
+    orec* r = (orec*)malloc((n ? n : 1) * sizeof(orec));
+    for (uint64_t i = 0; i < n; i++) {
+        r[i].key = keys[i]; r[i].pos = i; r[i].op = ops[i]; r[i].val = 0;
+        out_key[i] = none; out_val[i] = none; out_found[i] = 0;
+    }
+    qsort(r, n, sizeof(orec), cmp_key_pos);
+    uint64_t* sk = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; i++) sk[i] = r[i].key;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint64_t start = b == 0 ? 0 : upper_bound_u64(sk, n, m->mkba[b - 1]);
+        uint64_t end = upper_bound_u64(sk, n, m->mkba[b]);
+        for (uint64_t j = start; j < end; j++) {
+            uint64_t q = r[j].key, i = r[j].pos;
+            int64_t x = m->head[b];
+            while (q > m->bound[x]) x = m->next[x];
+            const uint64_t* nk = m->keys + x * m->NS;
+            uint32_t sz = m->size[x];
+            uint32_t p = (uint32_t)lower_bound_u64(nk, sz, q);
+            if (r[j].op == OP_LOOKUP) {
+                if (p < sz && nk[p] == q) { out_key[i] = q; out_val[i] = m->vals[x * m->NS + p]; out_found[i] = 1; }
+            } else if (r[j].op == OP_SUCC) {
+                /* the smallest stored key >= q: in this node, else the first key of the next
+                 * non-empty node in chain and bucket order */
+                uint64_t bb = b;
+                while (p >= m->size[x]) {
+                    p = 0;
+                    x = m->next[x];
+                    while (x == NIL) {
+                        if (++bb >= m->nb) break;
+                        x = m->head[bb];
+                    }
+                    if (x == NIL) break;
+                }
+                if (x != NIL) { out_key[i] = m->keys[x * m->NS + p]; out_val[i] = m->vals[x * m->NS + p]; out_found[i] = 1; }
+            }
+        }
+    }
+    free(r); free(sk);
+}
+
+/* Layout dump in bucket and chain order.  With NULL arrays only the counts are written:
+ * counts[0] = buckets, counts[1] = nodes in chains, counts[2] = live keys. */
+void om_model_dump(const om_model* m, uint64_t* counts, uint64_t* mkba, uint32_t* chain_len,
+                   uint32_t* node_size, uint64_t* node_bound, uint64_t* keys, uint64_t* vals)
+{
+    uint64_t nn = 0, nk = 0;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint32_t c = 0;
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x]) {
+            if (node_size) { node_size[nn] = m->size[x]; node_bound[nn] = m->bound[x]; }
+            if (keys)
+                for (uint32_t s = 0; s < m->size[x]; s++) {
+                    keys[nk + s] = m->keys[x * m->NS + s];
+                    vals[nk + s] = m->vals[x * m->NS + s];
+                }
+            nn++;
+            nk += m->size[x];
+            c++;
+        }
+        if (chain_len) chain_len[b] = c;
+        if (mkba) mkba[b] = m->mkba[b];
+    }
+    counts[0] = m->nb;
+    counts[1] = nn;
+    counts[2] = nk;
+}
+
+/* Invariant check.  Returns 0 when all hold, else the number of the first violated invariant:
+ *  1 MKBA strictly increasing, last entry KEY_MAX
+ *  2 every chain non-empty, node bounds strictly increasing, last node bound == maxBucket
+ *  3 keys strictly increasing inside a node and inside (previous bound, bound]
+ *  4 0 <= size <= NS, and a size-0 node only as a bucket's only node
+ *  5 nodes in chains + free nodes == nodes ever allocated
+ *  6 (only if build_shape) every node holds exactly p keys except the last bucket's (1..p) */
+int om_model_check(const om_model* m, int build_shape)
+{
+    uint64_t in_chains = 0;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        if (b > 0 && !(m->mkba[b - 1] < m->mkba[b])) return 1;
+        if (b + 1 == m->nb && m->mkba[b] != m->kmax) return 1;
+        int64_t x = m->head[b];
+        if (x == NIL) return 2;
+        int have_lo = b > 0;
+        uint64_t lo = b > 0 ? m->mkba[b - 1] : 0;
+        uint64_t chain = 0;
+        int64_t last = NIL;
+        for (; x != NIL; x = m->next[x]) {
+            chain++;
+            in_chains++;
+            if (chain > m->hw) return 2;
+            uint32_t sz = m->size[x];
+            if (sz > m->NS) return 4;
+            if (last != NIL && !(m->bound[last] < m->bound[x])) return 2;
+            for (uint32_t s = 0; s < sz; s++) {
+                uint64_t k = m->keys[x * m->NS + s];
+                if (have_lo && !(k > lo)) return 3;
+                if (!(k <= m->bound[x])) return 3;
+                if (s > 0 && !(m->keys[x * m->NS + s - 1] < k)) return 3;
+            }
+            lo = m->bound[x];
+            have_lo = 1;
+            last = x;
+        }
+        if (m->bound[last] != m->mkba[b]) return 2;
+        if (chain > 1)
+            for (x = m->head[b]; x != NIL; x = m->next[x])
+                if (m->size[x] == 0) return 4;
+        if (build_shape) {
+            if (chain != 1) return 6;
+            uint32_t sz = m->size[m->head[b]];
+            if (b + 1 < m->nb ? sz != m->p : (sz > m->p || (m->nb > 1 && sz == 0))) return 6;
+        }
+    }
+    if (in_chains + m->nfree != m->hw) return 5;
+    return 0;
+}
