@@ -1,0 +1,411 @@
+"""Benchmark of the FliX hot path on GB300 (one JSON line on stdout).
+
+Workload (read-scale case): 2^26 distinct uniform uint64 keys bulk-loaded at node size 64 (32 keys
+per node, 2^21 buckets).  One step runs every stage of the hot path once over fresh-from-HBM
+batches:
+    lookup 2^24 (30% misses) -> successor 2^24 (30% misses) -> range 2^18 (1..1000 keys each)
+    -> insert 2^20 fresh keys -> delete the same 2^20 keys -> restructure.
+Each batch is sorted on the GPU inside the timed region (the paper's unsorted-query mode, Sec. 6.4).
+The insert/delete pair and the restructure return the index to its starting layout, so every step
+does the same work.  Ops per step = 2^24 + 2^24 + 2^18 + 2^20 + 2^20.
+
+`value` is whole-job Mops/s over device-resident inputs; `e2e` is the same step through the public
+Python API from pinned host buffers with the host<->device copies inside the timed region.
+`--impl reference` times the CPU oracle instead (a bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload as W  # noqa: E402
+
+LOG_LOAD = 26
+LOG_Q = 24
+LOG_R = 18
+LOG_U = 20
+NODE_SIZE = 64
+KW = 64
+METRIC = "Mops/s per op mix at 1 GB300 (bit-exact vs oracle), % HBM roofline; p50/p99 latency"
+WORKLOAD = ("read-scale: 2^26 distinct uniform uint64 keys/values, node size 64; per step lookup 2^24 "
+            "(30% miss) + successor 2^24 (30% miss) + range 2^18 (1-1000 keys) + insert 2^20 fresh + "
+            "delete the same 2^20 + restructure")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_inputs(seed, log_load=LOG_LOAD, log_q=LOG_Q, log_r=LOG_R, log_u=LOG_U):
+    c = W.read_scale(seed=seed, n_load=1 << log_load, batch=1 << log_q, n_range=1 << log_r)
+    n_load = 1 << log_load
+    fresh = W.universe(KW, seed, n_load + (1 << log_q), n_load + (1 << log_q) + (1 << log_u))
+    c["ins_keys"] = fresh
+    c["ins_vals"] = W.values_for(KW, fresh, salt=9)
+    # successor queries: a second seeded draw with the same recipe
+    c2 = W.read_scale(seed=seed + 1, n_load=1 << log_load, batch=1 << log_q, n_range=0)
+    c["succ_queries"] = c2["queries"]
+    return c
+
+
+def ops_per_step(log_q=LOG_Q, log_r=LOG_R, log_u=LOG_U):
+    return dict(lookup=1 << log_q, successor=1 << log_q, range=1 << log_r, insert=1 << log_u, delete=1 << log_u)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]) if p[3] not in ("[N/A]", "N/A") else 0.0,
+                                 hw=p[5], hwt=p[6], swt=p[7], pcap=p[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"] == "Active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def gpu_id_for_smi(torch):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel):
+    """ncu DRAM bytes per item for `kernel`, valid only while its source is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)[kernel]
+        src = open(os.path.join(ROOT, "paper_2604_16725_gb300", "csrc", d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != d["sha256"]:
+            return None
+        return d
+    except Exception:
+        return None
+
+
+def run_step(torch, idx, bufs, stream, events=None):
+    """One step on device-resident inputs.  events: dict phase -> (start, end) CUDA events."""
+    def ev(name, which):
+        if events is not None:
+            events[name][which].record(stream)
+
+    ev("lookup", 0)
+    idx.lookup(bufs["q"], stream=stream, out=bufs["lv"])
+    ev("lookup", 1)
+    ev("successor", 0)
+    idx.successor(bufs["sq"], stream=stream)
+    ev("successor", 1)
+    ev("range", 0)
+    idx.range(bufs["lo"], bufs["hi"], capacity=bufs["rcap"], stream=stream)
+    ev("range", 1)
+    ev("insert", 0)
+    idx.insert(bufs["ik"], bufs["iv"], stream=stream)
+    ev("insert", 1)
+    ev("delete", 0)
+    idx.delete(bufs["ik"], stream=stream)
+    ev("delete", 1)
+    ev("restructure", 0)
+    idx.restructure(stream=stream)
+    ev("restructure", 1)
+
+
+def run_step_e2e(torch, idx, host, stream):
+    """The same step through the public API from pinned host buffers; results read back to host."""
+    dev = lambda t: t.to("cuda", non_blocking=True)  # noqa: E731
+    with torch.cuda.stream(stream):
+        v, f = idx.lookup(dev(host["q"]), stream=stream)
+        host["lv"].copy_(v, non_blocking=True)
+        host["lf"].copy_(f, non_blocking=True)
+        sk, sv = idx.successor(dev(host["sq"]), stream=stream)
+        host["sk"].copy_(sk, non_blocking=True)
+        host["sv"].copy_(sv, non_blocking=True)
+        off, rk, rv = idx.range(dev(host["lo"]), dev(host["hi"]), capacity=host["rcap"], stream=stream)
+        host["roff"].copy_(off, non_blocking=True)
+        host["rk"][: rk.numel()].copy_(rk, non_blocking=True)
+        host["rv"][: rv.numel()].copy_(rv, non_blocking=True)
+        idx.insert(dev(host["ik"]), dev(host["iv"]), stream=stream)
+        idx.delete(dev(host["ik"]), stream=stream)
+        idx.restructure(stream=stream)
+    stream.synchronize()
+
+
+def cpu_oracle_sample(c, scale_log=4):
+    """The oracle, as it stands, on a bounded sample of the step: every batch 2^-scale_log of its size,
+    against the full 2^26-key map.  Returns (Mops/s, seconds, description)."""
+    import oracle
+    mp = oracle.Map(KW)
+    mp.bulk_load(c["load_keys"], c["load_vals"])
+    nq = c["queries"].size >> scale_log
+    nr = c["range_lo"].size >> scale_log
+    nu = c["ins_keys"].size >> scale_log
+    t0 = time.perf_counter()
+    mp.read(np.full(nq, W.OP_LOOKUP, np.uint8), c["queries"][:nq])
+    mp.read(np.full(nq, W.OP_SUCC, np.uint8), c["succ_queries"][:nq])
+    mp.read(np.full(nr, W.OP_RANGE, np.uint8), c["range_lo"][:nr], c["range_hi"][:nr])
+    mp.update(np.full(nu, W.OP_INSERT, np.uint8), c["ins_keys"][:nu], c["ins_vals"][:nu])
+    mp.update(np.full(nu, W.OP_DELETE, np.uint8), c["ins_keys"][:nu])
+    dt = time.perf_counter() - t0
+    ops = 2 * nq + nr + 2 * nu
+    desc = ("oracle (plain C, 1 thread) on the full 2^26-key map; per step 2^%d lookups, 2^%d successors, "
+            "2^%d ranges, 2^%d inserts, 2^%d deletes" % (LOG_Q - scale_log, LOG_Q - scale_log, LOG_R - scale_log,
+                                                         LOG_U - scale_log, LOG_U - scale_log))
+    return ops / dt / 1e6, dt, desc
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    c = make_inputs(seed=2000)
+    vals = []
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        mops, dt, desc = cpu_oracle_sample(c, scale_log=6)
+        if s >= args.warmup:
+            vals.append((mops, dt))
+    v = statistics.median(m for m, _ in vals)
+    ms = statistics.median(d for _, d in vals) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mops/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "each step: every batch at 1/64 of its size"},
+            "cpu_baseline": {"value": v, "unit": "Mops/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="flix", choices=["flix", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    import paper_2604_16725_gb300 as fx
+
+    c = make_inputs(seed=2000 + 17 * rank)
+    idx = fx.Index(key_bits=KW, node_size=NODE_SIZE)
+    stream = torch.cuda.Stream()
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()  # noqa: E731
+    idx.bulk_load(td(c["load_keys"]), td(c["load_vals"]), stream=stream)
+    bufs = dict(q=td(c["queries"]), sq=td(c["succ_queries"]), lo=td(c["range_lo"]), hi=td(c["range_hi"]),
+                ik=td(c["ins_keys"]), iv=td(c["ins_vals"]), lv=torch.empty(1 << LOG_Q, dtype=torch.int64, device="cuda"))
+    # size the range output once (counts), outside the timed region
+    off, rk, rv = idx.range(bufs["lo"], bufs["hi"], stream=stream)
+    bufs["rcap"] = int(rk.numel())
+    del off, rk, rv
+    stream.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        run_step(torch, idx, bufs, stream)
+    phases = ["lookup", "successor", "range", "insert", "delete", "restructure"]
+    events = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for p in phases}
+    per_phase = {p: [] for p in phases}
+    step_ms = []
+    launches0 = idx.launch_count()
+    barrier()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id_for_smi(torch)) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            run_step(torch, idx, bufs, stream, events)
+            s1.record(stream)
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            for p in phases:
+                per_phase[p].append(events[p][0].elapsed_time(events[p][1]))
+        t_end.record(stream)
+        barrier()
+    clocks = clk.summary()
+    total_ms = t_start.elapsed_time(t_end)
+    launches = idx.launch_count() - launches0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ops = ops_per_step()
+    n_ops = sum(ops.values())
+    ms_step = total_ms / args.steps
+    value = n_ops * world / (ms_step * 1e-3) / 1e6
+
+    # per-kernel durations: a second pass of the same steps with per-launch CUDA events
+    idx.profile(True)
+    idx.profile_reset()
+    for _ in range(args.steps):
+        run_step(torch, idx, bufs, stream)
+    torch.cuda.synchronize()
+    prof = idx.profile_read()
+    idx.profile(False)
+
+    # roofline of the dominant kernel: the radix-sort scatter pass
+    peak, peak_kind = measured_peaks()
+    down = prof.get("sort_downsweep", {"launches": 0, "ms": 0.0})
+    # algorithmic bytes of the scatter passes of one step (8 passes per sort, 64-bit keys, 32-bit payload):
+    # first pass reads keys only (payload = position), later passes read key+payload; all write key+payload
+    ks = 8
+    sort_items = [1 << LOG_Q, 1 << LOG_Q, 1 << LOG_R, 1 << LOG_U, 1 << LOG_U]
+    step_bytes = sum(n * ((ks) + (ks + 4)) + 7 * n * (2 * (ks + 4)) for n in sort_items)
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else "sort_downsweep"
+    achieved = step_bytes * args.steps / (down["ms"] * 1e-3) / 1e9 if down["ms"] else 0.0
+    tr = traffic_record("sort_downsweep")
+    traffic = None
+    if tr:
+        traffic = tr["dram_bytes_per_item"] * (1 << LOG_Q)
+    roofline = {"kernel": "sort_downsweep", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind + " hbm copy", "traffic": traffic,
+                "traffic_unit": "bytes per 2^24-item launch",
+                "dominant_by_time": dom,
+                "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4)
+                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+    # the search-and-apply kernel (lookup/successor): bytes it must move per query
+    rp = prof.get("read_point", {"launches": 0, "ms": 0.0})
+    nb = (1 << LOG_LOAD) // (NODE_SIZE // 2)
+    touched = nb * (1 - np.exp(-(1 << LOG_Q) / nb))
+    per_batch = (1 << LOG_Q) * (ks + 4) + touched * (NODE_SIZE // 2) * ks + 0.7 * (1 << LOG_Q) * 32 + (1 << LOG_Q) * ks
+    per_batch_succ = per_batch + (1 << LOG_Q) * ks
+    rp_bytes = (per_batch + per_batch_succ) * args.steps
+    rp_ach = rp_bytes / (rp["ms"] * 1e-3) / 1e9 if rp["ms"] else 0.0
+    apply_roofline = {"kernel": "read_point", "bound": "hbm", "achieved": rp_ach, "peak": peak, "unit": "GB/s",
+                      "frac": rp_ach / peak}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "node_size": NODE_SIZE, "key_bits": KW,
+                       "l2": "inputs larger than L2: 2.2 GB of nodes and >3 GB touched per step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "per_op": {p: {"mops": (ops[p] / (statistics.median(per_phase[p]) * 1e-3) / 1e6) if p in ops else None,
+                           "ms_p50": statistics.median(per_phase[p]),
+                           "ms_p99": float(np.percentile(per_phase[p], 99))} for p in phases},
+            "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+            "roofline": roofline, "apply_roofline": apply_roofline, "gpu_launches": launches,
+            "clocks": clocks}
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()  # noqa: E731
+        host = dict(q=pin(c["queries"]), sq=pin(c["succ_queries"]), lo=pin(c["range_lo"]), hi=pin(c["range_hi"]),
+                    ik=pin(c["ins_keys"]), iv=pin(c["ins_vals"]), rcap=bufs["rcap"])
+        n = 1 << LOG_Q
+        for k, shape, dt in (("lv", n, torch.int64), ("lf", n, torch.uint8), ("sk", n, torch.int64),
+                             ("sv", n, torch.int64), ("roff", (1 << LOG_R) + 1, torch.int64),
+                             ("rk", bufs["rcap"], torch.int64), ("rv", bufs["rcap"], torch.int64)):
+            host[k] = torch.empty(shape, dtype=dt).pin_memory()
+        for _ in range(3):
+            run_step_e2e(torch, idx, host, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run_step_e2e(torch, idx, host, stream)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_ms], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv")) + \
+            host["ik"].numel() * 8
+        d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "lf", "sk", "sv", "roff", "rk", "rv"))
+        line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+    if rank == 0 and not args.no_cpu_baseline:
+        mops, dt, desc = cpu_oracle_sample(c)
+        line["cpu_baseline"] = {"value": mops, "unit": "Mops/s", "cores": 1, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * flix.h -- C ABI of a GB300-native (sm_103a) implementation of FliX, the flipped-indexing GPU
+ * ordered map (Kharal, Brown, Henneberg, Schuhknecht: "FliX: Flipped-Indexing for Scalable GPU
+ * Queries and Updates", arXiv 2604.16725).
+ *
+ * Data layer (Sec. 3.2): buckets are chains of fixed-capacity nodes (node_size key/value slots plus
+ * maxKey, size and a node-link); the MKBA holds every bucket's maxBucket.  There is no index layer:
+ * every batch is radix-sorted by key and each bucket pulls the operations in its key range
+ * (maxBucket_{i-1}, maxBucket_i] from the sorted batch (Sec. 3.3, Sec. 4.1), then applies them in
+ * place (lookup and successor Sec. 3.3 / Sec. 6.5; insert with node split Sec. 4.3.2; delete with
+ * compaction and node reclamation Sec. 4.4; restructuring Sec. 3.5).
+ *
+ * Conventions shared by every entry point:
+ *  - Keys and values have the same width, fixed at creation: uint32 (FLIX_KEY_U32) or uint64
+ *    (FLIX_KEY_U64).  KEY_MAX = all ones is reserved: it is the last bucket's maxBucket and the
+ *    successor "none" key, so it cannot be stored.  VAL_NONE = all ones is the miss value.
+ *  - Arrays named d_* are caller-owned DEVICE memory on the handle's GPU; arrays named h_* are
+ *    caller-owned HOST memory.  Device arrays must stay valid until the stream reaches the call.
+ *    The handle owns its node pool, MKBA and scratch memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *    enqueued on it in order.  Calls that must return a size or an admission decision read a few
+ *    bytes back and synchronise the stream (stated per call).
+ *  - Batch semantics (Sec. 3.3 runs queries on a sorted batch; the paper only runs homogeneous
+ *    batches): in a mixed batch every lookup, successor and range query sees the state BEFORE the
+ *    batch; then the batch's inserts and deletes take effect in submission order.  Inserting a
+ *    present key keeps its value (Sec. 3.2); deleting an absent key does nothing.
+ *  - Errors are return codes (flix_status).  FLIX_EINVAL and FLIX_ENOMEM from an update or build
+ *    leave the structure unchanged (the node demand is counted before anything is written).
+ *  - One handle is used by one host thread and one stream at a time.
+ */
+#ifndef FLIX_H
+#define FLIX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flix_index* flix_t;
+
+typedef enum {
+    FLIX_OK = 0,
+    FLIX_EINVAL = -1,      /* bad argument, or KEY_MAX in an insert/build key array */
+    FLIX_ENOMEM = -2,      /* node pool or caller output capacity too small; nothing changed */
+    FLIX_ECUDA = -3,       /* a CUDA runtime call failed (flix_last_error has the text) */
+    FLIX_ETYPE = -4,       /* unsupported key type or node size */
+    FLIX_ETIMEDOUT = -5,   /* a bounded device-side wait gave up */
+    FLIX_EINTERNAL = -6,   /* a device-side consistency check failed */
+    FLIX_ENOTIMPL = -7
+} flix_status;
+
+typedef enum { FLIX_KEY_U32 = 0, FLIX_KEY_U64 = 1 } flix_keytype;
+
+/* Operation codes of mixed batches (flix_apply). */
+enum {
+    FLIX_OP_NOP = 0,
+    FLIX_OP_LOOKUP = 1,    /* point query (Sec. 3.3) */
+    FLIX_OP_SUCC = 2,      /* successor: smallest stored key >= key (Sec. 6.5) */
+    FLIX_OP_RANGE = 3,     /* all pairs with lo <= key <= hi; lo = key, hi = aux (named in Sec. 2.1) */
+    FLIX_OP_INSERT = 4,    /* insert (key, aux) if key is absent (Sec. 3.2, Sec. 4.3.2) */
+    FLIX_OP_DELETE = 5     /* physical delete (Sec. 3.2, Sec. 4.4) */
+};
+
+typedef struct {
+    flix_keytype key_type;
+    uint32_t node_size;    /* NS: slots per node, a power of two in [4, 128] (Sec. 5.3.1) */
+    uint32_t fill_pct;     /* keys per node after a build or restructure, % of NS (Sec. 3.2: 50) */
+    uint32_t grow;         /* nonzero: the node pool grows when an update needs more nodes */
+    uint64_t pool_nodes;   /* initial node-pool capacity; 0 = sized by the first bulk load */
+    uint32_t sort_digit_bits; /* radix digit width of the batch sort: 8 (default) */
+    uint32_t reserved[7];
+} flix_config;
+
+typedef struct {
+    uint64_t buckets;         /* number of buckets (MKBA entries) */
+    uint64_t nodes_used;      /* nodes in bucket chains */
+    uint64_t nodes_free;      /* nodes on the free list */
+    uint64_t pool_nodes;      /* node-pool capacity */
+    uint64_t live_keys;       /* stored pairs */
+    uint64_t max_chain;       /* longest bucket chain, in nodes */
+    uint64_t node_bytes;      /* bytes of one node: keys, values, maxKey, size, node-link */
+    uint64_t used_bytes;      /* nodes_used * node_bytes + MKBA and bucket heads */
+    uint64_t reserved_bytes;  /* device bytes held by the pool and the bucket arrays */
+} flix_stats_t;
+
+/* Fill *cfg with defaults for key type kt: node_size 32 (u32) or 64 (u64), fill 50%, grow on. */
+void flix_config_default(flix_config* cfg, flix_keytype kt);
+
+/* Create an empty index (one bucket with one empty node) on the current CUDA device.
+ * Returns FLIX_ETYPE for an unsupported key type or node size, FLIX_ECUDA if allocation fails. */
+int flix_create(const flix_config* cfg, flix_t* out);
+
+/* Free every device and host resource of h (synchronises the device). */
+int flix_destroy(flix_t h);
+
+/* Initial build (Sec. 3.2): sort the n pairs by key, keep the first pair of each duplicated key,
+ * cut the sorted keys into groups of fill_pct*node_size, one single-node bucket per group; each
+ * group's largest key becomes its maxBucket, the last bucket's is KEY_MAX.  Replaces the contents.
+ * d_keys/d_vals: n keys and n values.  Synchronises (reads back the distinct count).
+ * FLIX_EINVAL if a key is KEY_MAX (contents unchanged). */
+int flix_bulk_load(flix_t h, const void* d_keys, const void* d_vals, uint64_t n, void* stream);
+
+/* Point queries (Sec. 3.3): d_vals_out[i] = value of d_keys[i] or VAL_NONE; d_found_or_null[i] =
+ * 1/0 if given.  Asynchronous. */
+int flix_lookup(flix_t h, const void* d_keys, uint64_t n, void* d_vals_out, uint8_t* d_found_or_null,
+                void* stream);
+
+/* Successor queries (Sec. 6.5: smallest stored key >= key): d_keys_out[i], d_vals_out[i], or
+ * (KEY_MAX, VAL_NONE) when none exists.  Asynchronous. */
+int flix_successor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out,
+                   void* stream);
+
+/* Range queries [d_lo[i], d_hi[i]] (inclusive; empty when lo > hi): pairs ascending per query,
+ * concatenated in query order; d_offsets_out[n+1] (uint64) holds each query's start and the total.
+ * d_keys_out/d_vals_out hold out_capacity pairs.  Synchronises to read the total into
+ * *h_total_out; returns FLIX_ENOMEM (offsets written, pairs not) if it exceeds out_capacity. */
+int flix_range(flix_t h, const void* d_lo, const void* d_hi, uint64_t n, uint64_t* d_offsets_out,
+               void* d_keys_out, void* d_vals_out, uint64_t out_capacity, uint64_t* h_total_out,
+               void* stream);
+
+/* Insert n pairs (Sec. 4.3.2: merge into the first node with key <= maxKey, split full nodes into
+ * halves).  Synchronises once (node-demand admission).  FLIX_EINVAL if a key is KEY_MAX,
+ * FLIX_ENOMEM if the pool is short and grow is off; both leave the contents unchanged. */
+int flix_insert(flix_t h, const void* d_keys, const void* d_vals, uint64_t n, void* stream);
+
+/* Delete n keys (Sec. 4.4: compaction, emptied nodes leave their chain and are reused).
+ * Synchronises once. */
+int flix_delete(flix_t h, const void* d_keys, uint64_t n, void* stream);
+
+/* Mixed batch of n ops (codes FLIX_OP_*), keys d_keys, per-op aux (insert value or range hi).
+ * Reads see the pre-batch state.  Per op i:
+ *   LOOKUP: d_vals_out[i] = value or VAL_NONE, d_found[i] = hit, d_keys_out[i] = key or KEY_MAX
+ *   SUCC  : d_keys_out[i], d_vals_out[i] = successor pair or (KEY_MAX, VAL_NONE), d_found[i]
+ *   others: (KEY_MAX, VAL_NONE, 0)
+ * d_range_off[n+1]: exclusive prefix of range result counts (0 for non-range ops); the pairs go to
+ * d_range_keys/d_range_vals (capacity range_cap).  Any output pointer may be NULL if the batch has
+ * no op that writes it.  Synchronises (range total and node admission).  Errors as for
+ * flix_insert and flix_range; on FLIX_ENOMEM for the range capacity the updates are not applied. */
+int flix_apply(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d_aux, uint64_t n,
+               void* d_keys_out, void* d_vals_out, uint8_t* d_found, uint64_t* d_range_off,
+               void* d_range_keys, void* d_range_vals, uint64_t range_cap, uint64_t* h_range_total,
+               void* stream);
+
+/* Restructure (Sec. 3.5): flatten every chain, re-cut the live pairs into single-node buckets at
+ * the build fill, reset the MKBA and the free list.  Synchronises. */
+int flix_restructure(flix_t h, void* stream);
+
+/* Statistics of h (synchronises). */
+int flix_stats(flix_t h, flix_stats_t* out, void* stream);
+
+/* All live pairs in key order into d_keys/d_vals (capacity cap); *h_n = count.  Synchronises.
+ * FLIX_ENOMEM (nothing written) if the count exceeds cap. */
+int flix_export(flix_t h, void* d_keys, void* d_vals, uint64_t cap, uint64_t* h_n, void* stream);
+
+/* Layout dump in bucket and chain order, into HOST arrays (for tests and debugging).  With all
+ * arrays NULL only h_counts[3] = {buckets, nodes in chains, live keys} is written.  Otherwise:
+ * h_mkba[buckets], h_chain_len[buckets], h_node_size[nodes], h_node_bound[nodes] (maxKey),
+ * h_keys[keys], h_vals[keys]; key-width arrays are uint32 or uint64 per the key type.
+ * Synchronises. */
+int flix_dump_layout(flix_t h, uint64_t* h_counts, void* h_mkba, uint32_t* h_chain_len,
+                     uint32_t* h_node_size, void* h_node_bound, void* h_keys, void* h_vals,
+                     void* stream);
+
+/* Per-kernel timing.  While enabled, every kernel launch of h is bracketed by CUDA events on the
+ * launch stream.  flix_profile_read synchronises and returns up to max_entries rows: kernel name
+ * (NUL-terminated, 48 bytes per row in h_names), launch count and total milliseconds. */
+int flix_profile_enable(flix_t h, int enable);
+int flix_profile_reset(flix_t h);
+int flix_profile_read(flix_t h, uint32_t max_entries, char* h_names, uint64_t* h_launches,
+                      double* h_total_ms, uint32_t* h_n_entries);
+
+/* Number of kernels h has launched since creation. */
+uint64_t flix_launch_count(flix_t h);
+
+/* Text of an error code, and the last CUDA error text recorded by h (never NULL). */
+const char* flix_strerror(int code);
+const char* flix_last_error(flix_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLIX_H */

@@ -1,0 +1,187 @@
+// Initial build (Sec. 3.2), restructuring (Sec. 3.5) and the live-pair gather they and the export
+// share.
+//
+// Build: the sorted, de-duplicated pairs are cut into groups of p = fill * NS keys; group i becomes
+// node i and bucket i, whose maxBucket is the group's largest key (the last bucket's is KEY_MAX).
+// Node ids follow bucket order, and the free stack holds the remaining ids with the smallest on
+// top, so nodes allocated later stay near their buckets.
+//
+// Restructure: every bucket's live count (a walk of its chain), a scan, a gather of the live pairs
+// in bucket and chain order (globally sorted), then the same cut.
+#include "flix_internal.cuh"
+
+namespace flix {
+namespace {
+
+constexpr int BT = 256;
+
+template <class K>
+__global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ix.nb) return;
+    uint64_t c = 0;
+    uint32_t steps = 0;
+    for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
+        if (++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); break; }
+        c += ix.size[x];
+    }
+    cnt[b] = c;
+}
+
+// one warp per bucket copies its chain's pairs to out[goff[b] ...]
+template <class K>
+__global__ void k_gather(DevIdx<K> ix, const uint64_t* __restrict__ goff, K* __restrict__ ok, K* __restrict__ ov)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= ix.nb) return;
+    uint64_t o = goff[b];
+    const uint32_t NS = ix.NS;
+    uint32_t steps = 0;
+    for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
+        if (++steps > ix.cap) break;
+        const uint32_t sz = ix.size[x];
+        for (uint32_t s = lane; s < sz; s += 32) {
+            ok[o + s] = ix.keys[(uint64_t)x * NS + s];
+            ov[o + s] = ix.vals[(uint64_t)x * NS + s];
+        }
+        o += sz;
+    }
+}
+
+template <class K>
+__global__ void k_cut_keys(DevIdx<K> ix, const K* __restrict__ sk, const K* __restrict__ sv, uint64_t n, uint32_t p)
+{
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const uint64_t node = e / p, slot = e - node * p;
+    ix.keys[node * ix.NS + slot] = sk[e];
+    ix.vals[node * ix.NS + slot] = sv[e];
+}
+
+template <class K>
+__global__ void k_cut_meta(DevIdx<K> ix, const K* __restrict__ sk, uint64_t n, uint32_t p, uint64_t nb_new,
+                           uint64_t cap, uint32_t* __restrict__ free_ids)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb_new) {
+        const uint64_t lo = i * p;
+        const uint64_t hi = lo + p < n ? lo + p : n;
+        const K mb = (i + 1 == nb_new) ? key_max<K>() : sk[hi - 1];
+        ix.size[i] = (uint32_t)(hi > lo ? hi - lo : 0);
+        ix.bound[i] = mb;
+        ix.next[i] = NIL;
+        ix.mkba[i] = mb;
+        ix.head[i] = (uint32_t)i;
+    }
+    // free stack: ids nb_new .. cap-1, smallest id on top
+    if (i < cap - nb_new) free_ids[i] = (uint32_t)(cap - 1 - i);
+}
+
+// keep the first pair of each run of equal keys: flags, then compaction by a scan
+template <class K>
+__global__ void k_dedupe_flags(const K* __restrict__ skeys, uint64_t n, uint32_t* __restrict__ head)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    head[j] = (j == 0 || skeys[j] != skeys[j - 1]) ? 1u : 0u;
+}
+
+template <class K>
+__global__ void k_dedupe_write(const K* __restrict__ skeys, const uint32_t* __restrict__ sidx,
+                               const K* __restrict__ vals, uint64_t n, const uint32_t* __restrict__ head,
+                               const uint32_t* __restrict__ pos, K* __restrict__ ok, K* __restrict__ ov)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || !head[j]) return;
+    ok[pos[j]] = skeys[j];
+    ov[pos[j]] = vals[sidx[j]];
+}
+
+// counts[0] = longest chain, counts[1] = live keys, counts[2] = nodes in chains
+template <class K>
+__global__ void k_stats(DevIdx<K> ix, unsigned long long* __restrict__ out)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ix.nb) return;
+    unsigned long long c = 0, k = 0;
+    uint32_t steps = 0;
+    for (uint32_t x = ix.head[b]; x != NIL && steps <= ix.cap; x = ix.next[x], steps++) {
+        c++;
+        k += ix.size[x];
+    }
+    atomicMax(&out[0], c);
+    atomicAdd(&out[1], k);
+    atomicAdd(&out[2], c);
+}
+
+}  // namespace
+
+template <class K>
+cudaError_t live_count(Ctx& c, uint64_t* cnt)
+{
+    return launch(c, K_LIVE_COUNT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_live_count<K>, dev_view<K>(c.h), cnt);
+}
+
+template <class K>
+cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v)
+{
+    return launch(c, K_GATHER, dim3(div_up(c.h->nb * 32, BT)), dim3(BT), 0, k_gather<K>, dev_view<K>(c.h), goff,
+                  out_k, out_v);
+}
+
+template <class K>
+cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t nb_new)
+{
+    flix_index* h = c.h;
+    h->nb = nb_new;
+    DevIdx<K> ix = dev_view<K>(h);
+    cudaError_t e = launch(c, K_CUT_KEYS, dim3(div_up(n, BT)), dim3(BT), 0, k_cut_keys<K>, ix, sk, sv, n, h->p);
+    if (e) return e;
+    const uint64_t work = nb_new > h->cap - nb_new ? nb_new : h->cap - nb_new;
+    e = launch(c, K_CUT_META, dim3(div_up(work, BT)), dim3(BT), 0, k_cut_meta<K>, ix, sk, n, h->p, nb_new, h->cap,
+               h->free_ids);
+    if (e) return e;
+    h->free_top = h->cap - nb_new;
+    return cudaSuccess;
+}
+
+template <class K>
+cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K* vals, uint64_t n, K* ok, K* ov,
+                          uint32_t* n_dev)
+{
+    Arena& A = c.h->arena;
+    uint32_t* head = A.take<uint32_t>(n + 1);
+    uint32_t* pos = A.take<uint32_t>(n + 1);
+    if (!head || !pos) return cudaErrorMemoryAllocation;
+    if (n == 0) return cudaMemsetAsync(n_dev, 0, 4, c.st);
+    cudaError_t e = launch(c, K_DEDUPE, dim3(div_up(n, BT)), dim3(BT), 0, k_dedupe_flags<K>, skeys, n, head);
+    if (e) return e;
+    if ((e = scan_exclusive<uint32_t, uint32_t>(c, head, pos, n))) return e;
+    if ((e = cudaMemcpyAsync(n_dev, pos + n, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+    return launch(c, K_DEDUPE, dim3(div_up(n, BT)), dim3(BT), 0, k_dedupe_write<K>, skeys, sidx, vals, n,
+                  (const uint32_t*)head, (const uint32_t*)pos, ok, ov);
+}
+
+template <class K>
+cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
+{
+    cudaError_t e = cudaMemsetAsync(out3, 0, 3 * sizeof(uint64_t), c.st);
+    if (e) return e;
+    return launch(c, K_STATS, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_stats<K>, dev_view<K>(c.h),
+                  reinterpret_cast<unsigned long long*>(out3));
+}
+
+#define FLIX_BUILD_INST(K)                                                                                 \
+    template cudaError_t live_count<K>(Ctx&, uint64_t*);                                                   \
+    template cudaError_t gather_live<K>(Ctx&, const uint64_t*, K*, K*);                                    \
+    template cudaError_t cut_buckets<K>(Ctx&, const K*, const K*, uint64_t, uint64_t);                     \
+    template cudaError_t dedupe_sorted<K>(Ctx&, const K*, const uint32_t*, const K*, uint64_t, K*, K*,     \
+                                          uint32_t*);                                                      \
+    template cudaError_t stats_kernel<K>(Ctx&, uint64_t*);
+
+FLIX_BUILD_INST(uint32_t)
+FLIX_BUILD_INST(uint64_t)
+
+}  // namespace flix

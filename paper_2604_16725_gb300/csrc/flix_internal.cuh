@@ -1,0 +1,252 @@
+// Internal definitions shared by the FliX CUDA sources (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "flix.h"
+
+namespace flix {
+
+constexpr uint32_t NIL = 0xFFFFFFFFu;
+
+// Net effect of one key's update run within a batch (composition of its inserts and deletes in
+// submission order): insert-if-absent, delete, or delete-then-insert ("upsert": present afterwards
+// with the new value whatever the prior state).
+enum Eff : uint32_t { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
+
+// Device error word bits (checked at the next synchronising call).
+enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u };
+
+template <class K>
+__host__ __device__ constexpr K key_max() { return static_cast<K>(~K(0)); }
+
+// Device view of the data layer (Sec. 3.2).  Node pool in structure-of-arrays form: node n's keys
+// are keys[n*NS .. n*NS+size[n]) in ascending order, values alongside; bound[n] is its maxKey and
+// next[n] its node-link.  mkba[b] is bucket b's maxBucket and head[b] its first node.
+template <class K>
+struct DevIdx {
+    K* keys;
+    K* vals;
+    uint32_t* size;
+    K* bound;
+    uint32_t* next;
+    K* mkba;
+    uint32_t* head;
+    uint32_t NS;
+    uint32_t nb;
+    uint32_t cap;   // node-pool capacity: no chain walk takes more steps
+    uint32_t* err;
+};
+
+enum KernelId {
+    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_SMALL,
+    K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
+    K_PARTITION, K_READ_POINT, K_RANGE_COUNT, K_RANGE_FILL,
+    K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
+    K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY,
+    K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL,
+    K_NUM
+};
+
+// Bump allocator over one device buffer, reset at the start of every call.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    cudaError_t ensure(size_t bytes);
+    void reset() { used = 0; }
+    template <class T>
+    T* take(size_t count)
+    {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (used + bytes > cap) return nullptr;
+        T* p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return p;
+    }
+    void release();
+};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+}  // namespace flix
+
+struct flix_index {
+    flix_config cfg;
+    int kw;             // key width in bits (32 or 64)
+    size_t ks;          // key size in bytes
+    uint32_t NS;        // node capacity
+    uint32_t p;         // keys per node after a build or restructure
+    uint64_t cap = 0;   // node-pool capacity
+    uint64_t nb = 0;    // buckets
+    uint64_t free_top = 0;  // number of ids on the free stack (host mirror of the device state)
+    int device = 0;
+
+    // node pool and buckets (device)
+    void* keys = nullptr;
+    void* vals = nullptr;
+    uint32_t* size = nullptr;
+    void* bound = nullptr;
+    uint32_t* next = nullptr;
+    uint32_t* tnode = nullptr;     // per-node scratch: merged size from the update count pass
+    void* mkba = nullptr;
+    uint32_t* head = nullptr;
+    uint32_t* free_ids = nullptr;  // free stack: ids [0, free_top) are free nodes
+    uint32_t* err = nullptr;       // device error word
+
+    flix::Arena arena;
+    uint64_t* hpin = nullptr;      // small pinned host buffer for read-backs (64 words)
+
+    bool prof_on = false;
+    std::vector<flix::ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    uint64_t launches = 0;
+    std::string last_error;
+};
+
+namespace flix {
+
+extern const char* kKernelNames[K_NUM];
+
+// Per-call launch context.
+struct Ctx {
+    flix_index* h;
+    cudaStream_t st;
+};
+
+cudaEvent_t prof_event(flix_index* h);
+
+template <class Kern, class... Args>
+cudaError_t launch(Ctx& c, int kid, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
+{
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c.h->prof_on) {
+        a = prof_event(c.h);
+        b = prof_event(c.h);
+        cudaEventRecord(a, c.st);
+    }
+    kern<<<grid, block, smem, c.st>>>(args...);
+    cudaError_t e = cudaGetLastError();
+    if (c.h->prof_on) {
+        cudaEventRecord(b, c.st);
+        c.h->prof.push_back(ProfRec{kid, a, b});
+    }
+    c.h->launches++;
+    return e;
+}
+
+inline uint32_t div_up(uint64_t a, uint64_t b) { return static_cast<uint32_t>((a + b - 1) / b); }
+
+template <class K>
+DevIdx<K> dev_view(flix_index* h)
+{
+    DevIdx<K> d;
+    d.keys = static_cast<K*>(h->keys);
+    d.vals = static_cast<K*>(h->vals);
+    d.size = h->size;
+    d.bound = static_cast<K*>(h->bound);
+    d.next = h->next;
+    d.mkba = static_cast<K*>(h->mkba);
+    d.head = h->head;
+    d.NS = h->NS;
+    d.nb = static_cast<uint32_t>(h->nb);
+    d.cap = static_cast<uint32_t>(h->cap);
+    d.err = h->err;
+    return d;
+}
+
+// ---- sort and scan primitives (flix_sort.cu) -------------------------------------------------
+
+// Scratch bytes sort_pairs needs for n items.
+template <class K>
+size_t sort_scratch_bytes(uint64_t n);
+
+// Stable LSD radix sort of (key, payload) pairs by key, ascending.  vin == nullptr means the
+// payload is the item's position (0..n-1).  Output in kout/vout.  Scratch from the arena.
+template <class K>
+cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, uint64_t n);
+
+// Exclusive prefix sum out[0..n] of in[0..n) (out[n] = total).  Tin: uint32_t or uint64_t.
+template <class Tin, class Tout>
+cudaError_t scan_exclusive(Ctx& c, const Tin* in, Tout* out, uint64_t n);
+template <class Tout>
+size_t scan_scratch_bytes(uint64_t n);
+
+// ---- read path (flix_read.cu) ----------------------------------------------------------------
+
+// off[0..nb]: off[i] = number of sorted keys <= mkba[i-1] (off[0] = 0), by a merge-path co-rank
+// of the sorted MKBA with the sorted batch.  m_dev (optional) holds the batch length on the device
+// (then m is an upper bound).
+template <class K>
+cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m,
+                      const uint32_t* m_dev, uint32_t* off);
+
+template <class K>
+cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m,
+                       const uint32_t* off, const uint8_t* ops, K* keys_out, K* vals_out,
+                       uint8_t* found_out);
+
+// Range count: per range op its start (bucket, node, position) in sorted order and its pair
+// count cnt[idx] in submission order (0 for non-range ops when ops != nullptr).
+template <class K>
+cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* off,
+                        const uint8_t* ops, const K* hi, uint32_t* start_bucket, uint32_t* start_node,
+                        uint32_t* start_pos, uint64_t* cnt);
+
+template <class K>
+cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* ops,
+                       const uint32_t* start_bucket, const uint32_t* start_node, const uint32_t* start_pos,
+                       const uint64_t* off, K* rkeys, K* rvals);
+
+// ---- update path (flix_update.cu) ------------------------------------------------------------
+
+template <class K>
+cudaError_t validate_inserts(Ctx& c, const uint8_t* ops, const K* keys, uint64_t n, uint32_t* flag);
+
+// Reduce the sorted batch to one net update per key: ukey/uop/uval[0..U), U in *u_dev.
+// hom_op: FLIX_OP_INSERT or FLIX_OP_DELETE for homogeneous batches, 0 for mixed (ops used).
+template <class K>
+cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint8_t* ops,
+                         int hom_op, const K* aux, K* ukey, uint32_t* uop, K* uval, uint32_t* u_dev);
+
+template <class K>
+cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff,
+                         uint64_t* nf, uint8_t* allgone);
+
+template <class K>
+cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval,
+                         const uint32_t* uoff, const uint64_t* nf_off, const uint8_t* allgone,
+                         const uint32_t* alloc_ids, uint64_t push_base);
+
+cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint64_t from, uint64_t count, uint32_t* out);
+
+// ---- build / restructure / export (flix_build.cu) --------------------------------------------
+
+template <class K>
+cudaError_t live_count(Ctx& c, uint64_t* cnt);
+
+template <class K>
+cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v);
+
+// Cut n sorted distinct pairs into single-node buckets of p keys (Sec. 3.2); resets the free list.
+template <class K>
+cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t nb_new);
+
+template <class K>
+cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K* vals, uint64_t n,
+                          K* ok, K* ov, uint32_t* n_dev);
+
+template <class K>
+cudaError_t stats_kernel(Ctx& c, uint64_t* out3);
+
+}  // namespace flix

@@ -1,0 +1,514 @@
+// Update path: validation, per-key net effect of the sorted update list, node-demand count, free
+// list allocation and the in-place apply (insert with split, Sec. 4.3.2; delete with compaction
+// and node reclamation, Sec. 4.4).
+//
+// One warp owns one bucket and walks its chain (Sec. 4.1: an update goes to the first node with
+// key <= maxKey).  For each node that receives updates the warp lifts the node's keys and values
+// into shared memory (the paper lifts them into the tile's registers, Sec. 4.3.2), marks the
+// deleted slots (Tab. 4's mask), and computes every surviving or inserted key's position in the
+// merged run: a node key's position is its slot minus the deletions before it plus the inserted
+// keys before it; an inserted key's position is the count of surviving node keys below it plus the
+// inserted keys before it.  The merged run of t keys is laid out canonically: one node if
+// t <= NS, else floor(t / (NS/2)) nodes of NS/2 keys with the remainder in the last; the node keeps
+// the first piece, new nodes (popped from the free stack in bucket order) take the others, every
+// piece but the last takes its largest key as maxKey and the last keeps the node's maxKey.  An
+// emptied node leaves the chain and its id is pushed on the free stack, unless the bucket's whole
+// chain emptied, in which case its first node stays as an empty node.
+//
+// A count pass computes each node's merged size and each bucket's node demand before anything is
+// written, so that a batch the pool cannot hold is rejected with the structure unchanged.
+#include "flix_internal.cuh"
+
+namespace flix {
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int UP_THREADS = 128;
+constexpr int UP_WARPS = UP_THREADS / 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+template <class K>
+__global__ void k_validate(const uint8_t* __restrict__ ops, const K* __restrict__ keys, uint64_t n, uint32_t* flag)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if ((ops == nullptr || ops[i] == FLIX_OP_INSERT) && keys[i] == key_max<K>()) atomicOr(flag, ERR_BADKEY);
+}
+
+// head[j] = 1 where a new key starts in the sorted batch
+template <class K>
+__global__ void k_fold_flags(const K* __restrict__ skeys, uint64_t m, uint32_t* __restrict__ head)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    head[j] = (j == 0 || skeys[j] != skeys[j - 1]) ? 1u : 0u;
+}
+
+__global__ void k_fold_init(uint64_t m, uint32_t* __restrict__ lastdel, uint32_t* __restrict__ firstins,
+                            uint32_t* __restrict__ emit)
+{
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    lastdel[r] = 0;
+    firstins[r] = NIL;
+    emit[r] = 0;
+}
+
+// run id of sorted position j = inclusive count of heads up to j, minus one
+__device__ __forceinline__ uint32_t run_id(const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex, uint64_t j)
+{
+    return hex[j] + head[j] - 1;
+}
+
+// last delete of each run (position + 1)
+__global__ void k_fold_del(const uint32_t* __restrict__ sidx, uint64_t m, const uint8_t* __restrict__ ops,
+                           const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
+                           uint32_t* __restrict__ lastdel)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    if (ops[sidx[j]] == FLIX_OP_DELETE) atomicMax(&lastdel[run_id(head, hex, j)], (uint32_t)(j + 1));
+}
+
+// first insert after the run's last delete
+__global__ void k_fold_ins(const uint32_t* __restrict__ sidx, uint64_t m, const uint8_t* __restrict__ ops,
+                           const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
+                           const uint32_t* __restrict__ lastdel, uint32_t* __restrict__ firstins)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    if (ops[sidx[j]] != FLIX_OP_INSERT) return;
+    const uint32_t r = run_id(head, hex, j);
+    if ((uint32_t)(j + 1) > lastdel[r]) atomicMin(&firstins[r], (uint32_t)j);
+}
+
+// per run: net effect, emit flag and head position
+__global__ void k_fold_emit(uint64_t m, const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
+                            const uint32_t* __restrict__ lastdel, const uint32_t* __restrict__ firstins,
+                            uint32_t* __restrict__ emit, uint32_t* __restrict__ eff, uint32_t* __restrict__ hpos)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m || !head[j]) return;
+    const uint32_t r = hex[j];
+    const uint32_t ld = lastdel[r], fi = firstins[r];
+    uint32_t e;
+    if (ld == 0) e = fi == NIL ? EFF_NONE : EFF_INS;
+    else e = fi == NIL ? EFF_DEL : EFF_UPS;
+    emit[r] = e != EFF_NONE;
+    eff[r] = e;
+    hpos[r] = (uint32_t)j;
+}
+
+template <class K>
+__global__ void k_fold_write_mixed(uint64_t m, const K* __restrict__ skeys, const uint32_t* __restrict__ sidx,
+                                   const K* __restrict__ aux, const uint32_t* __restrict__ emit,
+                                   const uint32_t* __restrict__ epos, const uint32_t* __restrict__ eff,
+                                   const uint32_t* __restrict__ hpos, const uint32_t* __restrict__ firstins,
+                                   K* __restrict__ ukey, uint32_t* __restrict__ uop, K* __restrict__ uval)
+{
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m || !emit[r]) return;
+    const uint32_t p = epos[r];
+    ukey[p] = skeys[hpos[r]];
+    uop[p] = eff[r];
+    const uint32_t fi = firstins[r];
+    uval[p] = fi != NIL ? aux[sidx[fi]] : K(0);
+}
+
+// homogeneous batch: every head emits; a stable sort puts the first submitted op at the head
+template <class K>
+__global__ void k_fold_write_hom(uint64_t m, uint32_t eff, const K* __restrict__ skeys,
+                                 const uint32_t* __restrict__ sidx, const K* __restrict__ aux,
+                                 const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
+                                 K* __restrict__ ukey, uint32_t* __restrict__ uop, K* __restrict__ uval)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m || !head[j]) return;
+    const uint32_t p = hex[j];
+    ukey[p] = skeys[j];
+    uop[p] = eff;
+    uval[p] = (eff == EFF_INS && aux) ? aux[sidx[j]] : K(0);
+}
+
+__device__ __forceinline__ uint32_t pieces_of(uint32_t t, uint32_t NS)
+{
+    if (t == 0) return 0;
+    if (t <= NS) return 1;
+    return t / (NS >> 1);
+}
+
+// position in nk[0..sz) (shared memory) of the first key >= q
+template <class K>
+__device__ __forceinline__ uint32_t smem_lower_bound(const K* nk, uint32_t sz, K q)
+{
+    uint32_t base = 0, len = sz;
+    while (len > 0) {
+        uint32_t half = len >> 1;
+        if (nk[base + half] < q) { base += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return base;
+}
+
+// number of updates in [j, ue) whose key <= bd (the prefix routed to the current node)
+template <class K>
+__device__ __forceinline__ uint32_t routed_end(const K* __restrict__ ukey, uint32_t j, uint32_t ue, K bd)
+{
+    uint32_t k = j;
+    for (;;) {
+        const uint32_t u = k + (threadIdx.x & 31);
+        const bool in = u < ue && ukey[u] <= bd;
+        const uint32_t n = __popc(__ballot_sync(FULL, in));
+        k += n;
+        if (n < 32) return k;
+    }
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <class K>
+__global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
+                                                             const uint32_t* __restrict__ uop,
+                                                             const uint32_t* __restrict__ uoff,
+                                                             uint32_t* __restrict__ tnode, uint64_t* __restrict__ nf,
+                                                             uint8_t* __restrict__ allgone)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t NS = ix.NS;
+    K* sk = reinterpret_cast<K*>(smem_raw) + (size_t)w * NS;
+    const uint64_t b = (uint64_t)blockIdx.x * UP_WARPS + w;
+    if (b >= ix.nb) return;
+    const uint32_t us = uoff[b], ue = uoff[b + 1];
+    if (us == ue) {
+        if (lane == 0) { nf[b] = 0; allgone[b] = 0; }
+        return;
+    }
+    uint32_t node = ix.head[b];
+    uint32_t j = us;
+    uint64_t need = 0, dropped = 0;
+    bool all_dropped = true;
+    uint32_t steps = 0;
+    while (j < ue) {
+        if (node == NIL || ++steps > ix.cap) { if (lane == 0) atomicOr(ix.err, ERR_CHAIN); return; }
+        const uint32_t sz = ix.size[node];
+        const K bd = ix.bound[node];
+        const uint32_t nx = ix.next[node];
+        const uint32_t k = routed_end(ukey, j, ue, bd);
+        if (k == j) { all_dropped = false; node = nx; continue; }
+        for (uint32_t s = lane; s < sz; s += 32) sk[s] = ix.keys[(uint64_t)node * NS + s];
+        __syncwarp();
+        uint32_t add = 0, del = 0;
+        for (uint32_t c0 = j; c0 < k; c0 += 32) {
+            const uint32_t u = c0 + lane;
+            if (u < k) {
+                const K key = ukey[u];
+                const uint32_t op = uop[u];
+                const uint32_t pos = smem_lower_bound(sk, sz, key);
+                const bool present = pos < sz && sk[pos] == key;
+                if (!present && (op == EFF_INS || op == EFF_UPS)) add++;
+                if (present && op == EFF_DEL) del++;
+            }
+        }
+        add = warp_sum<K>(add);
+        del = warp_sum<K>(del);
+        const uint32_t t = sz + add - del;
+        if (lane == 0) tnode[node] = t;
+        const uint32_t q = pieces_of(t, NS);
+        if (q > 1) need += q - 1;
+        if (t == 0) dropped++;
+        else all_dropped = false;
+        j = k;
+        node = nx;
+        __syncwarp();
+    }
+    uint64_t freed = dropped;
+    uint8_t ag = 0;
+    if (all_dropped && node == NIL) { freed = dropped - 1; ag = 1; }
+    if (lane == 0) {
+        nf[b] = need | (freed << 32);
+        allgone[b] = ag;
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const K* __restrict__ ukey,
+                                                             const uint32_t* __restrict__ uop, const K* __restrict__ uval,
+                                                             const uint32_t* __restrict__ uoff,
+                                                             const uint32_t* __restrict__ tnode,
+                                                             const uint64_t* __restrict__ nf_off,
+                                                             const uint8_t* __restrict__ allgone,
+                                                             const uint32_t* __restrict__ alloc_ids,
+                                                             uint32_t* __restrict__ free_ids, uint64_t push_base)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t NS = ix.NS, S2 = NS >> 1;
+    // per-warp shared layout: keys[NS], vals[NS], addcnt[NS + 1], delmask[NS/32 + 1]
+    const size_t per_warp = (size_t)NS * 2 * sizeof(K) + (size_t)(NS + 1) * 4 + (NS / 32 + 1) * 4;
+    unsigned char* base = smem_raw + (size_t)w * ((per_warp + 15) & ~size_t(15));
+    K* sk = reinterpret_cast<K*>(base);
+    K* sv = sk + NS;
+    uint32_t* addcnt = reinterpret_cast<uint32_t*>(sv + NS);
+    uint32_t* delmask = addcnt + NS + 1;
+    const uint64_t b = (uint64_t)blockIdx.x * UP_WARPS + w;
+    if (b >= ix.nb) return;
+    const uint32_t us = uoff[b], ue = uoff[b + 1];
+    if (us == ue) return;
+    const uint32_t lt = lanemask_lt();
+    const uint64_t need_base = nf_off[b] & 0xFFFFFFFFull;
+    const uint64_t free_base = nf_off[b] >> 32;
+    const bool ag = allgone[b] != 0;
+    uint32_t node = ix.head[b];
+    uint32_t prev_tail = NIL;
+    uint32_t j = us;
+    uint64_t acur = 0, fcur = 0;
+    bool first = true, last_dropped = false;
+    uint32_t steps = 0;
+    while (j < ue) {
+        if (node == NIL || ++steps > ix.cap) { if (lane == 0) atomicOr(ix.err, ERR_CHAIN); return; }
+        const uint32_t sz = ix.size[node];
+        const K bd = ix.bound[node];
+        const uint32_t nx = ix.next[node];
+        const uint32_t k = routed_end(ukey, j, ue, bd);
+        if (k == j) {
+            prev_tail = node;
+            node = nx;
+            first = false;
+            last_dropped = false;
+            continue;
+        }
+        const uint32_t t = tnode[node];
+        const uint32_t q = pieces_of(t, NS);
+        // lift the node
+        for (uint32_t s = lane; s < sz; s += 32) {
+            sk[s] = ix.keys[(uint64_t)node * NS + s];
+            sv[s] = ix.vals[(uint64_t)node * NS + s];
+        }
+        for (uint32_t s = lane; s <= NS; s += 32) addcnt[s] = 0;
+        if (lane <= NS / 32) delmask[lane] = 0;
+        __syncwarp();
+        // output slot of merged position p: piece r (node for r = 0, new nodes after), slot in piece
+        auto place = [&](uint32_t p, K key, K val) {
+            uint32_t r = 0;
+            if (q > 1) { r = p / S2; if (r > q - 1) r = q - 1; }
+            const uint32_t slot = p - r * S2;
+            const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
+            ix.keys[(uint64_t)dn * NS + slot] = key;
+            ix.vals[(uint64_t)dn * NS + slot] = val;
+            if (q > 1 && r < q - 1 && slot == S2 - 1) ix.bound[dn] = key;
+        };
+        // pass 1: deletions mark their slot (Tab. 4's mask); upserts of present keys replace values
+        for (uint32_t c0 = j; c0 < k; c0 += 32) {
+            const uint32_t u = c0 + lane;
+            if (u < k) {
+                const K key = ukey[u];
+                const uint32_t op = uop[u];
+                const uint32_t pos = smem_lower_bound(sk, sz, key);
+                if (pos < sz && sk[pos] == key) {
+                    if (op == EFF_DEL) atomicOr(&delmask[pos >> 5], 1u << (pos & 31));
+                    else if (op == EFF_UPS) sv[pos] = uval[u];
+                }
+            }
+        }
+        __syncwarp();
+        // pass 2: inserted keys take their merged position
+        uint32_t added_before = 0;
+        for (uint32_t c0 = j; c0 < k; c0 += 32) {
+            const uint32_t u = c0 + lane;
+            bool add = false;
+            K key = K(0);
+            uint32_t pos = 0;
+            if (u < k) {
+                key = ukey[u];
+                const uint32_t op = uop[u];
+                pos = smem_lower_bound(sk, sz, key);
+                const bool present = pos < sz && sk[pos] == key;
+                add = !present && (op == EFF_INS || op == EFF_UPS);
+            }
+            const uint32_t am = __ballot_sync(FULL, add);
+            if (add) {
+                uint32_t dels_below = 0;
+                for (uint32_t wd = 0; wd < (pos >> 5); wd++) dels_below += __popc(delmask[wd]);
+                if (pos & 31) dels_below += __popc(delmask[pos >> 5] & ((1u << (pos & 31)) - 1));
+                const uint32_t p = pos - dels_below + added_before + __popc(am & lt);
+                place(p, key, uval[u]);
+                atomicAdd(&addcnt[pos], 1u);
+            }
+            added_before += __popc(am);
+        }
+        __syncwarp();
+        // pass 3: surviving node keys shift by (inserted before) - (deleted before)
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < sz; c0 += 32) {
+            const uint32_t s = c0 + lane;
+            uint32_t a = s < sz ? addcnt[s] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(FULL, a, o);
+                if (lane >= o) a += y;
+            }
+            if (s < sz && !((delmask[s >> 5] >> (s & 31)) & 1u)) {
+                uint32_t dels_below = 0;
+                for (uint32_t wd = 0; wd < (s >> 5); wd++) dels_below += __popc(delmask[wd]);
+                if (s & 31) dels_below += __popc(delmask[s >> 5] & ((1u << (s & 31)) - 1));
+                place(s - dels_below + carry + a, sk[s], sv[s]);
+            }
+            carry += __shfl_sync(FULL, a, 31);
+        }
+        // chain metadata
+        if (t == 0) {
+            if (ag && first) {
+                // the whole chain empties: its first node stays as the bucket's only node
+                if (lane == 0) ix.size[node] = 0;
+                prev_tail = node;
+                last_dropped = false;
+            } else {
+                if (lane == 0) {
+                    if (prev_tail == NIL) ix.head[b] = nx; else ix.next[prev_tail] = nx;
+                    free_ids[push_base + free_base + fcur] = node;
+                }
+                fcur++;
+                last_dropped = (nx == NIL);
+            }
+        } else {
+            for (uint32_t r = lane; r < q; r += 32) {
+                const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
+                const uint32_t dnext = r + 1 < q ? alloc_ids[need_base + acur + r] : nx;
+                ix.size[dn] = r + 1 < q ? S2 : t - (q - 1) * S2;
+                ix.next[dn] = dnext;
+                if (r + 1 == q) ix.bound[dn] = bd;
+            }
+            if (lane == 0) {
+                if (prev_tail == NIL) ix.head[b] = node; else ix.next[prev_tail] = node;
+            }
+            prev_tail = q > 1 ? alloc_ids[need_base + acur + q - 2] : node;
+            acur += q - 1;
+            last_dropped = false;
+        }
+        first = false;
+        j = k;
+        node = nx;
+        __syncwarp();
+    }
+    if (last_dropped && lane == 0 && prev_tail != NIL) ix.bound[prev_tail] = ix.mkba[b];
+}
+
+__global__ void k_alloc_copy(const uint32_t* __restrict__ free_ids, uint64_t from, uint64_t count,
+                             uint32_t* __restrict__ out)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = free_ids[from + i];
+}
+
+template <class K>
+size_t count_smem(uint32_t NS) { return (size_t)UP_WARPS * NS * sizeof(K); }
+
+template <class K>
+size_t apply_smem(uint32_t NS)
+{
+    const size_t per_warp = (size_t)NS * 2 * sizeof(K) + (size_t)(NS + 1) * 4 + (NS / 32 + 1) * 4;
+    return (size_t)UP_WARPS * ((per_warp + 15) & ~size_t(15));
+}
+
+}  // namespace
+
+template <class K>
+cudaError_t validate_inserts(Ctx& c, const uint8_t* ops, const K* keys, uint64_t n, uint32_t* flag)
+{
+    return launch(c, K_VALIDATE, dim3(div_up(n, 256)), dim3(256), 0, k_validate<K>, ops, keys, n, flag);
+}
+
+template <class K>
+cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint8_t* ops, int hom_op,
+                         const K* aux, K* ukey, uint32_t* uop, K* uval, uint32_t* u_dev)
+{
+    Arena& A = c.h->arena;
+    uint32_t* head = A.take<uint32_t>(m + 1);
+    uint32_t* hex = A.take<uint32_t>(m + 1);
+    if (!head || !hex) return cudaErrorMemoryAllocation;
+    const uint32_t g = div_up(m ? m : 1, 256);
+    cudaError_t e;
+    if (m == 0) return cudaMemsetAsync(u_dev, 0, 4, c.st);
+    if ((e = launch(c, K_FOLD_FLAGS, dim3(g), dim3(256), 0, k_fold_flags<K>, skeys, m, head))) return e;
+    if ((e = scan_exclusive<uint32_t, uint32_t>(c, head, hex, m))) return e;
+    if (hom_op) {
+        // U = number of distinct keys = hex[m]
+        if ((e = cudaMemcpyAsync(u_dev, hex + m, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+        const uint32_t eff = hom_op == FLIX_OP_INSERT ? EFF_INS : EFF_DEL;
+        return launch(c, K_FOLD_WRITE, dim3(g), dim3(256), 0, k_fold_write_hom<K>, m, eff, skeys, sidx, aux,
+                      (const uint32_t*)head, (const uint32_t*)hex, ukey, uop, uval);
+    }
+    uint32_t* lastdel = A.take<uint32_t>(m);
+    uint32_t* firstins = A.take<uint32_t>(m);
+    uint32_t* emit = A.take<uint32_t>(m + 1);
+    uint32_t* eff = A.take<uint32_t>(m);
+    uint32_t* hpos = A.take<uint32_t>(m);
+    uint32_t* epos = A.take<uint32_t>(m + 1);
+    if (!lastdel || !firstins || !emit || !eff || !hpos || !epos) return cudaErrorMemoryAllocation;
+    if ((e = launch(c, K_FOLD_INIT, dim3(g), dim3(256), 0, k_fold_init, m, lastdel, firstins, emit))) return e;
+    if ((e = launch(c, K_FOLD_DEL, dim3(g), dim3(256), 0, k_fold_del, sidx, m, ops, (const uint32_t*)head,
+                    (const uint32_t*)hex, lastdel)))
+        return e;
+    if ((e = launch(c, K_FOLD_INS, dim3(g), dim3(256), 0, k_fold_ins, sidx, m, ops, (const uint32_t*)head,
+                    (const uint32_t*)hex, (const uint32_t*)lastdel, firstins)))
+        return e;
+    if ((e = launch(c, K_FOLD_EMIT, dim3(g), dim3(256), 0, k_fold_emit, m, (const uint32_t*)head,
+                    (const uint32_t*)hex, (const uint32_t*)lastdel, (const uint32_t*)firstins, emit, eff, hpos)))
+        return e;
+    if ((e = scan_exclusive<uint32_t, uint32_t>(c, emit, epos, m))) return e;
+    if ((e = cudaMemcpyAsync(u_dev, epos + m, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+    return launch(c, K_FOLD_WRITE, dim3(g), dim3(256), 0, k_fold_write_mixed<K>, m, skeys, sidx, aux,
+                  (const uint32_t*)emit, (const uint32_t*)epos, (const uint32_t*)eff, (const uint32_t*)hpos,
+                  (const uint32_t*)firstins, ukey, uop, uval);
+}
+
+template <class K>
+cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff, uint64_t* nf,
+                         uint8_t* allgone)
+{
+    const uint32_t grid = div_up(c.h->nb, UP_WARPS);
+    return launch(c, K_UPD_COUNT, dim3(grid), dim3(UP_THREADS), count_smem<K>(c.h->NS), k_update_count<K>,
+                  dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone);
+}
+
+template <class K>
+cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint32_t* uoff,
+                         const uint64_t* nf_off, const uint8_t* allgone, const uint32_t* alloc_ids,
+                         uint64_t push_base)
+{
+    const uint32_t grid = div_up(c.h->nb, UP_WARPS);
+    return launch(c, K_UPD_APPLY, dim3(grid), dim3(UP_THREADS), apply_smem<K>(c.h->NS), k_update_apply<K>,
+                  dev_view<K>(c.h), ukey, uop, uval, uoff, (const uint32_t*)c.h->tnode, nf_off, allgone, alloc_ids,
+                  c.h->free_ids, push_base);
+}
+
+cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint64_t from, uint64_t count, uint32_t* out)
+{
+    return launch(c, K_ALLOC_COPY, dim3(div_up(count, 256)), dim3(256), 0, k_alloc_copy, free_ids, from, count, out);
+}
+
+#define FLIX_UPD_INST(K)                                                                                        \
+    template cudaError_t validate_inserts<K>(Ctx&, const uint8_t*, const K*, uint64_t, uint32_t*);             \
+    template cudaError_t fold_updates<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint8_t*, int,       \
+                                         const K*, K*, uint32_t*, K*, uint32_t*);                              \
+    template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const uint32_t*, uint64_t*, uint8_t*); \
+    template cudaError_t update_apply<K>(Ctx&, const K*, const uint32_t*, const K*, const uint32_t*,           \
+                                         const uint64_t*, const uint8_t*, const uint32_t*, uint64_t);
+
+FLIX_UPD_INST(uint32_t)
+FLIX_UPD_INST(uint64_t)
+
+}  // namespace flix

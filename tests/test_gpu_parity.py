@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element, on seeded inputs.
+
+All results are integers, so the bar is bit-exact equality of every output array and of the
+bucket/node layout (MKBA, chain lengths, node sizes, maxKeys, keys and values in chain order).
+Sizes span several sort tiles (4096 items), partition tiles (2048 merged items) and ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workload as W
+from tests.gpu_util import (apply_both, compare_contents, compare_layout, np_of, oracle_pair, policy_restructure,
+                            same)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fx():
+    import paper_2604_16725_gb300 as fx
+    fx.load()
+    assert torch.cuda.is_available()
+    return fx
+
+
+def test_config1_mixed_batch(fx):
+    c = W.config1(seed=0)
+    kw = c["kw"]
+    idx = fx.Index(key_bits=kw, node_size=32)
+    idx.bulk_load(c["load_keys"], c["load_vals"])
+    mp, md = oracle_pair(kw, 32, 50, c["load_keys"], c["load_vals"])
+    compare_layout(idx, md)
+    apply_both(idx, mp, md, c["ops"], c["keys"], c["aux"], kw)
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+
+
+def test_config1_homogeneous_batches(fx):
+    c = W.config1(seed=0)
+    kw = c["kw"]
+    idx = fx.Index(key_bits=kw, node_size=32)
+    idx.bulk_load(c["load_keys"], c["load_vals"])
+    mp, md = oracle_pair(kw, 32, 50, c["load_keys"], c["load_vals"])
+    ops, keys, aux = c["ops"], c["keys"], c["aux"]
+    lk = keys[ops == W.OP_LOOKUP]
+    v, f = idx.lookup(lk)
+    e = mp.read(np.full(lk.size, W.OP_LOOKUP), lk)
+    same(np_of(v, kw), e["vals"], "lookup.vals")
+    same(f.cpu().numpy(), e["found"], "lookup.found")
+    ik, iv = keys[ops == W.OP_INSERT], aux[ops == W.OP_INSERT]
+    idx.insert(ik, iv)
+    mp.update(np.full(ik.size, W.OP_INSERT), ik, iv)
+    md.update(np.full(ik.size, W.OP_INSERT), ik, iv)
+    compare_layout(idx, md)
+    dk = keys[ops == W.OP_DELETE]
+    idx.delete(dk)
+    mp.update(np.full(dk.size, W.OP_DELETE), dk)
+    md.update(np.full(dk.size, W.OP_DELETE), dk)
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+    sk, sv = idx.successor(lk)
+    e = mp.read(np.full(lk.size, W.OP_SUCC), lk)
+    same(np_of(sk, kw), e["keys"], "succ.keys")
+    same(np_of(sv, kw), e["vals"], "succ.vals")
+
+
+@pytest.mark.parametrize("kw,NS", [(32, 2), (64, 4), (32, 8), (64, 16), (32, 32), (64, 64), (32, 128), (64, 128)])
+def test_random_mixed_sequences(fx, kw, NS):
+    rng = np.random.default_rng(NS * 7 + kw)
+    dom = 1 << 16 if kw == 32 else 1 << 40
+    load = np.unique(rng.integers(0, dom, 3000, dtype=np.uint64))
+    load = load[rng.permutation(load.size)].astype(np.uint64)
+    fill = 50 if NS > 2 else 100
+    idx = fx.Index(key_bits=kw, node_size=NS, fill_pct=fill)
+    idx.bulk_load(load.astype(np.uint32 if kw == 32 else np.uint64), (load * 3 + 1).astype(np.uint32 if kw == 32 else np.uint64))
+    mp, md = oracle_pair(kw, NS, fill, load, load * 3 + 1)
+    compare_layout(idx, md)
+    dt = np.uint32 if kw == 32 else np.uint64
+    for b in range(14):
+        n = int(rng.integers(0, 9000))
+        center = int(rng.integers(0, dom))
+        width = dom if b % 3 else max(dom // 200, 64)
+        keys = ((center + rng.integers(0, width, n)) % dom).astype(np.uint64)
+        ops = rng.choice([W.OP_LOOKUP, W.OP_SUCC, W.OP_RANGE, W.OP_INSERT, W.OP_INSERT, W.OP_DELETE, W.OP_DELETE,
+                          W.OP_NOP], n).astype(np.uint8)
+        # some deletes and lookups of stored keys, some repeated keys inside the batch
+        kk, _ = mp.export()
+        if kk.size and n:
+            pick = rng.random(n) < 0.4
+            keys[pick] = kk[rng.integers(0, kk.size, int(pick.sum()))]
+            rep = rng.random(n) < 0.05
+            keys[rep] = keys[0]
+        aux = np.where(ops == W.OP_RANGE, np.minimum(keys + rng.integers(0, dom // 500 + 2, n).astype(np.uint64),
+                                                     np.uint64(dom)),
+                       rng.integers(0, 1 << 30, n).astype(np.uint64))
+        aux[(ops == W.OP_RANGE) & (rng.random(n) < 0.05)] = 0          # some lo > hi
+        apply_both(idx, mp, md, ops, keys.astype(dt), aux.astype(dt), kw)
+        compare_layout(idx, md)
+        if b % 5 == 4:
+            idx.restructure()
+            md.restructure()
+            compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+
+
+def test_read_scale_small(fx):
+    kw = 64
+    c = W.read_scale(seed=2000, n_load=1 << 18, batch=(1 << 16) + 37, n_range=(1 << 12) + 5, max_len=1000)
+    idx = fx.Index(key_bits=kw, node_size=64)
+    idx.bulk_load(c["load_keys"], c["load_vals"])
+    mp = oracle.Map(kw)
+    mp.bulk_load(c["load_keys"], c["load_vals"])
+    q = c["queries"]
+    v, f = idx.lookup(q)
+    e = mp.read(np.full(q.size, W.OP_LOOKUP), q)
+    same(np_of(v, kw), e["vals"], "lookup.vals")
+    same(f.cpu().numpy(), e["found"], "lookup.found")
+    assert abs(e["found"].mean() - 0.7) < 0.01
+    sk, sv = idx.successor(q)
+    e = mp.read(np.full(q.size, W.OP_SUCC), q)
+    same(np_of(sk, kw), e["keys"], "succ.keys")
+    same(np_of(sv, kw), e["vals"], "succ.vals")
+    lo, hi = c["range_lo"], c["range_hi"]
+    off, rk, rv = idx.range(lo, hi)
+    e = mp.read(np.full(lo.size, W.OP_RANGE), lo, hi)
+    same(off.cpu().numpy().view(np.uint64), e["range_off"], "range.off")
+    same(np_of(rk, kw), e["range_keys"], "range.keys")
+    same(np_of(rv, kw), e["range_vals"], "range.vals")
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "zipf_dense", "sequential"])
+def test_update_heavy_small(fx, dist):
+    kw, NS = 32, 32
+    ins, deletes = W.update_heavy(dist, seed=3000, n_batches=10, batch=(1 << 13) + 3, n_del_batches=4)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    mp, md = oracle_pair(kw, NS, 50, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    compare_layout(idx, md)
+    for k, v in ins:
+        idx.insert(k, v)
+        mp.update(np.full(k.size, W.OP_INSERT), k, v)
+        md.update(np.full(k.size, W.OP_INSERT), k, v)
+        compare_layout(idx, md)
+        policy_restructure(idx, md)
+        compare_layout(idx, md)
+    stored, _ = mp.export()
+    for d in deletes(stored.astype(np.uint32)):
+        idx.delete(d)
+        mp.update(np.full(d.size, W.OP_DELETE), d)
+        md.update(np.full(d.size, W.OP_DELETE), d)
+        compare_layout(idx, md)
+    idx.restructure()
+    md.restructure()
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+
+
+def test_edge_cases(fx):
+    for kw in (32, 64):
+        dt = np.uint32 if kw == 32 else np.uint64
+        km = (1 << kw) - 1
+        idx = fx.Index(key_bits=kw, node_size=8)
+        # empty index
+        v, f = idx.lookup(np.array([0, 5, km], dt))
+        assert np_of(v, kw).tolist() == [km] * 3 and f.cpu().tolist() == [0, 0, 0]
+        sk, sv = idx.successor(np.array([0, km], dt))
+        assert np_of(sk, kw).tolist() == [km, km]
+        off, rk, rv = idx.range(np.array([0], dt), np.array([km], dt))
+        assert off.cpu().tolist() == [0, 0]
+        # empty batches
+        idx.insert(np.zeros(0, dt), np.zeros(0, dt))
+        idx.delete(np.zeros(0, dt))
+        v, f = idx.lookup(np.zeros(0, dt))
+        assert v.numel() == 0
+        # reserved key rejected, structure unchanged
+        idx.insert(np.array([1, 2, 3], dt), np.array([10, 20, 30], dt))
+        before = idx.dump_layout()
+        with pytest.raises(fx.FlixError) as ei:
+            idx.insert(np.array([4, km], dt), np.array([1, 1], dt))
+        assert ei.value.code == -1
+        with pytest.raises(fx.FlixError):
+            idx.bulk_load(np.array([km], dt), np.array([0], dt))
+        after = idx.dump_layout()
+        for fld in before:
+            same(before[fld], after[fld], "unchanged." + fld)
+        # duplicates in a bulk load keep the first pair
+        idx.bulk_load(np.array([9, 7, 9, 7], dt), np.array([1, 2, 3, 4], dt))
+        k, vv = idx.export()
+        assert np_of(k, kw).tolist() == [7, 9] and np_of(vv, kw).tolist() == [2, 1]
+        # lookup / delete of KEY_MAX is a miss / no-op
+        idx.delete(np.array([km], dt))
+        v, f = idx.lookup(np.array([km], dt))
+        assert f.cpu().tolist() == [0]
+        # range capacity too small
+        L = fx.load()
+        import ctypes
+        lo = torch.tensor([0], dtype=idx.tdtype, device="cuda")
+        hi = torch.tensor([-1], dtype=idx.tdtype, device="cuda")
+        offs = torch.empty(2, dtype=torch.int64, device="cuda")
+        rk = torch.empty(1, dtype=idx.tdtype, device="cuda")
+        tot = ctypes.c_uint64(0)
+        code = L.flix_range(idx._h, ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(hi.data_ptr()), 1,
+                            ctypes.c_void_p(offs.data_ptr()), ctypes.c_void_p(rk.data_ptr()),
+                            ctypes.c_void_p(rk.data_ptr()), 1, ctypes.byref(tot), None)
+        torch.cuda.synchronize()
+        assert code == -2 and tot.value == 2
+
+
+def test_pool_exhaustion_leaves_structure_unchanged(fx):
+    kw = 32
+    dt = np.uint32
+    idx = fx.Index(key_bits=kw, node_size=4, pool_nodes=8, grow=False)
+    idx.bulk_load(np.arange(1, 9, dtype=dt), np.arange(1, 9, dtype=dt))     # 4 buckets of 2 keys
+    before = idx.dump_layout()
+    with pytest.raises(fx.FlixError) as ei:
+        idx.insert(np.arange(100, 140, dtype=dt), np.arange(40, dtype=dt))
+    assert ei.value.code == -2
+    after = idx.dump_layout()
+    for fld in before:
+        same(before[fld], after[fld], "unchanged." + fld)
+    # with growth on, the same batch succeeds and matches the model
+    idx2 = fx.Index(key_bits=kw, node_size=4, pool_nodes=8, grow=True)
+    idx2.bulk_load(np.arange(1, 9, dtype=dt), np.arange(1, 9, dtype=dt))
+    md = oracle.Model(kw, 4, 50)
+    md.bulk_load(np.arange(1, 9), np.arange(1, 9))
+    idx2.insert(np.arange(100, 140, dtype=dt), np.arange(40, dtype=dt))
+    md.update(np.full(40, W.OP_INSERT), np.arange(100, 140), np.arange(40))
+    compare_layout(idx2, md)
+    assert idx2.stats()["pool_nodes"] > 8
+
+
+@pytest.mark.slow
+def test_read_scale_full_size_sampled(fx):
+    """The read-scale workload at full size (2^26 u64 keys, NS = 64, 2^24 queries, 2^18 ranges) in
+    the launch configuration the benchmark times; sampled outputs checked against the oracle's
+    definitions over the sorted stored set."""
+    kw = 64
+    c = W.read_scale(seed=2000)
+    idx = fx.Index(key_bits=kw, node_size=64)
+    keys_d = torch.from_numpy(c["load_keys"].view(np.int64)).cuda()
+    vals_d = torch.from_numpy(c["load_vals"].view(np.int64)).cuda()
+    idx.bulk_load(keys_d, vals_d)
+    order = np.argsort(c["load_keys"])
+    sk_all, sv_all = c["load_keys"][order], c["load_vals"][order]
+    s = idx.stats()
+    assert s["buckets"] == (1 << 26) // 32 and s["live_keys"] == 1 << 26 and s["max_chain"] == 1
+    q = c["queries"]
+    qd = torch.from_numpy(q.view(np.int64)).cuda()
+    v, f = idx.lookup(qd)
+    sk, sv = idx.successor(qd)
+    rng = np.random.default_rng(1)
+    samp = np.concatenate([rng.integers(0, q.size, 200000), np.arange(4096), np.arange(q.size - 4096, q.size)])
+    ev, ef = oracle.sorted_lookup(sk_all, sv_all, q[samp], kw)
+    same(np_of(v, kw)[samp], ev, "lookup.vals")
+    same(f.cpu().numpy()[samp], ef, "lookup.found")
+    esk, esv, _ = oracle.sorted_successor(sk_all, sv_all, q[samp], kw)
+    same(np_of(sk, kw)[samp], esk, "succ.keys")
+    same(np_of(sv, kw)[samp], esv, "succ.vals")
+    lo, hi = c["range_lo"], c["range_hi"]
+    off, rk, rv = idx.range(lo, hi)
+    offn = off.cpu().numpy().view(np.uint64)
+    same(np.diff(offn), oracle.sorted_range_counts(sk_all, lo, hi), "range.counts")
+    rkn, rvn = np_of(rk, kw), np_of(rv, kw)
+    for i in rng.integers(0, lo.size, 2000):
+        a = np.searchsorted(sk_all, lo[i], "left")
+        b = np.searchsorted(sk_all, hi[i], "right")
+        same(rkn[offn[i]:offn[i + 1]], sk_all[a:b], "range.keys")
+        same(rvn[offn[i]:offn[i + 1]], sv_all[a:b], "range.vals")
