@@ -106,6 +106,25 @@ int flix_bulk_load(flix_t h, const void* d_keys, const void* d_vals, uint64_t n,
 int flix_lookup(flix_t h, const void* d_keys, uint64_t n, void* d_vals_out, uint8_t* d_found_or_null,
                 void* stream);
 
+/* Bytes of the fixed device scratch array used by flix_lookup_noalloc. */
+#define FLIX_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* flix_lookup without any device allocation during the call.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they query -- a process
+ * whose allocator has already reserved the whole device for its own pools, a latency-bound path
+ * that must not block on cudaMalloc's implicit device synchronisation, or a host with a custom
+ * allocator this library cannot see.  Same arguments and results as flix_lookup.
+ * Its scratch (sort buffers and bucket offsets) is one fixed array of FLIX_NOALLOC_SCRATCH_BYTES
+ * compiled into the library; every GPU that loads the library holds it until the process exits.
+ * A call needs about 24*n bytes (uint64 keys; 16*n for uint32) plus 4 bytes per bucket plus a few
+ * KB, so e.g. 2^17 keys on an index of up to 2^21 buckets fit; a larger request returns
+ * FLIX_EINVAL before launching anything (flix_last_error gives the sizes).  The first call on a
+ * device looks up the array's device address on that device, so make it before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other streams, threads or
+ * handles on the same device) race and must be serialised by the caller.  Asynchronous. */
+int flix_lookup_noalloc(flix_t h, const void* d_keys, uint64_t n, void* d_vals_out, uint8_t* d_found_or_null,
+                        void* stream);
+
 /* Successor queries (Sec. 6.5: smallest stored key >= key): d_keys_out[i], d_vals_out[i], or
  * (KEY_MAX, VAL_NONE) when none exists.  Asynchronous. */
 int flix_successor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out,

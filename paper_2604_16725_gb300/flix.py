@@ -49,6 +49,7 @@ SIGNATURES = {
     "flix_destroy": (_INT, [_VP]),
     "flix_bulk_load": (_INT, [_VP, _VP, _VP, _U64, _VP]),
     "flix_lookup": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "flix_lookup_noalloc": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_successor": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_range": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_insert": (_INT, [_VP, _VP, _VP, _U64, _VP]),
