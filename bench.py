@@ -66,7 +66,7 @@ def ops_per_step(log_q=LOG_Q, log_r=LOG_R, log_u=LOG_U):
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,11 +92,19 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Samples taken between wall-clock times t0 and t1 (seconds since the epoch)."""
+        import datetime
         rows = []
         for line in (getattr(self, "out", "") or "").splitlines():
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if t0 is not None and ts is not None and not (t0 <= ts <= t1):
                 continue
             try:
                 rows.append(dict(sm=float(p[1]), smax=float(p[2]), power=float(p[3]) if p[3] not in ("[N/A]", "N/A") else 0.0,
@@ -241,13 +249,16 @@ def reference_arm(args):
 
 
 def main():
+    global LOG_LOAD, LOG_Q
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flix", choices=["flix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
+    ap.add_argument("--log-q", type=int, default=LOG_Q, help="log2 of the lookup/successor batch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -261,7 +272,10 @@ def main():
     torch.cuda.set_device(local)
     import paper_2604_16725_gb300 as fx
 
-    c = make_inputs(seed=2000 + 17 * rank)
+    LOG_LOAD, LOG_Q = args.log_load, args.log_q
+    if (LOG_LOAD, LOG_Q) != (26, 24):
+        args.no_cpu_baseline = True
+    c = make_inputs(seed=2000 + 17 * rank, log_load=LOG_LOAD, log_q=LOG_Q)
     idx = fx.Index(key_bits=KW, node_size=NODE_SIZE)
     stream = torch.cuda.Stream()
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()  # noqa: E731
@@ -287,9 +301,11 @@ def main():
     per_phase = {p: [] for p in phases}
     step_ms = []
     launches0 = idx.launch_count()
-    barrier()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(gpu_id_for_smi(torch)) as clk:
+        time.sleep(1.0)            # let the sampler start before the timed region
+        barrier()
+        wall0 = time.time()
         t_start.record(stream)
         for _ in range(args.steps):
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -302,7 +318,9 @@ def main():
                 per_phase[p].append(events[p][0].elapsed_time(events[p][1]))
         t_end.record(stream)
         barrier()
-    clocks = clk.summary()
+        wall1 = time.time()
+        time.sleep(0.3)
+    clocks = clk.summary(wall0 - 0.25, wall1 + 0.25)
     total_ms = t_start.elapsed_time(t_end)
     launches = idx.launch_count() - launches0
     if world > 1:
@@ -310,7 +328,7 @@ def main():
         t = torch.tensor([total_ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ops = ops_per_step()
+    ops = ops_per_step(log_q=LOG_Q)
     n_ops = sum(ops.values())
     ms_step = total_ms / args.steps
     value = n_ops * world / (ms_step * 1e-3) / 1e6
