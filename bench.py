@@ -163,7 +163,7 @@ def run_step(torch, idx, bufs, stream, events=None):
             events[name][which].record(stream)
 
     ev("lookup", 0)
-    idx.lookup(bufs["q"], stream=stream, out=bufs["lv"])
+    idx.lookup(bufs["q"], stream=stream, out=bufs["lv"], found=False)
     ev("lookup", 1)
     ev("successor", 0)
     idx.successor(bufs["sq"], stream=stream)
@@ -186,9 +186,8 @@ def run_step_e2e(torch, idx, host, stream):
     """The same step through the public API from pinned host buffers; results read back to host."""
     dev = lambda t: t.to("cuda", non_blocking=True)  # noqa: E731
     with torch.cuda.stream(stream):
-        v, f = idx.lookup(dev(host["q"]), stream=stream)
+        v, _ = idx.lookup(dev(host["q"]), stream=stream, found=False)
         host["lv"].copy_(v, non_blocking=True)
-        host["lf"].copy_(f, non_blocking=True)
         sk, sv = idx.successor(dev(host["sq"]), stream=stream)
         host["sk"].copy_(sk, non_blocking=True)
         host["sv"].copy_(sv, non_blocking=True)
@@ -259,6 +258,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
     ap.add_argument("--log-q", type=int, default=LOG_Q, help="log2 of the lookup/successor batch")
+    ap.add_argument("--sort-variant", type=int, default=0, help="0 auto, 1 one-sweep, 2 reduce-then-scan")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -276,7 +276,7 @@ def main():
     if (LOG_LOAD, LOG_Q) != (26, 24):
         args.no_cpu_baseline = True
     c = make_inputs(seed=2000 + 17 * rank, log_load=LOG_LOAD, log_q=LOG_Q)
-    idx = fx.Index(key_bits=KW, node_size=NODE_SIZE)
+    idx = fx.Index(key_bits=KW, node_size=NODE_SIZE, sort_variant=args.sort_variant)
     stream = torch.cuda.Stream()
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()  # noqa: E731
     idx.bulk_load(td(c["load_keys"]), td(c["load_vals"]), stream=stream)
@@ -344,19 +344,19 @@ def main():
 
     # roofline of the dominant kernel: the radix-sort scatter pass
     peak, peak_kind = measured_peaks()
-    down = prof.get("sort_downsweep", {"launches": 0, "ms": 0.0})
+    down = prof.get("sort_onesweep", {"launches": 0, "ms": 0.0})
     # algorithmic bytes of the scatter passes of one step (8 passes per sort, 64-bit keys, 32-bit payload):
     # first pass reads keys only (payload = position), later passes read key+payload; all write key+payload
     ks = 8
     sort_items = [1 << LOG_Q, 1 << LOG_Q, 1 << LOG_R, 1 << LOG_U, 1 << LOG_U]
     step_bytes = sum(n * ((ks) + (ks + 4)) + 7 * n * (2 * (ks + 4)) for n in sort_items)
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else "sort_downsweep"
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else "sort_onesweep"
     achieved = step_bytes * args.steps / (down["ms"] * 1e-3) / 1e9 if down["ms"] else 0.0
-    tr = traffic_record("sort_downsweep")
+    tr = traffic_record("sort_onesweep")
     traffic = None
     if tr:
         traffic = tr["dram_bytes_per_item"] * (1 << LOG_Q)
-    roofline = {"kernel": "sort_downsweep", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"kernel": "sort_onesweep", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind + " hbm copy", "traffic": traffic,
                 "traffic_unit": "bytes per 2^24-item launch",
                 "dominant_by_time": dom,
@@ -378,7 +378,7 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "node_size": NODE_SIZE, "key_bits": KW,
                        "l2": "inputs larger than L2: 2.2 GB of nodes and >3 GB touched per step",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single", "sort_variant": args.sort_variant},
             "per_op": {p: {"mops": (ops[p] / (statistics.median(per_phase[p]) * 1e-3) / 1e6) if p in ops else None,
                            "ms_p50": statistics.median(per_phase[p]),
                            "ms_p99": float(np.percentile(per_phase[p], 99))} for p in phases},
@@ -390,7 +390,7 @@ def main():
         host = dict(q=pin(c["queries"]), sq=pin(c["succ_queries"]), lo=pin(c["range_lo"]), hi=pin(c["range_hi"]),
                     ik=pin(c["ins_keys"]), iv=pin(c["ins_vals"]), rcap=bufs["rcap"])
         n = 1 << LOG_Q
-        for k, shape, dt in (("lv", n, torch.int64), ("lf", n, torch.uint8), ("sk", n, torch.int64),
+        for k, shape, dt in (("lv", n, torch.int64), ("sk", n, torch.int64),
                              ("sv", n, torch.int64), ("roff", (1 << LOG_R) + 1, torch.int64),
                              ("rk", bufs["rcap"], torch.int64), ("rv", bufs["rcap"], torch.int64)):
             host[k] = torch.empty(shape, dtype=dt).pin_memory()
@@ -409,7 +409,7 @@ def main():
             e2e_ms = float(t.item())
         h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv")) + \
             host["ik"].numel() * 8
-        d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "lf", "sk", "sv", "roff", "rk", "rv"))
+        d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
         line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
     if rank == 0 and not args.no_cpu_baseline:

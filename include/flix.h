@@ -69,8 +69,13 @@ typedef struct {
     uint32_t grow;         /* nonzero: the node pool grows when an update needs more nodes */
     uint64_t pool_nodes;   /* initial node-pool capacity; 0 = sized by the first bulk load */
     uint32_t sort_digit_bits; /* radix digit width of the batch sort: 8 (default) */
-    uint32_t reserved[7];
+    uint32_t sort_variant;    /* FLIX_SORT_*: how each radix pass finds its output offsets */
+    uint32_t reserved[6];
 } flix_config;
+
+/* Batch-sort variants (same stable order, different speed): one-sweep passes with decoupled
+ * look-back, or reduce-then-scan passes (a counting read, a scan, then the scatter). */
+enum { FLIX_SORT_AUTO = 0, FLIX_SORT_ONESWEEP = 1, FLIX_SORT_REDUCE_SCAN = 2 };
 
 typedef struct {
     uint64_t buckets;         /* number of buckets (MKBA entries) */

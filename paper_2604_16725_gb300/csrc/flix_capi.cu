@@ -11,7 +11,7 @@
 namespace flix {
 
 const char* kKernelNames[K_NUM] = {
-    "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_small",
+    "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep",
     "scan_partials", "scan_top", "scan_apply",
     "partition", "read_point", "range_count", "range_fill",
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
@@ -525,6 +525,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     if (!valid_ns(cfg->node_size)) return FLIX_ETYPE;
     if (cfg->fill_pct == 0 || cfg->fill_pct > 100) return FLIX_EINVAL;
     if (cfg->sort_digit_bits != 0 && cfg->sort_digit_bits != 8) return FLIX_ENOTIMPL;
+    if (cfg->sort_variant > FLIX_SORT_REDUCE_SCAN) return FLIX_EINVAL;
     flix_index* h = new flix_index();
     h->cfg = *cfg;
     h->kw = cfg->key_type == FLIX_KEY_U32 ? 32 : 64;

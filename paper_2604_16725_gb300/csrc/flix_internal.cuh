@@ -20,7 +20,7 @@ constexpr uint32_t NIL = 0xFFFFFFFFu;
 enum Eff : uint32_t { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
 
 // Device error word bits (checked at the next synchronising call).
-enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u };
+enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u, ERR_SPIN = 16u };
 
 template <class K>
 __host__ __device__ constexpr K key_max() { return static_cast<K>(~K(0)); }
@@ -44,7 +44,7 @@ struct DevIdx {
 };
 
 enum KernelId {
-    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_SMALL,
+    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
     K_PARTITION, K_READ_POINT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,

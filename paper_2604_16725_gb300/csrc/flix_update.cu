@@ -2,8 +2,9 @@
 // list allocation and the in-place apply (insert with split, Sec. 4.3.2; delete with compaction
 // and node reclamation, Sec. 4.4).
 //
-// One warp owns one bucket and walks its chain (Sec. 4.1: an update goes to the first node with
-// key <= maxKey).  For each node that receives updates the warp lifts the node's keys and values
+// A warp owns 32 consecutive buckets: its lanes load every bucket's sublist bounds and first node
+// in parallel, then the warp works through the buckets that have updates, walking each chain
+// (Sec. 4.1: an update goes to the first node with key <= maxKey).  For each node that receives updates the warp lifts the node's keys and values
 // into shared memory (the paper lifts them into the tile's registers, Sec. 4.3.2), marks the
 // deleted slots (Tab. 4's mask), and computes every surviving or inserted key's position in the
 // merged run: a node key's position is its slot minus the deletions before it plus the inserted
@@ -178,6 +179,68 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
     return v;
 }
 
+// First-node state of the 32 consecutive buckets a warp owns (lane l: bucket b0 + l): the bucket's
+// update sublist [us, ue) and its first node's id, size, maxKey and node-link, all loaded in
+// parallel before the warp works through the buckets that have updates.
+template <class K>
+struct UGroup {
+    uint32_t us, ue, node, sz, nx;
+    K bd;
+};
+
+template <class K>
+__device__ __forceinline__ uint32_t load_ugroup(const DevIdx<K>& ix, const uint32_t* __restrict__ uoff, uint64_t b0,
+                                                uint32_t lane, UGroup<K>& g)
+{
+    const uint64_t b = b0 + lane;
+    const bool valid = b < ix.nb;
+    g.us = valid ? uoff[b] : 0u;
+    g.ue = valid ? uoff[b + 1] : 0u;
+    const bool touched = g.us < g.ue;
+    g.node = NIL;
+    g.sz = 0;
+    g.nx = NIL;
+    g.bd = K(0);
+    if (touched) {
+        g.node = ix.head[b];
+        g.sz = ix.size[g.node];
+        g.bd = ix.bound[g.node];
+        g.nx = ix.next[g.node];
+    }
+    return __ballot_sync(FULL, touched);
+}
+
+constexpr int MAXQ = 4;   // node slots per lane when a node is held in registers (NS <= 128)
+
+// Load the first sz keys (and values if vals != nullptr) of a node into per-lane registers.
+template <class K>
+__device__ __forceinline__ void lift_regs(const K* __restrict__ nk, const K* __restrict__ nv, uint32_t sz,
+                                          uint32_t lane, K (&rk)[MAXQ], K (&rv)[MAXQ])
+{
+#pragma unroll
+    for (int q = 0; q < MAXQ; q++) {
+        const uint32_t s = lane + 32 * q;
+        if (s < sz) {
+            rk[q] = nk[s];
+            if (nv) rv[q] = nv[s];
+        }
+    }
+}
+
+template <class K>
+__device__ __forceinline__ void stage_regs(K* sk, K* sv, uint32_t sz, uint32_t lane, const K (&rk)[MAXQ],
+                                           const K (&rv)[MAXQ])
+{
+#pragma unroll
+    for (int q = 0; q < MAXQ; q++) {
+        const uint32_t s = lane + 32 * q;
+        if (s < sz) {
+            sk[s] = rk[q];
+            if (sv) sv[s] = rv[q];
+        }
+    }
+}
+
 template <class K>
 __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
                                                              const uint32_t* __restrict__ uop,
@@ -189,57 +252,78 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t NS = ix.NS;
     K* sk = reinterpret_cast<K*>(smem_raw) + (size_t)w * NS;
-    const uint64_t b = (uint64_t)blockIdx.x * UP_WARPS + w;
-    if (b >= ix.nb) return;
-    const uint32_t us = uoff[b], ue = uoff[b + 1];
-    if (us == ue) {
-        if (lane == 0) { nf[b] = 0; allgone[b] = 0; }
-        return;
+    const uint64_t b0 = ((uint64_t)blockIdx.x * UP_WARPS + w) * 32;
+    if (b0 >= ix.nb) return;
+    UGroup<K> g;
+    uint32_t mask = load_ugroup(ix, uoff, b0, lane, g);
+    if (b0 + lane < ix.nb && !((mask >> lane) & 1u)) {
+        nf[b0 + lane] = 0;
+        allgone[b0 + lane] = 0;
     }
-    uint32_t node = ix.head[b];
-    uint32_t j = us;
-    uint64_t need = 0, dropped = 0;
-    bool all_dropped = true;
-    uint32_t steps = 0;
-    while (j < ue) {
-        if (node == NIL || ++steps > ix.cap) { if (lane == 0) atomicOr(ix.err, ERR_CHAIN); return; }
-        const uint32_t sz = ix.size[node];
-        const K bd = ix.bound[node];
-        const uint32_t nx = ix.next[node];
-        const uint32_t k = routed_end(ukey, j, ue, bd);
-        if (k == j) { all_dropped = false; node = nx; continue; }
-        for (uint32_t s = lane; s < sz; s += 32) sk[s] = ix.keys[(uint64_t)node * NS + s];
-        __syncwarp();
-        uint32_t add = 0, del = 0;
-        for (uint32_t c0 = j; c0 < k; c0 += 32) {
-            const uint32_t u = c0 + lane;
-            if (u < k) {
-                const K key = ukey[u];
-                const uint32_t op = uop[u];
-                const uint32_t pos = smem_lower_bound(sk, sz, key);
-                const bool present = pos < sz && sk[pos] == key;
-                if (!present && (op == EFF_INS || op == EFF_UPS)) add++;
-                if (present && op == EFF_DEL) del++;
+    while (mask) {
+        const uint32_t i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t ue = __shfl_sync(FULL, g.ue, i);
+        uint32_t j = __shfl_sync(FULL, g.us, i);
+        uint32_t node = __shfl_sync(FULL, g.node, i);
+        uint32_t sz = __shfl_sync(FULL, g.sz, i);
+        uint32_t nx = __shfl_sync(FULL, g.nx, i);
+        K bd = __shfl_sync(FULL, g.bd, i);
+        uint64_t need = 0, dropped = 0;
+        bool all_dropped = true;
+        uint32_t steps = 0;
+        for (;;) {
+            K rk[MAXQ], rv[MAXQ];
+            lift_regs<K>(ix.keys + (uint64_t)node * NS, nullptr, sz, lane, rk, rv);   // overlaps routed_end
+            const uint32_t k = routed_end(ukey, j, ue, bd);
+            if (k == j) {
+                all_dropped = false;
+            } else {
+                stage_regs<K>(sk, nullptr, sz, lane, rk, rv);
+                __syncwarp();
+                uint32_t add = 0, del = 0;
+                for (uint32_t c0 = j; c0 < k; c0 += 32) {
+                    const uint32_t u = c0 + lane;
+                    if (u < k) {
+                        const K key = ukey[u];
+                        const uint32_t op = uop[u];
+                        const uint32_t pos = smem_lower_bound(sk, sz, key);
+                        const bool present = pos < sz && sk[pos] == key;
+                        if (!present && (op == EFF_INS || op == EFF_UPS)) add++;
+                        if (present && op == EFF_DEL) del++;
+                    }
+                }
+                add = warp_sum<K>(add);
+                del = warp_sum<K>(del);
+                const uint32_t t = sz + add - del;
+                if (lane == 0) tnode[node] = t;
+                const uint32_t q = pieces_of(t, NS);
+                if (q > 1) need += q - 1;
+                if (t == 0) dropped++;
+                else all_dropped = false;
+                j = k;
+                __syncwarp();
             }
+            if (j >= ue) break;
+            node = nx;
+            if (node == NIL || ++steps > ix.cap) {
+                if (lane == 0) atomicOr(ix.err, ERR_CHAIN);
+                return;
+            }
+            sz = ix.size[node];
+            bd = ix.bound[node];
+            nx = ix.next[node];
         }
-        add = warp_sum<K>(add);
-        del = warp_sum<K>(del);
-        const uint32_t t = sz + add - del;
-        if (lane == 0) tnode[node] = t;
-        const uint32_t q = pieces_of(t, NS);
-        if (q > 1) need += q - 1;
-        if (t == 0) dropped++;
-        else all_dropped = false;
-        j = k;
-        node = nx;
-        __syncwarp();
-    }
-    uint64_t freed = dropped;
-    uint8_t ag = 0;
-    if (all_dropped && node == NIL) { freed = dropped - 1; ag = 1; }
-    if (lane == 0) {
-        nf[b] = need | (freed << 32);
-        allgone[b] = ag;
+        uint64_t freed = dropped;
+        uint8_t ag = 0;
+        if (all_dropped && nx == NIL) {   // every node of the chain empties: the first one stays
+            freed = dropped - 1;
+            ag = 1;
+        }
+        if (lane == 0) {
+            nf[b0 + i] = need | (freed << 32);
+            allgone[b0 + i] = ag;
+        }
     }
 }
 
@@ -263,147 +347,166 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
     K* sv = sk + NS;
     uint32_t* addcnt = reinterpret_cast<uint32_t*>(sv + NS);
     uint32_t* delmask = addcnt + NS + 1;
-    const uint64_t b = (uint64_t)blockIdx.x * UP_WARPS + w;
-    if (b >= ix.nb) return;
-    const uint32_t us = uoff[b], ue = uoff[b + 1];
-    if (us == ue) return;
+    const uint64_t b0 = ((uint64_t)blockIdx.x * UP_WARPS + w) * 32;
+    if (b0 >= ix.nb) return;
+    UGroup<K> g;
+    uint32_t mask = load_ugroup(ix, uoff, b0, lane, g);
+    // per-bucket allocation cursors and the first node's merged size, also in parallel
+    uint64_t nfo_l = 0;
+    uint32_t t0_l = 0, ag_l = 0;
+    if ((mask >> lane) & 1u) {
+        nfo_l = nf_off[b0 + lane];
+        ag_l = allgone[b0 + lane];
+        t0_l = tnode[g.node];
+    }
     const uint32_t lt = lanemask_lt();
-    const uint64_t need_base = nf_off[b] & 0xFFFFFFFFull;
-    const uint64_t free_base = nf_off[b] >> 32;
-    const bool ag = allgone[b] != 0;
-    uint32_t node = ix.head[b];
-    uint32_t prev_tail = NIL;
-    uint32_t j = us;
-    uint64_t acur = 0, fcur = 0;
-    bool first = true, last_dropped = false;
-    uint32_t steps = 0;
-    while (j < ue) {
-        if (node == NIL || ++steps > ix.cap) { if (lane == 0) atomicOr(ix.err, ERR_CHAIN); return; }
-        const uint32_t sz = ix.size[node];
-        const K bd = ix.bound[node];
-        const uint32_t nx = ix.next[node];
-        const uint32_t k = routed_end(ukey, j, ue, bd);
-        if (k == j) {
-            prev_tail = node;
-            node = nx;
-            first = false;
-            last_dropped = false;
-            continue;
-        }
-        const uint32_t t = tnode[node];
-        const uint32_t q = pieces_of(t, NS);
-        // lift the node
-        for (uint32_t s = lane; s < sz; s += 32) {
-            sk[s] = ix.keys[(uint64_t)node * NS + s];
-            sv[s] = ix.vals[(uint64_t)node * NS + s];
-        }
-        for (uint32_t s = lane; s <= NS; s += 32) addcnt[s] = 0;
-        if (lane <= NS / 32) delmask[lane] = 0;
-        __syncwarp();
-        // output slot of merged position p: piece r (node for r = 0, new nodes after), slot in piece
-        auto place = [&](uint32_t p, K key, K val) {
-            uint32_t r = 0;
-            if (q > 1) { r = p / S2; if (r > q - 1) r = q - 1; }
-            const uint32_t slot = p - r * S2;
-            const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
-            ix.keys[(uint64_t)dn * NS + slot] = key;
-            ix.vals[(uint64_t)dn * NS + slot] = val;
-            if (q > 1 && r < q - 1 && slot == S2 - 1) ix.bound[dn] = key;
-        };
-        // pass 1: deletions mark their slot (Tab. 4's mask); upserts of present keys replace values
-        for (uint32_t c0 = j; c0 < k; c0 += 32) {
-            const uint32_t u = c0 + lane;
-            if (u < k) {
-                const K key = ukey[u];
-                const uint32_t op = uop[u];
-                const uint32_t pos = smem_lower_bound(sk, sz, key);
-                if (pos < sz && sk[pos] == key) {
-                    if (op == EFF_DEL) atomicOr(&delmask[pos >> 5], 1u << (pos & 31));
-                    else if (op == EFF_UPS) sv[pos] = uval[u];
-                }
-            }
-        }
-        __syncwarp();
-        // pass 2: inserted keys take their merged position
-        uint32_t added_before = 0;
-        for (uint32_t c0 = j; c0 < k; c0 += 32) {
-            const uint32_t u = c0 + lane;
-            bool add = false;
-            K key = K(0);
-            uint32_t pos = 0;
-            if (u < k) {
-                key = ukey[u];
-                const uint32_t op = uop[u];
-                pos = smem_lower_bound(sk, sz, key);
-                const bool present = pos < sz && sk[pos] == key;
-                add = !present && (op == EFF_INS || op == EFF_UPS);
-            }
-            const uint32_t am = __ballot_sync(FULL, add);
-            if (add) {
-                uint32_t dels_below = 0;
-                for (uint32_t wd = 0; wd < (pos >> 5); wd++) dels_below += __popc(delmask[wd]);
-                if (pos & 31) dels_below += __popc(delmask[pos >> 5] & ((1u << (pos & 31)) - 1));
-                const uint32_t p = pos - dels_below + added_before + __popc(am & lt);
-                place(p, key, uval[u]);
-                atomicAdd(&addcnt[pos], 1u);
-            }
-            added_before += __popc(am);
-        }
-        __syncwarp();
-        // pass 3: surviving node keys shift by (inserted before) - (deleted before)
-        uint32_t carry = 0;
-        for (uint32_t c0 = 0; c0 < sz; c0 += 32) {
-            const uint32_t s = c0 + lane;
-            uint32_t a = s < sz ? addcnt[s] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(FULL, a, o);
-                if (lane >= o) a += y;
-            }
-            if (s < sz && !((delmask[s >> 5] >> (s & 31)) & 1u)) {
-                uint32_t dels_below = 0;
-                for (uint32_t wd = 0; wd < (s >> 5); wd++) dels_below += __popc(delmask[wd]);
-                if (s & 31) dels_below += __popc(delmask[s >> 5] & ((1u << (s & 31)) - 1));
-                place(s - dels_below + carry + a, sk[s], sv[s]);
-            }
-            carry += __shfl_sync(FULL, a, 31);
-        }
-        // chain metadata
-        if (t == 0) {
-            if (ag && first) {
-                // the whole chain empties: its first node stays as the bucket's only node
-                if (lane == 0) ix.size[node] = 0;
+    while (mask) {
+        const uint32_t i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint64_t b = b0 + i;
+        const uint32_t ue = __shfl_sync(FULL, g.ue, i);
+        uint32_t j = __shfl_sync(FULL, g.us, i);
+        uint32_t node = __shfl_sync(FULL, g.node, i);
+        uint32_t sz = __shfl_sync(FULL, g.sz, i);
+        uint32_t nx = __shfl_sync(FULL, g.nx, i);
+        K bd = __shfl_sync(FULL, g.bd, i);
+        uint32_t t = __shfl_sync(FULL, t0_l, i);
+        const uint64_t nfo = __shfl_sync(FULL, nfo_l, i);
+        const bool ag = __shfl_sync(FULL, ag_l, i) != 0;
+        const uint64_t need_base = nfo & 0xFFFFFFFFull;
+        const uint64_t free_base = nfo >> 32;
+        uint32_t prev_tail = NIL;
+        uint64_t acur = 0, fcur = 0;
+        bool first = true, last_dropped = false;
+        uint32_t steps = 0;
+        for (;;) {
+            K rk[MAXQ], rv[MAXQ];
+            lift_regs<K>(ix.keys + (uint64_t)node * NS, ix.vals + (uint64_t)node * NS, sz, lane, rk, rv);
+            const uint32_t k = routed_end(ukey, j, ue, bd);
+            if (k == j) {
                 prev_tail = node;
                 last_dropped = false;
             } else {
-                if (lane == 0) {
-                    if (prev_tail == NIL) ix.head[b] = nx; else ix.next[prev_tail] = nx;
-                    free_ids[push_base + free_base + fcur] = node;
+                const uint32_t q = pieces_of(t, NS);
+                stage_regs<K>(sk, sv, sz, lane, rk, rv);
+                for (uint32_t s = lane; s <= NS; s += 32) addcnt[s] = 0;
+                if (lane <= NS / 32) delmask[lane] = 0;
+                __syncwarp();
+                // output slot of merged position p: piece r (the node for r = 0, new nodes after)
+                auto place = [&](uint32_t p, K key, K val) {
+                    uint32_t r = 0;
+                    if (q > 1) { r = p / S2; if (r > q - 1) r = q - 1; }
+                    const uint32_t slot = p - r * S2;
+                    const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
+                    ix.keys[(uint64_t)dn * NS + slot] = key;
+                    ix.vals[(uint64_t)dn * NS + slot] = val;
+                    if (q > 1 && r < q - 1 && slot == S2 - 1) ix.bound[dn] = key;
+                };
+                // pass 1: deletions mark their slot (Tab. 4's mask); upserts of present keys replace values
+                for (uint32_t c0 = j; c0 < k; c0 += 32) {
+                    const uint32_t u = c0 + lane;
+                    if (u < k) {
+                        const K key = ukey[u];
+                        const uint32_t op = uop[u];
+                        const uint32_t pos = smem_lower_bound(sk, sz, key);
+                        if (pos < sz && sk[pos] == key) {
+                            if (op == EFF_DEL) atomicOr(&delmask[pos >> 5], 1u << (pos & 31));
+                            else if (op == EFF_UPS) sv[pos] = uval[u];
+                        }
+                    }
                 }
-                fcur++;
-                last_dropped = (nx == NIL);
+                __syncwarp();
+                // pass 2: inserted keys take their merged position
+                uint32_t added_before = 0;
+                for (uint32_t c0 = j; c0 < k; c0 += 32) {
+                    const uint32_t u = c0 + lane;
+                    bool add = false;
+                    K key = K(0);
+                    uint32_t pos = 0;
+                    if (u < k) {
+                        key = ukey[u];
+                        const uint32_t op = uop[u];
+                        pos = smem_lower_bound(sk, sz, key);
+                        const bool present = pos < sz && sk[pos] == key;
+                        add = !present && (op == EFF_INS || op == EFF_UPS);
+                    }
+                    const uint32_t am = __ballot_sync(FULL, add);
+                    if (add) {
+                        uint32_t dels_below = 0;
+                        for (uint32_t wd = 0; wd < (pos >> 5); wd++) dels_below += __popc(delmask[wd]);
+                        if (pos & 31) dels_below += __popc(delmask[pos >> 5] & ((1u << (pos & 31)) - 1));
+                        const uint32_t p = pos - dels_below + added_before + __popc(am & lt);
+                        place(p, key, uval[u]);
+                        atomicAdd(&addcnt[pos], 1u);
+                    }
+                    added_before += __popc(am);
+                }
+                __syncwarp();
+                // pass 3: surviving node keys shift by (inserted before) - (deleted before)
+                uint32_t carry = 0;
+                for (uint32_t c0 = 0; c0 < sz; c0 += 32) {
+                    const uint32_t s = c0 + lane;
+                    uint32_t a = s < sz ? addcnt[s] : 0;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        uint32_t y = __shfl_up_sync(FULL, a, o);
+                        if (lane >= o) a += y;
+                    }
+                    if (s < sz && !((delmask[s >> 5] >> (s & 31)) & 1u)) {
+                        uint32_t dels_below = 0;
+                        for (uint32_t wd = 0; wd < (s >> 5); wd++) dels_below += __popc(delmask[wd]);
+                        if (s & 31) dels_below += __popc(delmask[s >> 5] & ((1u << (s & 31)) - 1));
+                        place(s - dels_below + carry + a, sk[s], sv[s]);
+                    }
+                    carry += __shfl_sync(FULL, a, 31);
+                }
+                // chain metadata
+                if (t == 0) {
+                    if (ag && first) {
+                        // the whole chain empties: its first node stays as the bucket's only node
+                        if (lane == 0) ix.size[node] = 0;
+                        prev_tail = node;
+                        last_dropped = false;
+                    } else {
+                        if (lane == 0) {
+                            if (prev_tail == NIL) ix.head[b] = nx; else ix.next[prev_tail] = nx;
+                            free_ids[push_base + free_base + fcur] = node;
+                        }
+                        fcur++;
+                        last_dropped = (nx == NIL);
+                    }
+                } else {
+                    for (uint32_t r = lane; r < q; r += 32) {
+                        const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
+                        const uint32_t dnext = r + 1 < q ? alloc_ids[need_base + acur + r] : nx;
+                        ix.size[dn] = r + 1 < q ? S2 : t - (q - 1) * S2;
+                        ix.next[dn] = dnext;
+                        if (r + 1 == q) ix.bound[dn] = bd;
+                    }
+                    if (lane == 0) {
+                        if (prev_tail == NIL) ix.head[b] = node; else ix.next[prev_tail] = node;
+                    }
+                    prev_tail = q > 1 ? alloc_ids[need_base + acur + q - 2] : node;
+                    acur += q - 1;
+                    last_dropped = false;
+                }
+                j = k;
+                __syncwarp();
             }
-        } else {
-            for (uint32_t r = lane; r < q; r += 32) {
-                const uint32_t dn = r == 0 ? node : alloc_ids[need_base + acur + r - 1];
-                const uint32_t dnext = r + 1 < q ? alloc_ids[need_base + acur + r] : nx;
-                ix.size[dn] = r + 1 < q ? S2 : t - (q - 1) * S2;
-                ix.next[dn] = dnext;
-                if (r + 1 == q) ix.bound[dn] = bd;
+            first = false;
+            if (j >= ue) break;
+            node = nx;
+            if (node == NIL || ++steps > ix.cap) {
+                if (lane == 0) atomicOr(ix.err, ERR_CHAIN);
+                return;
             }
-            if (lane == 0) {
-                if (prev_tail == NIL) ix.head[b] = node; else ix.next[prev_tail] = node;
-            }
-            prev_tail = q > 1 ? alloc_ids[need_base + acur + q - 2] : node;
-            acur += q - 1;
-            last_dropped = false;
+            sz = ix.size[node];
+            bd = ix.bound[node];
+            nx = ix.next[node];
+            t = tnode[node];
         }
-        first = false;
-        j = k;
-        node = nx;
-        __syncwarp();
+        if (last_dropped && lane == 0 && prev_tail != NIL) ix.bound[prev_tail] = ix.mkba[b];
     }
-    if (last_dropped && lane == 0 && prev_tail != NIL) ix.bound[prev_tail] = ix.mkba[b];
 }
 
 __global__ void k_alloc_copy(const uint32_t* __restrict__ free_ids, uint64_t from, uint64_t count,
@@ -479,7 +582,7 @@ template <class K>
 cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff, uint64_t* nf,
                          uint8_t* allgone)
 {
-    const uint32_t grid = div_up(c.h->nb, UP_WARPS);
+    const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
     return launch(c, K_UPD_COUNT, dim3(grid), dim3(UP_THREADS), count_smem<K>(c.h->NS), k_update_count<K>,
                   dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone);
 }
@@ -489,7 +592,7 @@ cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uv
                          const uint64_t* nf_off, const uint8_t* allgone, const uint32_t* alloc_ids,
                          uint64_t push_base)
 {
-    const uint32_t grid = div_up(c.h->nb, UP_WARPS);
+    const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
     return launch(c, K_UPD_APPLY, dim3(grid), dim3(UP_THREADS), apply_smem<K>(c.h->NS), k_update_apply<K>,
                   dev_view<K>(c.h), ukey, uop, uval, uoff, (const uint32_t*)c.h->tnode, nf_off, allgone, alloc_ids,
                   c.h->free_ids, push_base);

@@ -24,10 +24,11 @@ def fx():
     return fx
 
 
-def test_config1_mixed_batch(fx):
+@pytest.mark.parametrize("sort_variant", [1, 2])
+def test_config1_mixed_batch(fx, sort_variant):
     c = W.config1(seed=0)
     kw = c["kw"]
-    idx = fx.Index(key_bits=kw, node_size=32)
+    idx = fx.Index(key_bits=kw, node_size=32, sort_variant=sort_variant)
     idx.bulk_load(c["load_keys"], c["load_vals"])
     mp, md = oracle_pair(kw, 32, 50, c["load_keys"], c["load_vals"])
     compare_layout(idx, md)
