@@ -9,7 +9,7 @@ bucket/node layout, see its header); this module builds it with gcc and wraps it
 arrays cross the boundary as uint64 whatever the key width.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` against the paper's worked
-examples (Tab. 3, Tab. 4, the build example of Sec. 3.2), brute force on tiny key domains, linear
+examples (Tab. 2, Tab. 3, the build example of Sec. 3.2), brute force on tiny key domains, linear
 scans and structural invariants.
 """
 from __future__ import annotations
@@ -217,7 +217,7 @@ class Model:
 
 
 def delete_compact(keys, dels):
-    """Tab. 4 step: returns (compacted keys, shift distance per slot, -1 for deleted slots)."""
+    """Tab. 3 step: returns (compacted keys, shift distance per slot, -1 for deleted slots)."""
     k, d = _u64(keys), _u64(dels)
     out = np.zeros(max(k.size, 1), np.uint64)
     sh = np.zeros(max(k.size, 1), np.int32)
@@ -226,7 +226,7 @@ def delete_compact(keys, dels):
 
 
 def merge_insert(keys, ins):
-    """Tab. 3 step: the node's keys merged with the insert sublist (present keys not repeated)."""
+    """Tab. 2 step: the node's keys merged with the insert sublist (present keys not repeated)."""
     k, i = _u64(keys), _u64(ins)
     out = np.zeros(k.size + i.size + 1, np.uint64)
     n = lib().om_merge_insert(_p(k), k.size, _p(i), i.size, _p(out))

@@ -22,8 +22,8 @@
  *     p = fill * NS; each bucket pulls its sublist from the sorted update list by a binary search for
  *     maxBucket_{i-1} (Sec. 3.3, Sec. 4.1); an update goes to the first node of the chain whose
  *     maxKey >= k (Sec. 4.1); deletes compact the node by shifting survivors left by the number of
- *     earlier deletions (Sec. 4.4, Tab. 4); inserts merge the sublist into the node in key order
- *     (Sec. 4.3.2, Tab. 3); a node that overflows is split into halves (Sec. 3.2, Sec. 5.3.1);
+ *     earlier deletions (Sec. 4.4, Tab. 3); inserts merge the sublist into the node in key order
+ *     (Sec. 4.3.2, Tab. 2); a node that overflows is split into halves (Sec. 3.2, Sec. 5.3.1);
  *     emptied nodes leave the chain and are reused (Sec. 4.4); restructuring flattens every chain
  *     into half-full single-node buckets and resets the MKBA (Sec. 3.5, Sec. 6.6).
  *
@@ -31,7 +31,7 @@
  *     canonical layout: a merged run of t keys stays one node if t <= NS; otherwise it becomes
  *     q = floor(t / s) nodes (s = NS/2, the even half of Sec. 5.3.1): q-1 nodes of s keys and a last
  *     node of the remaining t-(q-1)s keys.  Every piece but the last takes its own largest key as
- *     maxKey; the last keeps the old node's maxKey.  This reproduces Tab. 3.  An emptied node is
+ *     maxKey; the last keeps the old node's maxKey.  This reproduces Tab. 2.  An emptied node is
  *     unlinked unless the whole chain emptied, in which case the chain's first node stays as an empty
  *     node; when the chain's last node leaves, its maxKey (= maxBucket) passes to the new last node.
  *
@@ -282,7 +282,7 @@ int om_map_update(om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys,
  * 2. Structural model
  * ---------------------------------------------------------------------------------------------- */
 
-/* Sec. 4.4 / Tab. 4: each node key is compared with the delete keys and marked; a survivor moves
+/* Sec. 4.4 / Tab. 3: each node key is compared with the delete keys and marked; a survivor moves
  * left by the number of deletions among the slots before it.  shift[i] = -1 for a deleted slot.
  * Returns the new size. */
 uint32_t om_delete_compact(const uint64_t* keys, uint32_t n, const uint64_t* dk, uint32_t m,
@@ -304,7 +304,7 @@ uint32_t om_delete_compact(const uint64_t* keys, uint32_t n, const uint64_t* dk,
     return n - del_count;
 }
 
-/* Sec. 4.3.2 / Tab. 3: the sorted insert sublist is merged into the node's sorted keys; a key
+/* Sec. 4.3.2 / Tab. 2: the sorted insert sublist is merged into the node's sorted keys; a key
  * already present is not inserted again.  Returns the merged size. */
 uint32_t om_merge_insert(const uint64_t* keys, uint32_t n, const uint64_t* ins, uint32_t m, uint64_t* out)
 {

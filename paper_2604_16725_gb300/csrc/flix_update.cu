@@ -6,7 +6,7 @@
 // in parallel, then the warp works through the buckets that have updates, walking each chain
 // (Sec. 4.1: an update goes to the first node with key <= maxKey).  For each node that receives updates the warp lifts the node's keys and values
 // into shared memory (the paper lifts them into the tile's registers, Sec. 4.3.2), marks the
-// deleted slots (Tab. 4's mask), and computes every surviving or inserted key's position in the
+// deleted slots (Tab. 3's mask), and computes every surviving or inserted key's position in the
 // merged run: a node key's position is its slot minus the deletions before it plus the inserted
 // keys before it; an inserted key's position is the count of surviving node keys below it plus the
 // inserted keys before it.  The merged run of t keys is laid out canonically: one node if
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
                     ix.vals[(uint64_t)dn * NS + slot] = val;
                     if (q > 1 && r < q - 1 && slot == S2 - 1) ix.bound[dn] = key;
                 };
-                // pass 1: deletions mark their slot (Tab. 4's mask); upserts of present keys replace values
+                // pass 1: deletions mark their slot (Tab. 3's mask); upserts of present keys replace values
                 for (uint32_t c0 = j; c0 < k; c0 += 32) {
                     const uint32_t u = c0 + lane;
                     if (u < k) {

@@ -1,7 +1,7 @@
 """Pins of the CPU oracle against what the paper fixes: its worked examples and closed forms.
 
-* Tab. 3 (Sec. 4.3.2): TL-Bulk insertion, merged node and the split into halves.
-* Tab. 4 (Sec. 4.4): TL-Bulk deletion, the deletion mask, the shift-left distances and the result.
+* Tab. 2 (Sec. 4.3.2): TL-Bulk insertion, merged node and the split into halves.
+* Tab. 3 (Sec. 4.4): TL-Bulk deletion, the deletion mask, the shift-left distances and the result.
 * Sec. 3.2: the initial build cuts the sorted keys into groups of p = nodesize/2; every p-th key is
   the bucket's maxBucket.
 * The canonical split rule's closed form (t <= NS: one node; else floor(t/s) pieces).
@@ -17,18 +17,18 @@ def ints(s):
     return [int(x) for x in s.split()]
 
 
-def test_tab3_merge_insert_row():
-    g = read_golden("tab3_tl_bulk_insert.txt")
+def test_tab2_merge_insert_row():
+    g = read_golden("tab2_tl_bulk_insert.txt")
     node, sub = ints(g["node"]), ints(g["sublist"])
-    # step 3 of Tab. 3: 15, 17 and 39 are merged; 65 waits for the split
+    # step 3 of Tab. 2: 15, 17 and 39 are merged; 65 waits for the split
     merged = oracle.merge_insert(node, sub[:3])
     assert merged.tolist() == ints(g["step3"])
     # a key already present is not inserted a second time
     assert oracle.merge_insert(node, [25, 30]).tolist() == node
 
 
-def test_tab3_split_through_model():
-    g = read_golden("tab3_tl_bulk_insert.txt")
+def test_tab2_split_through_model():
+    g = read_golden("tab2_tl_bulk_insert.txt")
     NS = int(g["node_size"])
     m = oracle.Model(32, NS, fill_pct=100)        # p = NS: the five keys form one node
     node = ints(g["node"])
@@ -46,8 +46,8 @@ def test_tab3_split_through_model():
     assert m.check() == 0
 
 
-def test_tab4_delete_compaction():
-    g = read_golden("tab4_tl_bulk_delete.txt")
+def test_tab3_delete_compaction():
+    g = read_golden("tab3_tl_bulk_delete.txt")
     node, dels = ints(g["node"]), ints(g["delete"])
     out, shift = oracle.delete_compact(node, dels)
     assert out.tolist() == ints(g["final"])
@@ -55,8 +55,8 @@ def test_tab4_delete_compaction():
     assert [1 if s < 0 else 0 for s in shift.tolist()] == ints(g["mask"])
 
 
-def test_tab4_through_model():
-    g = read_golden("tab4_tl_bulk_delete.txt")
+def test_tab3_through_model():
+    g = read_golden("tab3_tl_bulk_delete.txt")
     NS = int(g["node_size"])
     m = oracle.Model(64, NS, fill_pct=100)
     node = ints(g["node"])
