@@ -59,6 +59,22 @@ def make_inputs(seed, log_load=LOG_LOAD, log_q=LOG_Q, log_r=LOG_R, log_u=LOG_U):
     return c
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The slowest rank's time (replicas run independently; the job ends with the last one)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mops(ops_per_rank_step: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank's ops over the slowest rank's step time."""
+    return ops_per_rank_step * world / (ms_per_step * 1e-3) / 1e6
+
+
 def ops_per_step(log_q=LOG_Q, log_r=LOG_R, log_u=LOG_U):
     return dict(lookup=1 << log_q, successor=1 << log_q, range=1 << log_r, insert=1 << log_u, delete=1 << log_u)
 
@@ -323,15 +339,11 @@ def main():
     clocks = clk.summary(wall0 - 0.25, wall1 + 0.25)
     total_ms = t_start.elapsed_time(t_end)
     launches = idx.launch_count() - launches0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ops = ops_per_step(log_q=LOG_Q)
     n_ops = sum(ops.values())
     ms_step = total_ms / args.steps
-    value = n_ops * world / (ms_step * 1e-3) / 1e6
+    value = whole_job_mops(n_ops, world, ms_step)
 
     # per-kernel durations: a second pass of the same steps with per-launch CUDA events
     idx.profile(True)
@@ -402,11 +414,7 @@ def main():
             run_step_e2e(torch, idx, host, stream)
         barrier()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_ms], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, world)
         h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv")) + \
             host["ik"].numel() * 8
         d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
