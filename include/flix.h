@@ -166,6 +166,26 @@ int flix_apply(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d
                void* d_range_keys, void* d_range_vals, uint64_t range_cap, uint64_t* h_range_total,
                void* stream);
 
+/* flix_apply without any host synchronisation, for streams of batches and CUDA-graph capture (the
+ * paper runs one batch per launch; this form keeps the whole batch on the device).  Same batch
+ * semantics and outputs as flix_apply.  Admission is decided on the device: if an insert carries
+ * KEY_MAX, the free nodes do not cover the batch's node demand, or the range pairs exceed range_cap,
+ * the batch's updates and range pairs are not written (lookup and successor results still are).
+ * d_status: caller-owned DEVICE uint64[4] written by the call: flags (1 reserved key, 2 node pool
+ * short, 4 range capacity short), range pair total, nodes the batch needed, free nodes before it.
+ * The handle's scratch must already hold a batch of n ops (flix_reserve); otherwise FLIX_ENOMEM is
+ * returned before anything is launched.  The call never grows the pool.  Kernel parameters
+ * capture the current bucket count and pool, so a captured graph must be re-captured after
+ * flix_bulk_load, flix_restructure or pool growth. */
+int flix_apply_async(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d_aux, uint64_t n,
+                     void* d_keys_out, void* d_vals_out, uint8_t* d_found, uint64_t* d_range_off,
+                     void* d_range_keys, void* d_range_vals, uint64_t range_cap, uint64_t* d_status,
+                     void* stream);
+
+/* Reserve scratch for batches of up to batch_max ops and grow the pool (if needed) so that at least
+ * free_nodes_min nodes are free.  Synchronises.  FLIX_ENOMEM if the device cannot hold it. */
+int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* stream);
+
 /* Restructure (Sec. 3.5): flatten every chain, re-cut the live pairs into single-node buckets at
  * the build fill, reset the MKBA and the free list.  Synchronises. */
 int flix_restructure(flix_t h, void* stream);

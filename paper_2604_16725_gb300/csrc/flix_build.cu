@@ -143,8 +143,7 @@ cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t n
     e = launch(c, K_CUT_META, dim3(div_up(work, BT)), dim3(BT), 0, k_cut_meta<K>, ix, sk, n, h->p, nb_new, h->cap,
                h->free_ids);
     if (e) return e;
-    h->free_top = h->cap - nb_new;
-    return cudaSuccess;
+    return set_free_top(c, h->cap - nb_new);
 }
 
 template <class K>

@@ -15,7 +15,7 @@ const char* kKernelNames[K_NUM] = {
     "scan_partials", "scan_top", "scan_apply",
     "partition", "read_point", "range_count", "range_fill",
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
-    "update_count", "alloc_copy", "update_apply",
+    "update_count", "alloc_copy", "update_apply", "admit",
     "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill",
 };
 
@@ -287,28 +287,44 @@ int do_range(flix_index* h, const K* lo, const K* hi, uint64_t n, uint64_t* roff
     const uint64_t total = h->hpin[0];
     if (h_total) *h_total = total;
     if (total > rcap) return FLIX_ENOMEM;
-    if (total) CK(range_fill<K>(c, si, n, nullptr, sb, sn, sp, roff, rk, rv));
+    if (total) CK(range_fill<K>(c, si, n, nullptr, sb, sn, sp, roff, rk, rv, false));
     return FLIX_OK;
 }
 
+// Scratch bytes of one batch of n ops on nb buckets.
+template <class K>
+size_t batch_scratch_bytes(uint64_t n, uint64_t nb)
+{
+    return sort_scratch_bytes<K>(n) + al(n * sizeof(K)) * 3 + al(n * 4) * 16 + al(n * 8) * 2 + al((nb + 1) * 4) * 2 +
+           al((nb + 1) * 8) * 2 + al(nb + 1) + scan_scratch_bytes<uint64_t>(n) * 4 +
+           scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + (1 << 16);
+}
+
 // Reads of a mixed batch (snapshot), then its updates.  hom_op != 0: homogeneous insert/delete.
+// sync: read back the node demand and range total, decide admission (and pool growth) on the host
+// and report errors as return codes.  !sync: no host round trip; the admit kernel decides on the
+// device and writes d_status (flags, range total, need, free nodes before the batch).
 template <class K>
 int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const K* aux, uint64_t n, K* keys_out,
              K* vals_out, uint8_t* found, uint64_t* roff_user, K* rk, K* rv, uint64_t rcap, uint64_t* h_rtotal,
-             cudaStream_t st)
+             uint64_t* d_status, bool sync, cudaStream_t st)
 {
     if (h_rtotal) *h_rtotal = 0;
     if (n == 0) {
         if (roff_user) CK(cudaMemsetAsync(roff_user, 0, 8, st));
+        if (d_status) CK(cudaMemsetAsync(d_status, 0, 4 * sizeof(uint64_t), st));
         return FLIX_OK;
     }
     Ctx c{h, st};
     const uint64_t nb = h->nb;
     const bool mixed = hom_op == 0;
-    size_t need_bytes = sort_scratch_bytes<K>(n) + al(n * sizeof(K)) * 3 + al(n * 4) * 16 + al(n * 8) * 2 +
-                        al((nb + 1) * 4) * 2 + al((nb + 1) * 8) * 2 + al(nb + 1) + scan_scratch_bytes<uint64_t>(n) * 4 +
-                        scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + (1 << 16);
-    CK(h->arena.ensure(need_bytes));
+    const size_t need_bytes = batch_scratch_bytes<K>(n, nb);
+    if (sync) {
+        CK(h->arena.ensure(need_bytes));
+    } else if (h->arena.cap < need_bytes) {
+        h->last_error = "scratch not reserved for a batch of " + std::to_string(n) + " ops (call flix_reserve)";
+        return FLIX_ENOMEM;
+    }
     h->arena.reset();
     Arena& A = h->arena;
     uint32_t* status = A.take<uint32_t>(16);
@@ -340,31 +356,60 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     uint64_t* nf = A.take<uint64_t>(nb + 1);
     uint64_t* nf_off = A.take<uint64_t>(nb + 1);
     uint8_t* allgone = A.take<uint8_t>(nb + 1);
-    uint32_t* alloc_ids = A.take<uint32_t>(2 * n + 16);
+    const uint64_t alloc_cap = 2 * n + 16;   // a batch of U distinct updates allocates at most 2U nodes
+    uint32_t* alloc_ids = A.take<uint32_t>(alloc_cap);
     if (!ukey || !uop || !uval || !uoff || !nf || !nf_off || !allgone || !alloc_ids) return FLIX_ENOMEM;
     CK(fold_updates<K>(c, sk, si, n, ops, hom_op, aux, ukey, uop, uval, udev));
     CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff));
     CK(update_count<K>(c, ukey, uop, uoff, nf, allgone));
     CK(scan_exclusive<uint64_t, uint64_t>(c, nf, nf_off, nb));
-    int r = readback(h, st, {{status, 4}, {nf_off + nb, 8}, {roff ? (const void*)(roff + n) : (const void*)status, 8}});
-    if (r) return r;
-    const uint32_t flag = (uint32_t)(h->hpin[0] & 0xFFFFFFFFu);
-    const uint64_t need = h->hpin[1] & 0xFFFFFFFFull, freed = h->hpin[1] >> 32;
-    const uint64_t rtotal = (mixed && roff) ? h->hpin[2] : 0;
-    if (flag & ERR_BADKEY) return FLIX_EINVAL;
-    if (h_rtotal) *h_rtotal = rtotal;
-    if (mixed && rtotal > rcap) return FLIX_ENOMEM;
-    if (need > h->free_top) {
-        if (!h->cfg.grow) return FLIX_ENOMEM;
-        uint64_t nc = std::max<uint64_t>(h->cap * 2, h->cap + (need - h->free_top) + 1024);
-        int g = pool_grow(h, st, nc);
-        if (g) return g;
+    const uint64_t* nf_total = nf_off + nb;
+    const uint64_t* rtot_dev = (mixed && roff) ? roff + n : nullptr;
+    uint64_t need = 0, freed = 0, rtotal = 0;
+    if (sync) {
+        int r = readback(h, st, {{status, 4}, {nf_total, 8}, {rtot_dev ? (const void*)rtot_dev : (const void*)status, 8},
+                                 {&h->dstate->free_top, 8}});
+        if (r) return r;
+        const uint32_t flag = (uint32_t)(h->hpin[0] & 0xFFFFFFFFu);
+        need = h->hpin[1] & 0xFFFFFFFFull;
+        freed = h->hpin[1] >> 32;
+        rtotal = rtot_dev ? h->hpin[2] : 0;
+        h->free_top = h->hpin[3];
+        if (flag & ERR_BADKEY) return FLIX_EINVAL;
+        if (h_rtotal) *h_rtotal = rtotal;
+        if (mixed && rtotal > rcap) return FLIX_ENOMEM;
+        if (need > h->free_top) {
+            if (!h->cfg.grow) return FLIX_ENOMEM;
+            uint64_t nc = std::max<uint64_t>(h->cap * 2, h->cap + (need - h->free_top) + 1024);
+            int g = pool_grow(h, st, nc);
+            if (g) return g;
+            CK(set_free_top(c, h->free_top));
+        }
     }
-    if (mixed && rtotal) CK(range_fill<K>(c, si, n, ops, sb, sn, sp, roff, rk, rv));
-    const uint64_t from = h->free_top - need;
-    if (need) CK(alloc_copy(c, h->free_ids, from, need, alloc_ids));
-    CK(update_apply<K>(c, ukey, uop, uval, uoff, nf_off, allgone, alloc_ids, from));
-    h->free_top = from + freed;
+    CK(admit(c, nf_total, status, rtot_dev, mixed ? rcap : 0, d_status));
+    if (mixed && (!sync || rtotal)) CK(range_fill<K>(c, si, n, ops, sb, sn, sp, roff, rk, rv, true));
+    CK(alloc_copy(c, h->free_ids, alloc_ids, alloc_cap));
+    CK(update_apply<K>(c, ukey, uop, uval, uoff, nf_off, allgone, alloc_ids));
+    CK(commit(c));
+    if (sync) h->free_top = h->free_top - need + freed;
+    return FLIX_OK;
+}
+
+// Scratch for batches up to batch_max ops and at least free_nodes_min free nodes (synchronises).
+template <class K>
+int do_reserve(flix_index* h, uint64_t batch_max, uint64_t free_nodes_min, cudaStream_t st)
+{
+    Ctx c{h, st};
+    CK(h->arena.ensure(batch_scratch_bytes<K>(batch_max, std::max<uint64_t>(h->cap, h->nb))));
+    int r = readback(h, st, {{&h->dstate->free_top, 8}});
+    if (r) return r;
+    h->free_top = h->hpin[0];
+    if (h->free_top < free_nodes_min) {
+        int g = pool_grow(h, st, h->cap + (free_nodes_min - h->free_top) + 1024);
+        if (g) return g;
+        CK(set_free_top(c, h->free_top));
+    }
+    CK(cudaStreamSynchronize(st));
     return FLIX_OK;
 }
 
@@ -432,13 +477,14 @@ int do_stats(flix_index* h, flix_stats_t* o, cudaStream_t st)
     h->arena.reset();
     uint64_t* s3 = h->arena.take<uint64_t>(4);
     CK(stats_kernel<K>(c, s3));
-    int r = readback(h, st, {{s3, 8}, {s3 + 1, 8}, {s3 + 2, 8}});
+    int r = readback(h, st, {{s3, 8}, {s3 + 1, 8}, {s3 + 2, 8}, {&h->dstate->free_top, 8}});
     if (r) return r;
     memset(o, 0, sizeof(*o));
     o->buckets = h->nb;
     o->max_chain = h->hpin[0];
     o->live_keys = h->hpin[1];
     o->nodes_used = h->hpin[2];
+    h->free_top = h->hpin[3];
     o->nodes_free = h->free_top;
     o->pool_nodes = h->cap;
     o->node_bytes = 2ull * h->NS * sizeof(K) + sizeof(K) + 8;
@@ -535,6 +581,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     cudaGetDevice(&h->device);
     cudaError_t e;
     if ((e = cudaMalloc(&h->err, 64)) || (e = cudaMemset(h->err, 0, 64)) ||
+        (e = cudaMalloc(&h->dstate, sizeof(DevState))) || (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
         (e = cudaMallocHost(&h->hpin, 64 * sizeof(uint64_t)))) {
         int r = fail(h, e);
         flix_destroy(h);
@@ -558,6 +605,7 @@ int flix_destroy(flix_t h)
     pool_free(h);
     h->arena.release();
     if (h->err) cudaFree(h->err);
+    if (h->dstate) cudaFree(h->dstate);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -606,18 +654,20 @@ int flix_insert(flix_t h, const void* d_keys, const void* d_vals, uint64_t n, vo
 {
     if (!h || (n && (!d_keys || !d_vals)) || too_big(n)) return FLIX_EINVAL;
     return DISPATCH(do_batch<uint32_t>(h, nullptr, FLIX_OP_INSERT, (const uint32_t*)d_keys, (const uint32_t*)d_vals, n,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, S(stream)),
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, true,
+                                       S(stream)),
                     do_batch<uint64_t>(h, nullptr, FLIX_OP_INSERT, (const uint64_t*)d_keys, (const uint64_t*)d_vals, n,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, S(stream)));
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, true,
+                                       S(stream)));
 }
 
 int flix_delete(flix_t h, const void* d_keys, uint64_t n, void* stream)
 {
     if (!h || (n && !d_keys) || too_big(n)) return FLIX_EINVAL;
     return DISPATCH(do_batch<uint32_t>(h, nullptr, FLIX_OP_DELETE, (const uint32_t*)d_keys, nullptr, n, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, S(stream)),
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, true, S(stream)),
                     do_batch<uint64_t>(h, nullptr, FLIX_OP_DELETE, (const uint64_t*)d_keys, nullptr, n, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, S(stream)));
+                                       nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, true, S(stream)));
 }
 
 int flix_apply(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d_aux, uint64_t n, void* d_keys_out,
@@ -629,10 +679,32 @@ int flix_apply(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d
     return DISPATCH(
         do_batch<uint32_t>(h, d_ops, 0, (const uint32_t*)d_keys, (const uint32_t*)d_aux, n, (uint32_t*)d_keys_out,
                            (uint32_t*)d_vals_out, d_found, d_range_off, (uint32_t*)d_range_keys,
-                           (uint32_t*)d_range_vals, range_cap, h_range_total, S(stream)),
+                           (uint32_t*)d_range_vals, range_cap, h_range_total, nullptr, true, S(stream)),
         do_batch<uint64_t>(h, d_ops, 0, (const uint64_t*)d_keys, (const uint64_t*)d_aux, n, (uint64_t*)d_keys_out,
                            (uint64_t*)d_vals_out, d_found, d_range_off, (uint64_t*)d_range_keys,
-                           (uint64_t*)d_range_vals, range_cap, h_range_total, S(stream)));
+                           (uint64_t*)d_range_vals, range_cap, h_range_total, nullptr, true, S(stream)));
+}
+
+int flix_apply_async(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d_aux, uint64_t n,
+                     void* d_keys_out, void* d_vals_out, uint8_t* d_found, uint64_t* d_range_off, void* d_range_keys,
+                     void* d_range_vals, uint64_t range_cap, uint64_t* d_status, void* stream)
+{
+    if (!h || !d_status || (n && (!d_ops || !d_keys || !d_aux)) || too_big(n)) return FLIX_EINVAL;
+    if (range_cap && (!d_range_keys || !d_range_vals)) return FLIX_EINVAL;
+    return DISPATCH(
+        do_batch<uint32_t>(h, d_ops, 0, (const uint32_t*)d_keys, (const uint32_t*)d_aux, n, (uint32_t*)d_keys_out,
+                           (uint32_t*)d_vals_out, d_found, d_range_off, (uint32_t*)d_range_keys,
+                           (uint32_t*)d_range_vals, range_cap, nullptr, d_status, false, S(stream)),
+        do_batch<uint64_t>(h, d_ops, 0, (const uint64_t*)d_keys, (const uint64_t*)d_aux, n, (uint64_t*)d_keys_out,
+                           (uint64_t*)d_vals_out, d_found, d_range_off, (uint64_t*)d_range_keys,
+                           (uint64_t*)d_range_vals, range_cap, nullptr, d_status, false, S(stream)));
+}
+
+int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* stream)
+{
+    if (!h || too_big(batch_max)) return FLIX_EINVAL;
+    return DISPATCH(do_reserve<uint32_t>(h, batch_max, free_nodes_min, S(stream)),
+                    do_reserve<uint64_t>(h, batch_max, free_nodes_min, S(stream)));
 }
 
 int flix_restructure(flix_t h, void* stream)

@@ -48,7 +48,7 @@ enum KernelId {
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
     K_PARTITION, K_READ_POINT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
-    K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY,
+    K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY, K_ADMIT,
     K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL,
     K_NUM
 };
@@ -77,6 +77,22 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+// Device-resident allocator and admission state of a handle.  free_top is authoritative on the
+// device so that update batches can be admitted without a host round trip: the admit kernel compares
+// the batch's node demand with free_top, and the alloc, apply and commit kernels act only if it
+// admitted the batch.
+struct DevState {
+    unsigned long long free_top;   // number of ids on the free stack
+    unsigned long long admitted;   // 1 while an admitted batch is being applied
+    unsigned long long from;       // first popped stack slot (= free_top - need)
+    unsigned long long next_top;   // free_top after the batch (from + freed)
+    unsigned long long need;       // nodes the batch allocates
+    unsigned long long freed;      // nodes the batch frees
+};
+
+// Status bits an asynchronous batch reports (flix_apply_async).
+enum : uint64_t { ST_BADKEY = 1, ST_NODES = 2, ST_RANGE = 4 };
+
 }  // namespace flix
 
 struct flix_index {
@@ -101,6 +117,7 @@ struct flix_index {
     uint32_t* head = nullptr;
     uint32_t* free_ids = nullptr;  // free stack: ids [0, free_top) are free nodes
     uint32_t* err = nullptr;       // device error word
+    flix::DevState* dstate = nullptr;
 
     flix::Arena arena;
     uint64_t* hpin = nullptr;      // small pinned host buffer for read-backs (64 words)
@@ -203,10 +220,11 @@ cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m
                         const uint8_t* ops, const K* hi, uint32_t* start_bucket, uint32_t* start_node,
                         uint32_t* start_pos, uint64_t* cnt);
 
+// gated: write only if the device admission state admitted the batch
 template <class K>
 cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* ops,
                        const uint32_t* start_bucket, const uint32_t* start_node, const uint32_t* start_pos,
-                       const uint64_t* off, K* rkeys, K* rvals);
+                       const uint64_t* off, K* rkeys, K* rvals, bool gated);
 
 // ---- update path (flix_update.cu) ------------------------------------------------------------
 
@@ -226,9 +244,18 @@ cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint3
 template <class K>
 cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval,
                          const uint32_t* uoff, const uint64_t* nf_off, const uint8_t* allgone,
-                         const uint32_t* alloc_ids, uint64_t push_base);
+                         const uint32_t* alloc_ids);
 
-cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint64_t from, uint64_t count, uint32_t* out);
+// Device admission of an update batch: node demand nf_total (need | freed << 32) against free_top,
+// the reserved-key flag, and the range total against range_cap.  status (optional, 4 words):
+// flags (ST_*), range total, need, free_top before the batch.
+cudaError_t admit(Ctx& c, const uint64_t* nf_total, const uint32_t* badkey, const uint64_t* range_total,
+                  uint64_t range_cap, uint64_t* status);
+cudaError_t commit(Ctx& c);
+cudaError_t set_free_top(Ctx& c, uint64_t value);
+
+// Copy the admitted batch's popped node ids (at most cap_out) out of the free stack.
+cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint32_t* out, uint64_t cap_out);
 
 // ---- build / restructure / export (flix_build.cu) --------------------------------------------
 

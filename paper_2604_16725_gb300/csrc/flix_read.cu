@@ -300,8 +300,9 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
                                                            const uint32_t* __restrict__ start_node,
                                                            const uint32_t* __restrict__ start_pos,
                                                            const uint64_t* __restrict__ roff, K* __restrict__ rkeys,
-                                                           K* __restrict__ rvals)
+                                                           K* __restrict__ rvals, const DevState* __restrict__ ds)
 {
+    if (ds && !ds->admitted) return;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t j = ((uint64_t)blockIdx.x * RP_THREADS + threadIdx.x) >> 5;
     if (j >= m) return;
@@ -371,12 +372,14 @@ cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m
 
 template <class K>
 cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* ops, const uint32_t* start_bucket,
-                       const uint32_t* start_node, const uint32_t* start_pos, const uint64_t* roff, K* rkeys, K* rvals)
+                       const uint32_t* start_node, const uint32_t* start_pos, const uint64_t* roff, K* rkeys, K* rvals,
+                       bool gated)
 {
     if (m == 0) return cudaSuccess;
     const uint32_t grid = div_up(m * 32, RP_THREADS);
     return launch(c, K_RANGE_FILL, dim3(grid), dim3(RP_THREADS), 0, k_range_fill<K>, dev_view<K>(c.h), sidx, m, ops,
-                  start_bucket, start_node, start_pos, roff, rkeys, rvals);
+                  start_bucket, start_node, start_pos, roff, rkeys, rvals,
+                  gated ? (const DevState*)c.h->dstate : (const DevState*)nullptr);
 }
 
 #define FLIX_READ_INST(K)                                                                                  \
@@ -386,7 +389,7 @@ cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* 
     template cudaError_t range_count<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint32_t*,           \
                                         const uint8_t*, const K*, uint32_t*, uint32_t*, uint32_t*, uint64_t*); \
     template cudaError_t range_fill<K>(Ctx&, const uint32_t*, uint64_t, const uint8_t*, const uint32_t*,       \
-                                       const uint32_t*, const uint32_t*, const uint64_t*, K*, K*);
+                                       const uint32_t*, const uint32_t*, const uint64_t*, K*, K*, bool);
 
 FLIX_READ_INST(uint32_t)
 FLIX_READ_INST(uint64_t)

@@ -335,8 +335,11 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
                                                              const uint64_t* __restrict__ nf_off,
                                                              const uint8_t* __restrict__ allgone,
                                                              const uint32_t* __restrict__ alloc_ids,
-                                                             uint32_t* __restrict__ free_ids, uint64_t push_base)
+                                                             uint32_t* __restrict__ free_ids,
+                                                             const DevState* __restrict__ ds)
 {
+    if (!ds->admitted) return;
+    const uint64_t push_base = ds->from;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t NS = ix.NS, S2 = NS >> 1;
@@ -509,11 +512,50 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
     }
 }
 
-__global__ void k_alloc_copy(const uint32_t* __restrict__ free_ids, uint64_t from, uint64_t count,
-                             uint32_t* __restrict__ out)
+__global__ void k_alloc_copy(const uint32_t* __restrict__ free_ids, const DevState* __restrict__ ds,
+                             uint32_t* __restrict__ out, uint64_t cap_out)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) out[i] = free_ids[from + i];
+    if (!ds->admitted || i >= ds->need || i >= cap_out) return;
+    out[i] = free_ids[ds->from + i];
+}
+
+__global__ void k_admit(DevState* __restrict__ ds, const uint64_t* __restrict__ nf_total,
+                        const uint32_t* __restrict__ badkey, const uint64_t* __restrict__ range_total,
+                        uint64_t range_cap, uint64_t* __restrict__ status)
+{
+    const uint64_t v = *nf_total;
+    const uint64_t need = v & 0xFFFFFFFFull, freed = v >> 32;
+    const uint64_t top = ds->free_top;
+    const uint64_t rt = range_total ? *range_total : 0;
+    uint64_t flags = 0;
+    if (*badkey & ERR_BADKEY) flags |= ST_BADKEY;
+    if (need > top) flags |= ST_NODES;
+    if (rt > range_cap) flags |= ST_RANGE;
+    const bool ok = flags == 0;
+    ds->admitted = ok;
+    ds->need = need;
+    ds->freed = freed;
+    ds->from = ok ? top - need : top;
+    ds->next_top = ok ? top - need + freed : top;
+    if (status) {
+        status[0] = flags;
+        status[1] = rt;
+        status[2] = need;
+        status[3] = top;
+    }
+}
+
+__global__ void k_commit(DevState* __restrict__ ds)
+{
+    if (ds->admitted) ds->free_top = ds->next_top;
+    ds->admitted = 0;
+}
+
+__global__ void k_set_free_top(DevState* __restrict__ ds, uint64_t value)
+{
+    ds->free_top = value;
+    ds->admitted = 0;
 }
 
 template <class K>
@@ -589,18 +631,33 @@ cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint3
 
 template <class K>
 cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint32_t* uoff,
-                         const uint64_t* nf_off, const uint8_t* allgone, const uint32_t* alloc_ids,
-                         uint64_t push_base)
+                         const uint64_t* nf_off, const uint8_t* allgone, const uint32_t* alloc_ids)
 {
     const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
     return launch(c, K_UPD_APPLY, dim3(grid), dim3(UP_THREADS), apply_smem<K>(c.h->NS), k_update_apply<K>,
                   dev_view<K>(c.h), ukey, uop, uval, uoff, (const uint32_t*)c.h->tnode, nf_off, allgone, alloc_ids,
-                  c.h->free_ids, push_base);
+                  c.h->free_ids, (const DevState*)c.h->dstate);
 }
 
-cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint64_t from, uint64_t count, uint32_t* out)
+cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint32_t* out, uint64_t cap_out)
 {
-    return launch(c, K_ALLOC_COPY, dim3(div_up(count, 256)), dim3(256), 0, k_alloc_copy, free_ids, from, count, out);
+    return launch(c, K_ALLOC_COPY, dim3(div_up(cap_out, 256)), dim3(256), 0, k_alloc_copy, free_ids,
+                  (const DevState*)c.h->dstate, out, cap_out);
+}
+
+cudaError_t admit(Ctx& c, const uint64_t* nf_total, const uint32_t* badkey, const uint64_t* range_total,
+                  uint64_t range_cap, uint64_t* status)
+{
+    return launch(c, K_ADMIT, dim3(1), dim3(1), 0, k_admit, c.h->dstate, nf_total, badkey, range_total, range_cap,
+                  status);
+}
+
+cudaError_t commit(Ctx& c) { return launch(c, K_ADMIT, dim3(1), dim3(1), 0, k_commit, c.h->dstate); }
+
+cudaError_t set_free_top(Ctx& c, uint64_t value)
+{
+    c.h->free_top = value;
+    return launch(c, K_ADMIT, dim3(1), dim3(1), 0, k_set_free_top, c.h->dstate, value);
 }
 
 #define FLIX_UPD_INST(K)                                                                                        \
@@ -609,7 +666,7 @@ cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint64_t from, uint64_t
                                          const K*, K*, uint32_t*, K*, uint32_t*);                              \
     template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const uint32_t*, uint64_t*, uint8_t*); \
     template cudaError_t update_apply<K>(Ctx&, const K*, const uint32_t*, const K*, const uint32_t*,           \
-                                         const uint64_t*, const uint8_t*, const uint32_t*, uint64_t);
+                                         const uint64_t*, const uint8_t*, const uint32_t*);
 
 FLIX_UPD_INST(uint32_t)
 FLIX_UPD_INST(uint64_t)

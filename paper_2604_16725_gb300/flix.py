@@ -55,6 +55,8 @@ SIGNATURES = {
     "flix_insert": (_INT, [_VP, _VP, _VP, _U64, _VP]),
     "flix_delete": (_INT, [_VP, _VP, _U64, _VP]),
     "flix_apply": (_INT, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _U64, _VP, _VP]),
+    "flix_apply_async": (_INT, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _U64, _VP, _VP]),
+    "flix_reserve": (_INT, [_VP, _U64, _U64, _VP]),
     "flix_restructure": (_INT, [_VP, _VP]),
     "flix_stats": (_INT, [_VP, _VP, _VP]),
     "flix_export": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP]),
@@ -234,6 +236,21 @@ class Index:
         _check(code, "flix_apply", self._h)
         t = int(total.value)
         return dict(keys=ko, vals=vo, found=f, range_off=off, range_keys=rk[:t], range_vals=rv[:t])
+
+    def apply_async(self, ops, keys, aux, out, stream=None):
+        """Mixed batch with no host synchronisation (graph-capturable).  `out` holds preallocated
+        device tensors: keys, vals, found, range_off (n+1), range_keys, range_vals, status (4 x
+        int64).  Nothing is returned; read out["status"] after the stream reaches the call."""
+        o = self._dev(ops, torch.uint8)
+        k, a = self._dev(keys), self._dev(aux)
+        cap = out["range_keys"].numel()
+        _check(load().flix_apply_async(self._h, _ptr(o), _ptr(k), _ptr(a), k.numel(), _ptr(out["keys"]),
+                                       _ptr(out["vals"]), _ptr(out["found"]), _ptr(out["range_off"]),
+                                       _ptr(out["range_keys"]), _ptr(out["range_vals"]), cap, _ptr(out["status"]),
+                                       _stream(stream)), "flix_apply_async", self._h)
+
+    def reserve(self, batch_max: int, free_nodes_min: int = 0, stream=None):
+        _check(load().flix_reserve(self._h, batch_max, free_nodes_min, _stream(stream)), "flix_reserve", self._h)
 
     def restructure(self, stream=None):
         _check(load().flix_restructure(self._h, _stream(stream)), "flix_restructure", self._h)

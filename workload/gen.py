@@ -340,7 +340,8 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
             span = ((w[2 * m:] % np.uint64(max_len)).astype(np.uint64) + np.uint64(1)) * np.uint64(gap)
             with np.errstate(over="ignore"):
                 hi = kk + span
-            hi = np.where(hi < kk, np.uint64(key_max(kw) - 1), hi)
+            hi = np.where(hi < kk, np.uint64(key_max(kw) - 1), hi)          # 64-bit wrap
+            hi = np.minimum(hi, np.uint64(key_max(kw) - 1))
             aux[is_rng] = hi[is_rng].astype(dt)
             inserted.append(fresh)
             yield ops, keys, aux
