@@ -29,7 +29,7 @@ _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 __all__ = [
     "OP_NOP", "OP_LOOKUP", "OP_SUCC", "OP_RANGE", "OP_INSERT", "OP_DELETE",
     "key_max", "mix64", "mix32", "uniform01", "universe", "values_for", "zipf",
-    "scramble30", "log_uniform_sizes", "permutation",
+    "scramble30", "scramble_bits", "universe_at", "log_uniform_sizes", "permutation",
     "config1", "read_scale", "update_heavy", "mixed_stream", "serving_requests",
 ]
 
@@ -85,7 +85,13 @@ def universe(kw: int, seed: int, lo: int, hi: int) -> np.ndarray:
     all-ones word is redirected to the spare counter 2^kw - 1, which no caller uses.
     """
     assert 0 <= lo <= hi
-    ctr = np.arange(lo, hi, dtype=np.uint64)
+    assert kw == 64 or hi <= (1 << 32) - 1
+    return universe_at(kw, seed, np.arange(lo, hi, dtype=np.uint64))
+
+
+def universe_at(kw: int, seed: int, ctr: np.ndarray) -> np.ndarray:
+    """Keys of the seeded universe at the given counters (see `universe`)."""
+    ctr = np.asarray(ctr, dtype=np.uint64)
     if kw == 64:
         s = _stream_words(seed, 0xC0FFEE, 1)[0]
         k = mix64(ctr ^ s)
@@ -93,7 +99,7 @@ def universe(kw: int, seed: int, lo: int, hi: int) -> np.ndarray:
         if bad.any():
             k[bad] = mix64(np.array([_M64 ^ s], dtype=np.uint64))[0]
         return k
-    assert kw == 32 and hi <= (1 << 32) - 1
+    assert kw == 32
     s = np.uint32(int(_stream_words(seed, 0xC0FFEE, 1)[0]) & 0xFFFFFFFF)
     k = mix32(ctr.astype(np.uint32) ^ s)
     bad = k == np.uint32(0xFFFFFFFF)
@@ -350,18 +356,31 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
                 batches=batches)
 
 
+def scramble_bits(r: np.ndarray, bits: int, seed: int) -> np.ndarray:
+    """A seeded bijection of [0, 2^bits): four rounds of odd multiply and xorshift mod 2^bits."""
+    m = np.uint64((1 << bits) - 1)
+    x = np.asarray(r, dtype=np.uint64) & m
+    keys = _stream_words(seed, 77, 4) | np.uint64(1)
+    with np.errstate(over="ignore"):
+        for k in keys:
+            x = (x * k) & m
+            x ^= x >> np.uint64(max(bits // 2, 1))
+    return x
+
+
 def serving_requests(seed: int = 5000, kw: int = 64, universe_bits: int = 29, preload_bits: int = 28,
                      offered_ops_per_s: float = 1e8, n_requests: int = 100000, zipf_s: float = 0.9,
                      mix=(0.80, 0.10, 0.10)):
     """Serving-form request schedule: Poisson arrivals of requests of floor(2^U(0,12)) ops,
-    80/10/10 lookup/insert/delete over Zipf(0.9) ranks mapped through a seeded permutation.
+    80/10/10 lookup/insert/delete over Zipf(0.9) ranks mapped through a seeded bijection of the
+    universe's indices (so popular keys are spread over the key space).
 
-    Returns the universe, the preload count, and per-request (arrival_s, ops, keys, aux) arrays in
-    CSR form (req_off[n_requests + 1]).
+    The universe is mix(counter) for counters [0, 2^universe_bits); the first 2^preload_bits of it
+    are the preload (`universe(kw, seed, 0, 1 << preload_bits)`).  Returns the preload count and
+    per-request (arrival_s, ops, keys, aux) arrays in CSR form (req_off[n_requests + 1]).
     """
     dt = _kdt(kw)
     U = 1 << universe_bits
-    uni = universe(kw, seed, 0, U)
     sizes = log_uniform_sizes(seed, 1, n_requests, 0, 12)
     total = int(sizes.sum())
     mean_ops = total / n_requests
@@ -369,13 +388,13 @@ def serving_requests(seed: int = 5000, kw: int = 64, universe_bits: int = 29, pr
     gaps = -np.log1p(-uniform01(seed, 2, n_requests)) / rate
     arrival = np.cumsum(gaps)
     r = zipf(seed, 3, total, zipf_s, U) - 1
-    pi = permutation(seed, 4, U)
-    keys = uni[pi[r]].astype(dt)
+    ctr = scramble_bits(r, universe_bits, seed)
+    keys = universe_at(kw, seed, ctr).astype(dt)
     cum = np.cumsum(np.array(mix) / np.sum(mix))
     sel = np.searchsorted(cum, uniform01(seed, 5, total), side="right")
     ops = np.array([OP_LOOKUP, OP_INSERT, OP_DELETE], dtype=np.uint8)[np.minimum(sel, 2)]
     aux = np.where(ops == OP_INSERT, values_for(kw, keys, salt=3), 0).astype(dt)
     off = np.zeros(n_requests + 1, dtype=np.int64)
     off[1:] = np.cumsum(sizes)
-    return dict(kw=kw, universe=uni, n_preload=1 << preload_bits, arrival_s=arrival,
-                req_off=off, ops=ops, keys=keys, aux=aux)
+    return dict(kw=kw, universe_bits=universe_bits, n_preload=1 << preload_bits, arrival_s=arrival,
+                req_off=off, ops=ops, keys=keys, aux=aux, mean_ops=mean_ops)
