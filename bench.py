@@ -270,6 +270,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flix", choices=["flix", "reference"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served"],
+                    help="plain: the read-scale step (default); batched: mixed-batch stream through CUDA "
+                         "graphs vs plain launches; served: continuous batching under Poisson arrivals")
+    ap.add_argument("--batches", type=int, default=300, help="batched form: stream length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
@@ -279,6 +283,10 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.form == "batched":
+        return bench_batched(args)
+    if args.form == "served":
+        return bench_served(args)
 
     import torch
     rank, world, local = dist_env()
@@ -430,6 +438,148 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# Batched and served forms (their own JSON lines; the default run is the plain read-scale step)
+# ------------------------------------------------------------------------------------------------
+
+def bench_batched(args):
+    """Uneven mixed batches (sizes 2^8..2^22, 60/15/5/10/10 lookup/successor/range/insert/delete) on a
+    2^27-key uint64 index: plain per-batch flix_apply vs the batched form (CUDA graph per size class,
+    device-side admission).  Node size and sort variant come from the autotuner on a held-out seed."""
+    import torch
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.batched import BatchedRunner
+    from paper_2604_16725_gb300.tune import autotune
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    # autotune on a held-out seed, scaled-down preload
+    held = W.mixed_stream(seed=4999, n_preload=1 << 22, n_batches=40, lo_exp=8, hi_exp=20)
+    hb = [(torch.from_numpy(o).cuda(), torch.from_numpy(k.view(np.int64)).cuda(),
+           torch.from_numpy(a.view(np.int64)).cuda()) for o, k, a in held["batches"]()]
+    tune = autotune(64, held["preload_keys"], held["preload_vals"], hb, range_per_op=64, log=log)
+    NS, sv = tune["node_size"], tune["sort_variant"]
+    log("autotune: NS=%d sort_variant=%d" % (NS, sv))
+    del hb
+    s = W.mixed_stream(seed=4000, n_preload=1 << args.log_load if args.log_load != LOG_LOAD else 1 << 27,
+                       n_batches=args.batches)
+    batches = []
+    for o, k, a in s["batches"]():
+        batches.append((torch.from_numpy(o).cuda(), torch.from_numpy(k.view(np.int64)).cuda(),
+                        torch.from_numpy(a.view(np.int64)).cuda()))
+    n_ops = sum(int(k.numel()) for _, k, _ in batches)
+    pk = torch.from_numpy(s["preload_keys"].view(np.int64)).cuda()
+    pv = torch.from_numpy(s["preload_vals"].view(np.int64)).cuda()
+    max_b = max(int(k.numel()) for _, k, _ in batches)
+    results = {}
+    finals = {}
+    for mode in ("plain", "batched"):
+        idx = fx.Index(key_bits=64, node_size=NS, sort_variant=sv)
+        idx.bulk_load(pk, pv)
+        st = torch.cuda.Stream()
+        per = []
+        if mode == "batched":
+            run = BatchedRunner(idx, max_batch=max_b, min_log=8, range_per_op=64, free_nodes_min=n_ops // 4 + (1 << 20))
+            for o, k, a in batches:
+                run.graph_for(run.size_for(int(k.numel())))
+            st = run.stream
+        else:
+            idx.reserve(max_b, n_ops // 4 + (1 << 20))
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(batches) + 1)]
+        t0 = time.perf_counter()
+        evs[0].record(st)
+        for i, (o, k, a) in enumerate(batches):
+            if mode == "batched":
+                run.run(o, k, a)
+            else:
+                with torch.cuda.stream(st):
+                    idx.apply(o, k, a, range_capacity=64 * int(k.numel()), stream=st)
+            evs[i + 1].record(st)
+            if (i + 1) % 50 == 0:
+                if mode == "batched":
+                    run.restructure_if_needed()
+                else:
+                    s_ = idx.stats(stream=st)
+                    if s_["nodes_used"] > 2 * s_["buckets"] or s_["max_chain"] > 64:
+                        idx.restructure(stream=st)
+        if mode == "batched":
+            run.synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(batches))]
+        sizes = np.array([int(k.numel()) for _, k, _ in batches])
+        small = sizes <= 4096
+        results[mode] = {"mops": n_ops / wall / 1e6, "wall_s": wall,
+                         "batch_ms_p50": float(np.median(per)), "batch_ms_p99": float(np.percentile(per, 99)),
+                         "small_batches_mops": float(sizes[small].sum() / (np.array(per)[small].sum() * 1e-3) / 1e6)
+                         if small.any() else None}
+        k_, v_ = idx.export()
+        finals[mode] = (k_.cpu(), v_.cpu())
+        log("%s: %.1f Mops/s" % (mode, results[mode]["mops"]))
+        idx.close()
+        torch.cuda.empty_cache()
+    same_state = bool(torch.equal(finals["plain"][0], finals["batched"][0]) and
+                      torch.equal(finals["plain"][1], finals["batched"][1]))
+    line = {"form": "batched", "metric": METRIC, "value": results["batched"]["mops"], "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched: 2^27 uint64 keys preloaded; %d mixed batches, sizes log-uniform "
+                                   "2^8..2^22, 60/15/5/10/10 lookup/successor/range(1-1000)/insert/delete" % len(batches),
+                       "node_size": NS, "sort_variant": sv, "ops": n_ops},
+            "plain": results["plain"], "batched": results["batched"],
+            "speedup_vs_plain": results["batched"]["mops"] / results["plain"]["mops"],
+            "final_state_equal": same_state, "autotune": tune["table"]}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_served(args):
+    """Continuous batching of Poisson-arriving requests (1..4096 ops, 80/10/10 lookup/insert/delete
+    over Zipf(0.9) keys) on a 2^28-key uint64 index (universe 2^29): p50/p99 latency and sustained
+    Mops/s per offered load, and the plain per-request path at the lowest load."""
+    import torch
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.serve import Server, plain_serve
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    ubits = 29
+    pbits = 28 if args.log_load == LOG_LOAD else args.log_load
+    seed = 5000
+    pk = W.universe(64, seed, 0, 1 << pbits)
+    pv = W.values_for(64, pk)
+    idx = fx.Index(key_bits=64, node_size=64)
+    idx.bulk_load(torch.from_numpy(pk.view(np.int64)).cuda(), torch.from_numpy(pv.view(np.int64)).cuda())
+    del pk, pv
+    srv = Server(idx, max_batch=1 << 22, depth=2, min_log=8, free_nodes_min=1 << 22)
+    loads = []
+    for rate in (1e6, 1e7, 1e8, 1e9):
+        mean_ops = 585.0
+        n_req = int(min(max(rate * 2.0 / mean_ops, 2000), 80000))
+        req = W.serving_requests(seed=seed + int(np.log10(rate)), universe_bits=ubits, preload_bits=pbits,
+                                 offered_ops_per_s=rate, n_requests=n_req)
+        out = srv.serve(req["arrival_s"], req["req_off"], req["ops"], req["keys"], req["aux"])
+        lat = out["latency_s"] * 1e3
+        loads.append({"offered_mops": rate / 1e6, "requests": n_req, "ops": out["ops"],
+                      "sustained_mops": out["ops"] / out["wall_s"] / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "batches": out["batches"],
+                      "mean_batch_ops": out["ops"] / max(out["batches"], 1)})
+        log("offered %.0e: %s" % (rate, loads[-1]))
+    # plain per-request path at the lowest offered load (bounded number of requests)
+    req = W.serving_requests(seed=seed + 6, universe_bits=ubits, preload_bits=pbits, offered_ops_per_s=1e6,
+                             n_requests=600)
+    pl = plain_serve(idx, req["arrival_s"], req["req_off"], req["ops"], req["keys"], req["aux"])
+    lat = pl["latency_s"] * 1e3
+    plain = {"offered_mops": 1.0, "requests": 600, "sustained_mops": pl["ops"] / pl["wall_s"] / 1e6,
+             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    line = {"form": "served", "metric": METRIC, "value": max(x["sustained_mops"] for x in loads), "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served: 2^%d uint64 keys preloaded (universe 2^%d); Poisson requests of "
+                                   "floor(2^U(0,12)) ops, 80/10/10 lookup/insert/delete over Zipf(0.9)" % (pbits, ubits),
+                       "node_size": 64, "depth": 2},
+            "loads": loads, "plain_per_request": plain}
+    print(json.dumps(line))
     return 0
 
 

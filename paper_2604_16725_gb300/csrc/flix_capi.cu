@@ -247,14 +247,14 @@ int do_read_point(flix_index* h, int mode, const K* keys, uint64_t n, K* keys_ou
 {
     if (n == 0) return FLIX_OK;
     Ctx c{h, st};
-    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) + al((h->nb + 1) * 4) + (1 << 16)));
+    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 2 + (1 << 16)));
     h->arena.reset();
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);
-    uint32_t* off = h->arena.take<uint32_t>(h->nb + 1);
+    uint32_t* bk = h->arena.take<uint32_t>(n);
     CK(sort_pairs<K>(c, keys, nullptr, sk, si, n));
-    CK(partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, off));
-    CK(read_point<K>(c, mode, sk, si, n, off, nullptr, keys_out, vals_out, found));
+    CK(partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, nullptr, bk));
+    CK(read_point<K>(c, mode, sk, si, n, bk, nullptr, keys_out, vals_out, found));
     return FLIX_OK;
 }
 
@@ -268,8 +268,8 @@ int do_range(flix_index* h, const K* lo, const K* hi, uint64_t n, uint64_t* roff
         if (h_total) *h_total = 0;
         return FLIX_OK;
     }
-    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 4 + al(n * 8) +
-                       al((h->nb + 1) * 4) + scan_scratch_bytes<uint64_t>(n) + (1 << 16)));
+    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 5 + al(n * 8) +
+                       scan_scratch_bytes<uint64_t>(n) + (1 << 16)));
     h->arena.reset();
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);
@@ -277,10 +277,10 @@ int do_range(flix_index* h, const K* lo, const K* hi, uint64_t n, uint64_t* roff
     uint32_t* sn = h->arena.take<uint32_t>(n);
     uint32_t* sp = h->arena.take<uint32_t>(n);
     uint64_t* cnt = h->arena.take<uint64_t>(n);
-    uint32_t* off = h->arena.take<uint32_t>(h->nb + 1);
+    uint32_t* bk = h->arena.take<uint32_t>(n);
     CK(sort_pairs<K>(c, lo, nullptr, sk, si, n));
-    CK(partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, off));
-    CK(range_count<K>(c, sk, si, n, off, nullptr, hi, sb, sn, sp, cnt));
+    CK(partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, nullptr, bk));
+    CK(range_count<K>(c, sk, si, n, bk, nullptr, hi, sb, sn, sp, cnt));
     CK(scan_exclusive<uint64_t, uint64_t>(c, cnt, roff, n));
     int r = readback(h, st, {{roff + n, 8}});
     if (r) return r;
@@ -336,15 +336,15 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     uint64_t* roff = roff_user;
     uint32_t *sb = nullptr, *sn = nullptr, *sp = nullptr;
     if (mixed) {
-        uint32_t* off = A.take<uint32_t>(nb + 1);
-        CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, sk, n, nullptr, off));
-        CK(read_point<K>(c, 0, sk, si, n, off, ops, keys_out, vals_out, found));
+        uint32_t* bk = A.take<uint32_t>(n);
+        CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, sk, n, nullptr, nullptr, bk));
+        CK(read_point<K>(c, 0, sk, si, n, bk, ops, keys_out, vals_out, found));
         if (!roff) roff = A.take<uint64_t>(n + 1);
         sb = A.take<uint32_t>(n);
         sn = A.take<uint32_t>(n);
         sp = A.take<uint32_t>(n);
         uint64_t* cnt = A.take<uint64_t>(n);
-        CK(range_count<K>(c, sk, si, n, off, ops, aux, sb, sn, sp, cnt));
+        CK(range_count<K>(c, sk, si, n, bk, ops, aux, sb, sn, sp, cnt));
         CK(scan_exclusive<uint64_t, uint64_t>(c, cnt, roff, n));
     }
     // updates: net effect per key, bucket partition, node demand
@@ -360,7 +360,7 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     uint32_t* alloc_ids = A.take<uint32_t>(alloc_cap);
     if (!ukey || !uop || !uval || !uoff || !nf || !nf_off || !allgone || !alloc_ids) return FLIX_ENOMEM;
     CK(fold_updates<K>(c, sk, si, n, ops, hom_op, aux, ukey, uop, uval, udev));
-    CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff));
+    CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff, nullptr));
     CK(update_count<K>(c, ukey, uop, uoff, nf, allgone));
     CK(scan_exclusive<uint64_t, uint64_t>(c, nf, nf_off, nb));
     const uint64_t* nf_total = nf_off + nb;

@@ -204,19 +204,20 @@ size_t scan_scratch_bytes(uint64_t n);
 // off[0..nb]: off[i] = number of sorted keys <= mkba[i-1] (off[0] = 0), by a merge-path co-rank
 // of the sorted MKBA with the sorted batch.  m_dev (optional) holds the batch length on the device
 // (then m is an upper bound).
+// bk (optional): bk[j] = bucket of sorted key j.  off (optional) as above.
 template <class K>
 cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m,
-                      const uint32_t* m_dev, uint32_t* off);
+                      const uint32_t* m_dev, uint32_t* off, uint32_t* bk);
 
 template <class K>
 cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m,
-                       const uint32_t* off, const uint8_t* ops, K* keys_out, K* vals_out,
+                       const uint32_t* bk, const uint8_t* ops, K* keys_out, K* vals_out,
                        uint8_t* found_out);
 
 // Range count: per range op its start (bucket, node, position) in sorted order and its pair
 // count cnt[idx] in submission order (0 for non-range ops when ops != nullptr).
 template <class K>
-cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* off,
+cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* bk,
                         const uint8_t* ops, const K* hi, uint32_t* start_bucket, uint32_t* start_node,
                         uint32_t* start_pos, uint64_t* cnt);
 

@@ -1,5 +1,5 @@
 // flix_lookup_noalloc: the point-query path of flix_lookup with its scratch memory (sort buffers,
-// digit counts, bucket offsets) taken from one fixed array compiled into the library instead of
+// digit counts, per-query buckets) taken from one fixed array compiled into the library instead of
 // the handle's scratch arena, so the call itself allocates no device memory.
 //
 // Who needs it: callers that run where device allocation is unavailable or forbidden at call
@@ -58,7 +58,7 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 template <class K>
 size_t noalloc_need(uint64_t n, uint64_t nb)
 {
-    return sort_scratch_bytes<K>(n) + al256(n * sizeof(K)) + al256(n * 4) + al256((nb + 1) * 4);
+    return sort_scratch_bytes<K>(n) + al256(n * sizeof(K)) + al256(n * 4) * 2;
 }
 
 template <class K>
@@ -90,12 +90,12 @@ int lookup_noalloc(flix_index* h, const K* keys, uint64_t n, K* vals_out, uint8_
     Ctx c{h, st};
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);
-    uint32_t* off = h->arena.take<uint32_t>(h->nb + 1);
+    uint32_t* bk = h->arena.take<uint32_t>(n);
     e = cudaSuccess;
-    if (!sk || !si || !off) e = cudaErrorMemoryAllocation;
+    if (!sk || !si || !bk) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = sort_pairs<K>(c, keys, nullptr, sk, si, n);
-    if (e == cudaSuccess) e = partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, off);
-    if (e == cudaSuccess) e = read_point<K>(c, FLIX_OP_LOOKUP, sk, si, n, off, nullptr, nullptr, vals_out, found);
+    if (e == cudaSuccess) e = partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, nullptr, bk);
+    if (e == cudaSuccess) e = read_point<K>(c, FLIX_OP_LOOKUP, sk, si, n, bk, nullptr, nullptr, vals_out, found);
     h->arena = saved;
     h->prof_on = prof;
     if (e != cudaSuccess) {

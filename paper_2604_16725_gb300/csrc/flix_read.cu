@@ -5,18 +5,19 @@
 // first sorted key greater than maxBucket_{i-1}.  The paper finds that start with one binary search
 // per bucket.  Here all starts come from one merge-path co-ranking of the sorted MKBA with the
 // sorted batch (a key equal to a maxBucket goes before it), which yields the same offsets with
-// coalesced reads and one global search per 2048 merged items.
+// coalesced reads and one global search per 2048 merged items.  The same merge also tells every
+// operation its bucket (the number of maxBucket values below its key), which the read kernels use.
 //
-// Queries.  A warp owns 32 consecutive buckets and pulls their joint sublist [off[b0], off[b0+32])
-// from the partition; each lane takes one query, finds its bucket among the 32 by a shuffle
-// search over the buckets' starts, walks the node-links to the first node with key <= maxKey
-// (Sec. 4.1), and binary-searches that node.  Buckets with no queries cost one coalesced load.
+// Queries.  One thread per sorted query: it takes its bucket from the partition, walks the
+// node-links from the bucket's first node to the first node with key <= maxKey (Sec. 4.1) and
+// binary-searches that node.  Consecutive threads hold consecutive keys, so the threads of a warp
+// share buckets and nodes and their loads coalesce or hit L1; a bucket that receives many queries
+// (skew, or a padded batch's tail) is spread over as many threads as it has queries.
 #include "flix_internal.cuh"
 
 namespace flix {
 namespace {
 
-constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr int PT_THREADS = 256;
 constexpr int PT_ITEMS = 8;
 constexpr int PT_TILE = PT_THREADS * PT_ITEMS;
@@ -36,11 +37,13 @@ __device__ __forceinline__ uint64_t corank(const K* __restrict__ A, uint64_t nA,
     return lo;
 }
 
+// off[i + 1] = number of batch keys <= mkba[i] (off may be null); bk[j] = bucket of batch key j (bk
+// may be null).
 template <class K>
 __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ mkba, uint64_t nA,
                                                           const K* __restrict__ skeys, uint64_t mmax,
                                                           const uint32_t* __restrict__ m_dev,
-                                                          uint32_t* __restrict__ off)
+                                                          uint32_t* __restrict__ off, uint32_t* __restrict__ bk)
 {
     __shared__ K sA[PT_TILE];
     __shared__ K sB[PT_TILE];
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
     const uint64_t d0 = (uint64_t)blockIdx.x * PT_TILE;
     if (d0 >= L) return;
     const uint64_t d1 = d0 + PT_TILE < L ? d0 + PT_TILE : L;
-    if (blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
+    if (off && blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
     if (threadIdx.x < 2) s_a[threadIdx.x] = corank(mkba, nA, skeys, m, threadIdx.x ? d1 : d0);
     __syncthreads();
     const uint64_t a0 = s_a[0], a1 = s_a[1];
@@ -72,9 +75,10 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
         if (a + b >= la + lb) break;
         const bool takeA = (b >= lb) || (a < la && sA[a] < sB[b]);
         if (takeA) {
-            off[a0 + a + 1] = (uint32_t)(b0 + b);
+            if (off) off[a0 + a + 1] = (uint32_t)(b0 + b);
             a++;
         } else {
+            if (bk) bk[b0 + b] = (uint32_t)(a0 + a);
             b++;
         }
     }
@@ -106,90 +110,47 @@ __device__ __forceinline__ uint32_t node_upper_bound(const K* __restrict__ nk, u
     return base;
 }
 
-// Per-warp bucket-group state: lane l describes bucket b0 + l.
+// From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1).
 template <class K>
-struct Group {
-    uint32_t s_l, node_l, sz_l, nx_l;
-    K bd_l;
-    uint32_t S, E;
-};
-
-template <class K>
-__device__ __forceinline__ bool load_group(const DevIdx<K>& ix, const uint32_t* __restrict__ off, uint64_t b0,
-                                           uint32_t lane, Group<K>& g)
+__device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, uint32_t& node, uint32_t& sz, K& bd,
+                                          uint32_t& nx)
 {
-    const uint64_t nb = ix.nb;
-    const uint64_t b = b0 + lane;
-    g.s_l = off[b < nb ? b : nb];
-    const uint32_t e_l = off[b < nb ? b + 1 : nb];
-    g.S = __shfl_sync(FULL, g.s_l, 0);
-    g.E = __shfl_sync(FULL, e_l, 31);
-    if (g.S == g.E) return false;
-    g.node_l = 0; g.sz_l = 0; g.nx_l = NIL; g.bd_l = K(0);
-    if (b < nb && g.s_l < e_l) {
-        g.node_l = ix.head[b];
-        g.sz_l = ix.size[g.node_l];
-        g.bd_l = ix.bound[g.node_l];
-        g.nx_l = ix.next[g.node_l];
+    node = __ldg(ix.head + b);
+    sz = __ldg(ix.size + node);
+    bd = __ldg(ix.bound + node);
+    nx = __ldg(ix.next + node);
+    uint32_t steps = 0;
+    while (q > bd) {
+        if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return false; }
+        node = nx;
+        sz = __ldg(ix.size + node);
+        bd = __ldg(ix.bound + node);
+        nx = __ldg(ix.next + node);
     }
     return true;
 }
 
-// Lane index of the bucket (within the group) that owns sorted position j.
-__device__ __forceinline__ uint32_t find_slot(uint32_t s_l, uint32_t j)
-{
-    uint32_t i = 0;
-#pragma unroll
-    for (uint32_t st = 16; st; st >>= 1) {
-        uint32_t si = __shfl_sync(FULL, s_l, i + st);
-        if (si <= j) i += st;
-    }
-    return i;
-}
-
-// Walk node-links from (node, bd, sz, nx) to the first node whose maxKey >= q (Sec. 4.1).
-template <class K>
-__device__ __forceinline__ void walk_to(const DevIdx<K>& ix, K q, uint32_t& node, uint32_t& sz, K& bd, uint32_t& nx)
-{
-    uint32_t steps = 0;
-    while (q > bd) {
-        if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return; }
-        node = nx;
-        sz = ix.size[node];
-        bd = ix.bound[node];
-        nx = ix.next[node];
-    }
-}
-
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mode, const K* __restrict__ skeys,
-                                                           const uint32_t* __restrict__ sidx,
-                                                           const uint32_t* __restrict__ off,
+                                                           const uint32_t* __restrict__ sidx, uint64_t m,
+                                                           const uint32_t* __restrict__ bk,
                                                            const uint8_t* __restrict__ ops, K* __restrict__ keys_out,
                                                            K* __restrict__ vals_out, uint8_t* __restrict__ found_out)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t b0 = (((uint64_t)blockIdx.x * RP_THREADS + threadIdx.x) >> 5) * 32;
-    if (b0 >= ix.nb) return;
-    Group<K> g;
-    if (!load_group(ix, off, b0, lane, g)) return;
+    const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
+    if (j >= m) return;
+    const uint32_t idx = sidx[j];
+    const int op = mode ? mode : ops[idx];
     const K KM = key_max<K>();
-    const uint32_t NS = ix.NS;
-    for (uint32_t j0 = g.S; j0 < g.E; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        const uint32_t i = find_slot(g.s_l, j);
-        uint32_t node = __shfl_sync(FULL, g.node_l, i);
-        uint32_t sz = __shfl_sync(FULL, g.sz_l, i);
-        uint32_t nx = __shfl_sync(FULL, g.nx_l, i);
-        K bd = __shfl_sync(FULL, g.bd_l, i);
-        if (j >= g.E) continue;
+    K rk = KM, rv = KM;
+    uint8_t f = 0;
+    if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC) {
         const K q = skeys[j];
-        const uint32_t idx = sidx[j];
-        const int op = mode ? mode : ops[idx];
-        K rk = KM, rv = KM;
-        uint8_t f = 0;
-        if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC) {
-            walk_to(ix, q, node, sz, bd, nx);
+        const uint32_t b = bk[j];
+        const uint32_t NS = ix.NS;
+        uint32_t node, sz, nx;
+        K bd;
+        if (find_node(ix, b, q, node, sz, bd, nx)) {
             const K* nk = ix.keys + (uint64_t)node * NS;
             const uint32_t pos = node_lower_bound(nk, sz, q);
             if (op == FLIX_OP_LOOKUP) {
@@ -206,7 +167,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
                 // the smallest key >= q is the first key of the next non-empty node in chain order,
                 // continuing into the following buckets
                 uint32_t n2 = nx;
-                uint64_t bb = b0 + i;
+                uint64_t bb = b;
                 for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
                     if (n2 == NIL) {
                         if (++bb >= ix.nb) break;
@@ -223,73 +184,69 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
                 }
             }
         }
-        if (keys_out) keys_out[idx] = rk;
-        if (vals_out) vals_out[idx] = rv;
-        if (found_out) found_out[idx] = f;
     }
+    if (keys_out) keys_out[idx] = rk;
+    if (vals_out) vals_out[idx] = rv;
+    if (found_out) found_out[idx] = f;
 }
 
 // Range count: per range query, the start (bucket, node, position) and the number of stored keys
 // in [lo, hi].  Nodes whose maxKey <= hi are counted from their size alone.
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const K* __restrict__ skeys,
-                                                            const uint32_t* __restrict__ sidx,
-                                                            const uint32_t* __restrict__ off,
+                                                            const uint32_t* __restrict__ sidx, uint64_t m,
+                                                            const uint32_t* __restrict__ bk,
                                                             const uint8_t* __restrict__ ops, const K* __restrict__ hi_arr,
                                                             uint32_t* __restrict__ start_bucket,
                                                             uint32_t* __restrict__ start_node,
                                                             uint32_t* __restrict__ start_pos, uint64_t* __restrict__ cnt)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t b0 = (((uint64_t)blockIdx.x * RP_THREADS + threadIdx.x) >> 5) * 32;
-    if (b0 >= ix.nb) return;
-    Group<K> g;
-    if (!load_group(ix, off, b0, lane, g)) return;
-    const uint32_t NS = ix.NS;
-    for (uint32_t j0 = g.S; j0 < g.E; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        const uint32_t i = find_slot(g.s_l, j);
-        uint32_t node = __shfl_sync(FULL, g.node_l, i);
-        uint32_t sz = __shfl_sync(FULL, g.sz_l, i);
-        uint32_t nx = __shfl_sync(FULL, g.nx_l, i);
-        K bd = __shfl_sync(FULL, g.bd_l, i);
-        if (j >= g.E) continue;
-        const uint32_t idx = sidx[j];
-        if (ops && ops[idx] != FLIX_OP_RANGE) {
-            cnt[idx] = 0;
-            continue;
-        }
-        const K lo = skeys[j];
-        const K hi = hi_arr[idx];
-        uint64_t c = 0;
-        uint32_t bb = (uint32_t)(b0 + i);
-        walk_to(ix, lo, node, sz, bd, nx);
-        uint32_t pos = node_lower_bound(ix.keys + (uint64_t)node * NS, sz, lo);
-        start_bucket[j] = bb;
-        start_node[j] = node;
-        start_pos[j] = pos;
-        if (lo <= hi) {
-            for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
-                if (bd <= hi) {
-                    c += sz - pos;
-                } else {
-                    c += node_upper_bound(ix.keys + (uint64_t)node * NS, pos, sz, hi) - pos;
-                    break;
-                }
-                node = nx;
-                while (node == NIL) {
-                    if (++bb >= ix.nb) break;
-                    node = ix.head[bb];
-                }
-                if (node == NIL) break;
-                sz = ix.size[node];
-                bd = ix.bound[node];
-                nx = ix.next[node];
-                pos = 0;
-            }
-        }
-        cnt[idx] = c;
+    const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
+    if (j >= m) return;
+    const uint32_t idx = sidx[j];
+    if (ops && ops[idx] != FLIX_OP_RANGE) {
+        cnt[idx] = 0;
+        return;
     }
+    const uint32_t NS = ix.NS;
+    const K lo = skeys[j];
+    const K hi = hi_arr[idx];
+    uint32_t bb = bk[j];
+    uint32_t node, sz, nx;
+    K bd;
+    uint64_t c = 0;
+    if (!find_node(ix, bb, lo, node, sz, bd, nx)) {
+        cnt[idx] = 0;
+        start_bucket[j] = bb;
+        start_node[j] = ix.head[bb];
+        start_pos[j] = 0;
+        return;
+    }
+    uint32_t pos = node_lower_bound(ix.keys + (uint64_t)node * NS, sz, lo);
+    start_bucket[j] = bb;
+    start_node[j] = node;
+    start_pos[j] = pos;
+    if (lo <= hi) {
+        for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
+            if (bd <= hi) {
+                c += sz - pos;
+            } else {
+                c += node_upper_bound(ix.keys + (uint64_t)node * NS, pos, sz, hi) - pos;
+                break;
+            }
+            node = nx;
+            while (node == NIL) {
+                if (++bb >= ix.nb) break;
+                node = ix.head[bb];
+            }
+            if (node == NIL) break;
+            sz = ix.size[node];
+            bd = ix.bound[node];
+            nx = ix.next[node];
+            pos = 0;
+        }
+    }
+    cnt[idx] = c;
 }
 
 // Range fill: one warp per sorted query copies its pairs node by node (coalesced).
@@ -341,33 +298,29 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
 
 template <class K>
 cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m, const uint32_t* m_dev,
-                      uint32_t* off)
+                      uint32_t* off, uint32_t* bk)
 {
     const uint32_t grid = div_up(nb + m, PT_TILE);
-    return launch(c, K_PARTITION, dim3(grid), dim3(PT_THREADS), 0, k_partition<K>, mkba, nb, skeys, m, m_dev, off);
+    return launch(c, K_PARTITION, dim3(grid), dim3(PT_THREADS), 0, k_partition<K>, mkba, nb, skeys, m, m_dev, off, bk);
 }
 
 template <class K>
-cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* off,
+cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* bk,
                        const uint8_t* ops, K* keys_out, K* vals_out, uint8_t* found_out)
 {
     if (m == 0) return cudaSuccess;
-    const uint64_t groups = (c.h->nb + 31) / 32;
-    const uint32_t grid = div_up(groups * 32, RP_THREADS);
-    return launch(c, K_READ_POINT, dim3(grid), dim3(RP_THREADS), 0, k_read_point<K>, dev_view<K>(c.h), mode, skeys,
-                  sidx, off, ops, keys_out, vals_out, found_out);
+    return launch(c, K_READ_POINT, dim3(div_up(m, RP_THREADS)), dim3(RP_THREADS), 0, k_read_point<K>,
+                  dev_view<K>(c.h), mode, skeys, sidx, m, bk, ops, keys_out, vals_out, found_out);
 }
 
 template <class K>
-cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* off,
+cudaError_t range_count(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* bk,
                         const uint8_t* ops, const K* hi, uint32_t* start_bucket, uint32_t* start_node,
                         uint32_t* start_pos, uint64_t* cnt)
 {
     if (m == 0) return cudaSuccess;
-    const uint64_t groups = (c.h->nb + 31) / 32;
-    const uint32_t grid = div_up(groups * 32, RP_THREADS);
-    return launch(c, K_RANGE_COUNT, dim3(grid), dim3(RP_THREADS), 0, k_range_count<K>, dev_view<K>(c.h), skeys,
-                  sidx, off, ops, hi, start_bucket, start_node, start_pos, cnt);
+    return launch(c, K_RANGE_COUNT, dim3(div_up(m, RP_THREADS)), dim3(RP_THREADS), 0, k_range_count<K>,
+                  dev_view<K>(c.h), skeys, sidx, m, bk, ops, hi, start_bucket, start_node, start_pos, cnt);
 }
 
 template <class K>
@@ -382,8 +335,9 @@ cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* 
                   gated ? (const DevState*)c.h->dstate : (const DevState*)nullptr);
 }
 
-#define FLIX_READ_INST(K)                                                                                  \
-    template cudaError_t partition<K>(Ctx&, const K*, uint64_t, const K*, uint64_t, const uint32_t*, uint32_t*); \
+#define FLIX_READ_INST(K)                                                                                       \
+    template cudaError_t partition<K>(Ctx&, const K*, uint64_t, const K*, uint64_t, const uint32_t*, uint32_t*, \
+                                      uint32_t*);                                                               \
     template cudaError_t read_point<K>(Ctx&, int, const K*, const uint32_t*, uint64_t, const uint32_t*,        \
                                        const uint8_t*, K*, K*, uint8_t*);                                      \
     template cudaError_t range_count<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint32_t*,           \

@@ -45,9 +45,11 @@ class Server:
                 ops=torch.empty(max_batch, dtype=torch.uint8, device=dev),
                 keys=torch.empty(max_batch, dtype=dt, device=dev),
                 aux=torch.empty(max_batch, dtype=dt, device=dev),
+                dvals=torch.empty(max_batch, dtype=dt, device=dev),
+                dfound=torch.empty(max_batch, dtype=torch.uint8, device=dev),
                 vals=torch.empty(max_batch, dtype=dt).pin_memory(),
                 found=torch.empty(max_batch, dtype=torch.uint8).pin_memory(),
-                consumed=torch.cuda.Event(), done=None))
+                consumed=torch.cuda.Event()))
         self.per_insert = 1 if idx.node_size >= 4 else 2
         self.budget = self._free_nodes()
 
@@ -71,7 +73,6 @@ class Server:
         res_vals = np.empty(len(keys), dtype=np.uint32 if idx.kw == 32 else np.uint64) if collect else None
         res_found = np.empty(len(keys), dtype=np.uint8) if collect else None
         inflight = collections.deque()
-        last_done = {}
         log = []
         nxt = 0
         nb = 0
@@ -122,21 +123,19 @@ class Server:
                 ready = torch.cuda.Event()
                 ready.record(self.copy)
             self.compute.wait_event(ready)
-            # a size class's result buffers are overwritten only after its previous batch's copy-out
-            cls = max(self.runner.min_log, int(np.ceil(np.log2(max(n, 1)))))
-            if cls in last_done:
-                self.compute.wait_event(last_done[cls])
             r = self.runner.run(slot["ops"][:n], slot["keys"][:n], slot["aux"][:n])
+            # results leave the runner's shared buffers at once (device to device, on the compute
+            # stream), then go to the host on the copy stream while the next batch computes
+            with torch.cuda.stream(self.compute):
+                slot["dvals"][:n].copy_(r["vals"], non_blocking=True)
+                slot["dfound"][:n].copy_(r["found"], non_blocking=True)
             slot["consumed"].record(self.compute)
-            # device -> host on the copy stream after the batch
             self.copy.wait_event(slot["consumed"])
             with torch.cuda.stream(self.copy):
-                slot["vals"][:n].copy_(r["vals"], non_blocking=True)
-                slot["found"][:n].copy_(r["found"], non_blocking=True)
+                slot["vals"][:n].copy_(slot["dvals"][:n], non_blocking=True)
+                slot["found"][:n].copy_(slot["dfound"][:n], non_blocking=True)
                 done = torch.cuda.Event()
                 done.record(self.copy)
-            slot["done"] = done
-            last_done[cls] = done
             inflight.append((slot, nxt, b, lo, hi, done))
             log.append((nxt, b))
             nxt = b

@@ -44,7 +44,7 @@ def _measure(key_bits, NS, sv, preload_keys, preload_vals, batches, max_batch, r
         run.run(ops, keys, aux)
     run.synchronize()
     for ops, keys, aux in batches:                          # capture every class used
-        run._class(int(keys.numel()))
+        run.graph_for(run.size_for(int(keys.numel())))
     t0 = time.perf_counter()
     for ops, keys, aux in batches:
         run.run(ops, keys, aux)

@@ -315,32 +315,29 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
     cum = np.cumsum(np.array(mix) / np.sum(mix))
 
     def batches():
-        next_fresh = n_preload
-        inserted = []
+        # the keys inserted so far are universe counters [n_preload, n_preload + n_ins): sampling
+        # "preload or earlier insert" is sampling a counter below n_preload + n_ins
+        n_ins = 0
+        miss_ctr = 0
         for b, m in enumerate(sizes):
             m = int(m)
             u = uniform01(seed, 10 + 3 * b, m)
             ops = np.searchsorted(cum, u, side="right").astype(np.uint8) + 1
             ops = np.minimum(ops, OP_DELETE).astype(np.uint8)
-            keys = np.empty(m, dtype=dt)
             aux = np.zeros(m, dtype=dt)
             w = _stream_words(seed, 11 + 3 * b, 3 * m)
-            pool_n = n_preload + sum(len(x) for x in inserted)
-            src = (w[:m] % np.uint64(pool_n)).astype(np.int64)
-            known = src < n_preload
-            kk = np.empty(m, dtype=np.uint64)
-            kk[known] = pre[src[known]].astype(np.uint64) if known.any() else kk[known]
-            if (~known).any():
-                allins = np.concatenate(inserted) if inserted else np.empty(0, dtype=dt)
-                kk[~known] = allins[src[~known] - n_preload].astype(np.uint64)
+            src = w[:m] % np.uint64(n_preload + n_ins)
+            kk = universe_at(kw, seed, src).astype(np.uint64)
             hit = (w[m:2 * m] >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53)) < hit_rate
-            miss_keys = universe(kw, seed ^ 0x5A5A, next_fresh, next_fresh + m)
+            miss_keys = universe(kw, seed ^ 0x5A5A, miss_ctr, miss_ctr + m)
+            miss_ctr += m
             kk = np.where(hit, kk, miss_keys.astype(np.uint64))
             is_ins = ops == OP_INSERT
-            fresh = universe(kw, seed, next_fresh, next_fresh + int(is_ins.sum()))
-            next_fresh += m
+            k_ins = int(is_ins.sum())
+            fresh = universe(kw, seed, n_preload + n_ins, n_preload + n_ins + k_ins)
+            n_ins += k_ins
             kk[is_ins] = fresh.astype(np.uint64)
-            keys[:] = kk.astype(dt)
+            keys = kk.astype(dt)
             aux[is_ins] = values_for(kw, fresh, salt=b + 7)
             is_rng = ops == OP_RANGE
             span = ((w[2 * m:] % np.uint64(max_len)).astype(np.uint64) + np.uint64(1)) * np.uint64(gap)
@@ -349,7 +346,6 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
             hi = np.where(hi < kk, np.uint64(key_max(kw) - 1), hi)          # 64-bit wrap
             hi = np.minimum(hi, np.uint64(key_max(kw) - 1))
             aux[is_rng] = hi[is_rng].astype(dt)
-            inserted.append(fresh)
             yield ops, keys, aux
 
     return dict(kw=kw, preload_keys=pre, preload_vals=values_for(kw, pre), sizes=sizes,
