@@ -270,7 +270,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flix", choices=["flix", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served"],
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "update_heavy"],
                     help="plain: the read-scale step (default); batched: mixed-batch stream through CUDA "
                          "graphs vs plain launches; served: continuous batching under Poisson arrivals")
     ap.add_argument("--batches", type=int, default=300, help="batched form: stream length")
@@ -287,6 +287,8 @@ def main():
         return bench_batched(args)
     if args.form == "served":
         return bench_served(args)
+    if args.form == "update_heavy":
+        return bench_update_heavy(args)
 
     import torch
     rank, world, local = dist_env()
@@ -579,6 +581,75 @@ def bench_served(args):
                                    "floor(2^U(0,12)) ops, 80/10/10 lookup/insert/delete over Zipf(0.9)" % (pbits, ubits),
                        "node_size": 64, "depth": 2},
             "loads": loads, "plain_per_request": plain}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_update_heavy(args):
+    """uint32 keys, node size 32, start empty: 64 insert batches of 2^20 keys per distribution
+    (uniform, Zipf(0.99) over 2^30 scrambled and dense, sorted-sequential) with the restructure policy
+    (nodes > 2 * buckets or a chain > 64), then 32 delete batches removing a random 50%, then a final
+    restructure.  Reports throughput, restructures, bytes per key after each phase and the share of
+    nodes the final restructure recovers (the quantity of the paper's Tab. 4)."""
+    import torch
+    import paper_2604_16725_gb300 as fx
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    out = {}
+    n_batches = args.batches if args.batches != 300 else 64
+    for dist in ("uniform", "zipf", "zipf_dense", "sequential"):
+        ins, deletes = W.update_heavy(dist, seed=3000, n_batches=n_batches, batch=1 << 20)
+        idx = fx.Index(key_bits=32, node_size=32)
+        st = torch.cuda.Stream()
+        dev = [(torch.from_numpy(k.view(np.int32)).cuda(), torch.from_numpy(v.view(np.int32)).cuda()) for k, v in ins]
+        torch.cuda.synchronize()
+        t_ins = t_res = 0.0
+        n_res = 0
+        for k, v in dev:
+            t0 = time.perf_counter()
+            idx.insert(k, v, stream=st)
+            st.synchronize()
+            t_ins += time.perf_counter() - t0
+            s_ = idx.stats(stream=st)
+            if s_["nodes_used"] > 2 * s_["buckets"] or s_["max_chain"] > 64:
+                t0 = time.perf_counter()
+                idx.restructure(stream=st)
+                st.synchronize()
+                t_res += time.perf_counter() - t0
+                n_res += 1
+        s_ins = idx.stats(stream=st)
+        stored, _ = idx.export(stream=st)
+        dels = [torch.from_numpy(d.view(np.int32)).cuda() for d in deletes(stored.cpu().numpy().view(np.uint32))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d in dels:
+            idx.delete(d, stream=st)
+        st.synchronize()
+        t_del = time.perf_counter() - t0
+        s_del = idx.stats(stream=st)
+        t0 = time.perf_counter()
+        idx.restructure(stream=st)
+        st.synchronize()
+        t_fin = time.perf_counter() - t0
+        s_fin = idx.stats(stream=st)
+        bpk = lambda s: s["used_bytes"] / max(s["live_keys"], 1)  # noqa: E731
+        n_ins_ops = sum(int(k.numel()) for k, _ in dev)
+        n_del_ops = sum(int(d.numel()) for d in dels)
+        out[dist] = {"insert_mops": n_ins_ops / t_ins / 1e6, "restructures": n_res, "restructure_ms_total": t_res * 1e3,
+                     "delete_mops": n_del_ops / t_del / 1e6, "final_restructure_ms": t_fin * 1e3,
+                     "keys_after_inserts": s_ins["live_keys"], "bytes_per_key_after_inserts": bpk(s_ins),
+                     "bytes_per_key_after_deletes": bpk(s_del), "bytes_per_key_after_restructure": bpk(s_fin),
+                     "nodes_after_deletes": s_del["nodes_used"], "nodes_after_restructure": s_fin["nodes_used"],
+                     "nodes_recovered_pct": 100.0 * (s_del["nodes_used"] - s_fin["nodes_used"]) / max(s_del["nodes_used"], 1)}
+        log("%s: %s" % (dist, out[dist]))
+        idx.close()
+        del dev, dels
+        torch.cuda.empty_cache()
+    line = {"form": "update_heavy", "metric": METRIC, "value": out["uniform"]["insert_mops"], "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "update heavy: uint32, node size 32, start empty; %d insert batches of 2^20 per "
+                                   "distribution, then 32 delete batches removing 50%%, final restructure" % n_batches},
+            "distributions": out}
     print(json.dumps(line))
     return 0
 

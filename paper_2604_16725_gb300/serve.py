@@ -52,6 +52,13 @@ class Server:
                 consumed=torch.cuda.Event()))
         self.per_insert = 1 if idx.node_size >= 4 else 2
         self.budget = self._free_nodes()
+        self.warmup()
+
+    def warmup(self):
+        """Capture every size class's graph now, so that no request waits for a capture."""
+        for s in self.runner.sizes:
+            self.runner.graph_for(s)
+        self.compute.synchronize()
 
     def _free_nodes(self) -> int:
         self.runner.check()
@@ -109,6 +116,7 @@ class Server:
                 if need > self.budget:                 # even one request does not fit: grow the pool
                     self.idx.reserve(self.max_batch, need + self.budget + (1 << 20), stream=self.compute)
                     self.runner.invalidate()
+                    self.warmup()
                     self.budget = self._free_nodes()
             hi = int(req_off[b])
             n = hi - lo
