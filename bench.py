@@ -366,14 +366,13 @@ def main():
 
     # roofline of the dominant kernel: the radix-sort scatter pass
     peak, peak_kind = measured_peaks()
-    down = prof.get("sort_onesweep", {"launches": 0, "ms": 0.0})
-    # algorithmic bytes of the scatter passes of one step (8 passes per sort, 64-bit keys, 32-bit payload):
-    # first pass reads keys only (payload = position), later passes read key+payload; all write key+payload
+    down = prof.get("sort_onesweep", {"launches": 0, "ms": 0.0, "bytes": 0.0})
+    # algorithmic bytes of the scatter passes the sort plans ran, as the library counts them per launch:
+    # the first pass of a sort reads keys only (payload = position), later passes read key+payload, all
+    # write key+payload (64-bit keys, 32-bit payload); passes the plan leaves out are "sort_pass_idle"
     ks = 8
-    sort_items = [1 << LOG_Q, 1 << LOG_Q, 1 << LOG_R, 1 << LOG_U, 1 << LOG_U]
-    step_bytes = sum(n * ((ks) + (ks + 4)) + 7 * n * (2 * (ks + 4)) for n in sort_items)
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else "sort_onesweep"
-    achieved = step_bytes * args.steps / (down["ms"] * 1e-3) / 1e9 if down["ms"] else 0.0
+    achieved = down["bytes"] / (down["ms"] * 1e-3) / 1e9 if down["ms"] else 0.0
     tr = traffic_record("sort_onesweep")
     traffic = None
     if tr:

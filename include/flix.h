@@ -121,7 +121,7 @@ int flix_lookup(flix_t h, const void* d_keys, uint64_t n, void* d_vals_out, uint
  * allocator this library cannot see.  Same arguments and results as flix_lookup.
  * Its scratch (sort buffers and bucket offsets) is one fixed array of FLIX_NOALLOC_SCRATCH_BYTES
  * compiled into the library; every GPU that loads the library holds it until the process exits.
- * A call needs about 28*n bytes (uint64 keys; 20*n for uint32) plus a few KB, whatever the index
+ * A call needs about 31*n bytes (uint64 keys; 22*n for uint32) plus a few KB, whatever the index
  * size, so up to about 2^19 uint64 keys per call fit; a larger request returns
  * FLIX_EINVAL before launching anything (flix_last_error gives the sizes).  The first call on a
  * device looks up the array's device address on that device, so make it before any stream capture.
@@ -207,12 +207,15 @@ int flix_dump_layout(flix_t h, uint64_t* h_counts, void* h_mkba, uint32_t* h_cha
                      void* stream);
 
 /* Per-kernel timing.  While enabled, every kernel launch of h is bracketed by CUDA events on the
- * launch stream.  flix_profile_read synchronises and returns up to max_entries rows: kernel name
- * (NUL-terminated, 48 bytes per row in h_names), launch count and total milliseconds. */
+ * launch stream (and a batch sort reads its pass plan back, so that passes the plan leaves out are
+ * listed as "sort_pass_idle").  flix_profile_read synchronises and returns up to max_entries rows:
+ * kernel name (NUL-terminated, 48 bytes per row in h_names), launch count, total milliseconds and
+ * total algorithmic bytes (the bytes the launches must move by definition, for kernels where the
+ * host knows them, else 0).  Any output array may be NULL. */
 int flix_profile_enable(flix_t h, int enable);
 int flix_profile_reset(flix_t h);
 int flix_profile_read(flix_t h, uint32_t max_entries, char* h_names, uint64_t* h_launches,
-                      double* h_total_ms, uint32_t* h_n_entries);
+                      double* h_total_ms, double* h_bytes, uint32_t* h_n_entries);
 
 /* Number of kernels h has launched since creation. */
 uint64_t flix_launch_count(flix_t h);

@@ -11,7 +11,8 @@
 namespace flix {
 
 const char* kKernelNames[K_NUM] = {
-    "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep",
+    "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep", "sort_plan", "sort_pass_idle",
+    "sort_finish",
     "scan_partials", "scan_top", "scan_apply",
     "partition", "read_point", "range_count", "range_fill",
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
@@ -756,17 +757,18 @@ int flix_profile_reset(flix_t h)
 }
 
 int flix_profile_read(flix_t h, uint32_t max_entries, char* h_names, uint64_t* h_launches, double* h_total_ms,
-                      uint32_t* h_n_entries)
+                      double* h_bytes, uint32_t* h_n_entries)
 {
     if (!h) return FLIX_EINVAL;
     CK(cudaDeviceSynchronize());
     std::vector<uint64_t> cnt(K_NUM, 0);
-    std::vector<double> ms(K_NUM, 0.0);
+    std::vector<double> ms(K_NUM, 0.0), by(K_NUM, 0.0);
     for (const ProfRec& r : h->prof) {
         float t = 0.f;
         CK(cudaEventElapsedTime(&t, r.a, r.b));
         cnt[r.kid]++;
         ms[r.kid] += t;
+        by[r.kid] += r.bytes;
     }
     uint32_t k = 0;
     for (int i = 0; i < K_NUM; i++) {
@@ -778,6 +780,7 @@ int flix_profile_read(flix_t h, uint32_t max_entries, char* h_names, uint64_t* h
             }
             if (h_launches) h_launches[k] = cnt[i];
             if (h_total_ms) h_total_ms[k] = ms[i];
+            if (h_bytes) h_bytes[k] = by[i];
         }
         k++;
     }

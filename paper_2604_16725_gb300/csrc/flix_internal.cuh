@@ -20,7 +20,7 @@ constexpr uint32_t NIL = 0xFFFFFFFFu;
 enum Eff : uint32_t { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
 
 // Device error word bits (checked at the next synchronising call).
-enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u, ERR_SPIN = 16u };
+enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u, ERR_SPIN = 16u, ERR_SORT = 32u };
 
 template <class K>
 __host__ __device__ constexpr K key_max() { return static_cast<K>(~K(0)); }
@@ -44,7 +44,7 @@ struct DevIdx {
 };
 
 enum KernelId {
-    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP,
+    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP, K_SORT_PLAN, K_SORT_IDLE, K_SORT_FINISH,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
     K_PARTITION, K_READ_POINT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
@@ -74,7 +74,20 @@ struct Arena {
 
 struct ProfRec {
     int kid;
+    double bytes;   // algorithmic bytes the launch moves, where the host knows them (else 0)
     cudaEvent_t a, b;
+};
+
+// Device-side plan of one batch sort (written by the plan kernel, read by the passes and the
+// finish kernels): passes shift[0..npass) in LSD order; finish = 1 when groups of keys equal under
+// pmask still need sorting; nbig and cursor count and hand out the long groups.
+struct SortPlan {
+    uint32_t npass;
+    uint32_t finish;
+    uint32_t shift[8];
+    unsigned long long pmask;
+    unsigned long long nbig;
+    unsigned long long cursor;
 };
 
 // Device-resident allocator and admission state of a handle.  free_top is authoritative on the
@@ -142,8 +155,9 @@ struct Ctx {
 
 cudaEvent_t prof_event(flix_index* h);
 
+// Launch with profiling hooks; `bytes` = the launch's algorithmic bytes for the per-kernel roofline.
 template <class Kern, class... Args>
-cudaError_t launch(Ctx& c, int kid, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
+cudaError_t launch_b(Ctx& c, int kid, double bytes, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
 {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
     cudaEvent_t a = nullptr, b = nullptr;
@@ -156,10 +170,16 @@ cudaError_t launch(Ctx& c, int kid, dim3 grid, dim3 block, size_t smem, Kern ker
     cudaError_t e = cudaGetLastError();
     if (c.h->prof_on) {
         cudaEventRecord(b, c.st);
-        c.h->prof.push_back(ProfRec{kid, a, b});
+        c.h->prof.push_back(ProfRec{kid, bytes, a, b});
     }
     c.h->launches++;
     return e;
+}
+
+template <class Kern, class... Args>
+cudaError_t launch(Ctx& c, int kid, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
+{
+    return launch_b(c, kid, 0.0, grid, block, smem, kern, args...);
 }
 
 inline uint32_t div_up(uint64_t a, uint64_t b) { return static_cast<uint32_t>((a + b - 1) / b); }
@@ -188,8 +208,9 @@ DevIdx<K> dev_view(flix_index* h)
 template <class K>
 size_t sort_scratch_bytes(uint64_t n);
 
-// Stable LSD radix sort of (key, payload) pairs by key, ascending.  vin == nullptr means the
-// payload is the item's position (0..n-1).  Output in kout/vout.  Scratch from the arena.
+// Stable sort of the keys kin[0..n) with their positions: kout ascending, vout[i] = input position
+// of kout[i] (equal keys keep input order).  vin must be nullptr (the payload is the position) and
+// n < 2^32 - 1.  Scratch from the arena.
 template <class K>
 cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, uint64_t n);
 

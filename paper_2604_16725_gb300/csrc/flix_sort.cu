@@ -1,13 +1,17 @@
 // Batch sort (Sec. 3.3: each batch is sorted by key before buckets pull their operations; Tab. 1
 // times it) and prefix-sum primitives.
 //
-// The sort is a stable least-significant-digit radix sort of (key, payload) pairs with 8-bit
-// digits.  One read of the keys builds the digit histograms of every pass.  Each pass is one
-// scatter kernel over 4096-item tiles (512 threads x 8 items, two blocks per SM): a tile ranks its
-// items in shared memory with warp match/popc (stable: warp-striped items ranked in warp, item,
-// lane order), learns where each digit's run of this tile starts in the output, and writes the
-// locally sorted tile so that each digit's run is a contiguous store.  The start of each
-// (digit, tile) run comes either from
+// The sort is a stable least-significant-digit radix sort of (key, position) pairs with 8-bit
+// digits.  One read of the keys builds the digit histograms of every digit position, and a plan
+// kernel picks the passes from them on the device: digits that are the same in every key are
+// skipped, and when the highest few varying digits already split the batch into groups of about a
+// quarter item, only those are sorted and a finish kernel sorts each group of equal prefix in
+// place (for 2^24 uniform 64-bit keys: 4 passes instead of 8).  Each pass is one scatter kernel
+// over 4096-item tiles (512 threads x 8 items, two blocks per SM): a tile ranks its items in
+// shared memory (peers of a digit from 8 warp ballots, one per digit bit; stable: warp-striped
+// items ranked in warp, item, lane order), learns where each digit's run of this tile starts in
+// the output, and writes the locally sorted tile so that each digit's run is a contiguous store.
+// The start of each (digit, tile) run comes either from
 //   - one-sweep (after the single-pass "Onesweep" radix sort of Adinets and Merrill, 2022): every
 //     tile publishes its per-digit counts and looks back through the published states of earlier
 //     tiles (an aggregate, or an inclusive prefix that ends the walk), reading 8 earlier tiles per
@@ -100,21 +104,79 @@ __global__ void __launch_bounds__(256) k_hist_all(const K* __restrict__ keys, ui
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// In place: hist[p * RADIX + d] becomes the number of items whose pass-p digit is below d.
-__global__ void __launch_bounds__(RADIX) k_digit_bases(uint32_t* __restrict__ hist)
+// Stable rank of each lane's item among the warp's lanes with the same digit: the peer mask is
+// built from NB ballots, one per digit bit (NB = 9 when the digit value RADIX marks a lane
+// without an item).
+template <int NB>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d)
 {
-    __shared__ uint32_t sw[RADIX / 32];
-    uint32_t* h = hist + (size_t)blockIdx.x * RADIX;
-    uint32_t tot;
-    const uint32_t b = block_excl_scan<uint32_t, RADIX / 32>(h[threadIdx.x], sw, tot);
-    h[threadIdx.x] = b;
+    uint32_t peers = FULL;
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(FULL, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
+// Ranks the warp's OS_ITEMS x 32 items (item i of lane l is the warp's (i * 32 + l)-th) by digit:
+// rank[i] = items of the same digit earlier in the warp; wh[d] ends as the warp's count of digit d.
+// FULLT: every item is valid (no bounds test, 8 ballots).
+template <class K, bool FULLT>
+__device__ __forceinline__ void rank_warp(const K (&key)[OS_ITEMS], uint32_t (&rank)[OS_ITEMS], uint16_t* wh,
+                                          uint64_t wbase, uint64_t n, int shift)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < OS_ITEMS; i++) {
+        const uint32_t d = (FULLT || wbase + (uint64_t)i * 32 + lane < n) ? digit_of(key[i], shift) : RADIX;
+        const uint32_t peers = digit_peers<FULLT ? 8 : 9>(d);
+        const uint32_t leader = __ffs(peers) - 1;
+        const bool lead = lane == leader && (FULLT || d < RADIX);
+        uint32_t prior = 0;
+        if (lead) prior = wh[d];
+        prior = __shfl_sync(FULL, prior, leader);
+        rank[i] = prior + __popc(peers & lt);
+        if (lead) wh[d] = static_cast<uint16_t>(prior + __popc(peers));
+        __syncwarp();
+    }
+}
+
+// Where pass `pass` of a plan with np passes reads and writes: passes alternate between the output
+// pair and the scratch pair so that the last one writes the output; the first reads the input with
+// payload = position.
+template <class K>
+struct PassBufs {
+    const K* kin;
+    const uint32_t* vin;
+    K* kout;
+    uint32_t* vout;
+};
+template <class K>
+__device__ __forceinline__ PassBufs<K> pass_bufs(int pass, uint32_t np, const K* kin, K* kout, uint32_t* vout, K* tk,
+                                                 uint32_t* tv)
+{
+    const bool to_out = ((np - 1 - (uint32_t)pass) & 1u) == 0;
+    PassBufs<K> b;
+    b.kout = to_out ? kout : tk;
+    b.vout = to_out ? vout : tv;
+    b.kin = pass == 0 ? kin : (to_out ? tk : kout);
+    b.vin = pass == 0 ? nullptr : (to_out ? tv : vout);
+    return b;
 }
 
 // Reduce-then-scan: per-tile digit counts of one pass, counts[d * T + tile].
 template <class K>
-__global__ void __launch_bounds__(UP_THREADS_S) k_upsweep(const K* __restrict__ keys, uint64_t n, int shift,
+__global__ void __launch_bounds__(UP_THREADS_S) k_upsweep(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv,
+                                                          uint64_t n, int pass, const SortPlan* __restrict__ plan,
                                                           uint32_t* __restrict__ counts, uint32_t T)
 {
+    const uint32_t np = plan->npass;
+    if ((uint32_t)pass >= np) return;
+    const int shift = plan->shift[pass];
+    const K* keys = pass_bufs<K>(pass, np, kin, kout, vout, tk, tv).kin;
     __shared__ uint32_t sh[RADIX];
     sh[threadIdx.x] = 0;
     __syncthreads();
@@ -122,9 +184,9 @@ __global__ void __launch_bounds__(UP_THREADS_S) k_upsweep(const K* __restrict__ 
     const uint32_t lane = threadIdx.x & 31;
 #pragma unroll 4
     for (int i = 0; i < UP_ITEMS; i++) {
-        uint64_t pos = base + (uint64_t)i * UP_THREADS_S + threadIdx.x;
-        uint32_t d = pos < n ? digit_of(keys[pos], shift) : RADIX;
-        uint32_t peers = __match_any_sync(FULL, d);
+        const uint64_t pos = base + (uint64_t)i * UP_THREADS_S + threadIdx.x;
+        const uint32_t d = pos < n ? digit_of(keys[pos], shift) : RADIX;
+        const uint32_t peers = digit_peers<9>(d);
         if (d < RADIX && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&sh[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
@@ -132,32 +194,40 @@ __global__ void __launch_bounds__(UP_THREADS_S) k_upsweep(const K* __restrict__ 
 }
 
 // Reduce-then-scan: offsets[d * T + t] = bases[d] + (items of digit d in tiles < t).
-__global__ void __launch_bounds__(256) k_scan_digits(const uint32_t* __restrict__ counts, uint32_t T,
+__global__ void __launch_bounds__(256) k_scan_digits(const uint32_t* __restrict__ counts, uint32_t T, int pass,
+                                                    const SortPlan* __restrict__ plan,
                                                     const uint32_t* __restrict__ bases, uint32_t* __restrict__ offsets)
 {
+    if ((uint32_t)pass >= plan->npass) return;
     __shared__ uint32_t sw[NWARPS];
     const uint32_t d = blockIdx.x;
-    uint32_t carry = bases[d];
+    uint32_t carry = bases[(plan->shift[pass] >> 3) * RADIX + d];
     for (uint32_t t0 = 0; t0 < T; t0 += 256) {
-        uint32_t t = t0 + threadIdx.x;
-        uint32_t c = t < T ? counts[(uint64_t)d * T + t] : 0u;
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t c = t < T ? counts[(uint64_t)d * T + t] : 0u;
         uint32_t tot;
-        uint32_t ex = block_excl_scan<uint32_t>(c, sw, tot);
+        const uint32_t ex = block_excl_scan<uint32_t>(c, sw, tot);
         if (t < T) offsets[(uint64_t)d * T + t] = carry + ex;
         carry += tot;
     }
 }
 
-// One digit pass.  vin == nullptr: payload = position.  LOOKBACK selects one-sweep (status,
-// tile_ctr) or reduce-then-scan (offsets).
+// One digit pass of the plan.  LOOKBACK selects one-sweep (status, tile_ctr) or reduce-then-scan
+// (offsets).  A pass beyond the plan's count returns at once.
 template <class K, bool LOOKBACK>
-__global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                         K* __restrict__ kout, uint32_t* __restrict__ vout, uint64_t n,
-                                                         int shift, const uint32_t* __restrict__ bases,
+__global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv,
+                                                         uint64_t n, int pass, const SortPlan* __restrict__ plan,
+                                                         const uint32_t* __restrict__ bases,
                                                          const uint32_t* __restrict__ offsets, uint32_t T,
                                                          uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
                                                          uint32_t* __restrict__ err)
 {
+    const uint32_t np = plan->npass;
+    if ((uint32_t)pass >= np) return;
+    const int shift = plan->shift[pass];
+    const PassBufs<K> io = pass_bufs<K>(pass, np, kin, kout, vout, tk, tv);
+    bases += (shift >> 3) * RADIX;
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* sk = reinterpret_cast<K*>(smem_raw);
     uint32_t* sv = reinterpret_cast<uint32_t*>(sk + OS_TILE);
@@ -172,6 +242,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ k
     const uint32_t tile = LOOKBACK ? *s_tile : blockIdx.x;
     const uint64_t base = (uint64_t)tile * OS_TILE;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool full_tile = base + OS_TILE <= n;
 
     K key[OS_ITEMS];
     uint32_t val[OS_ITEMS];
@@ -179,25 +250,13 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ k
     const uint64_t wbase = base + (uint64_t)warp * 32 * OS_ITEMS;
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; i++) {
-        uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-        bool ok = pos < n;
-        key[i] = ok ? kin[pos] : K(0);
-        val[i] = ok ? (vin ? vin[pos] : static_cast<uint32_t>(pos)) : 0u;
+        const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+        const bool ok = full_tile || pos < n;
+        key[i] = ok ? io.kin[pos] : K(0);
+        val[i] = ok ? (io.vin ? io.vin[pos] : static_cast<uint32_t>(pos)) : 0u;
     }
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < OS_ITEMS; i++) {
-        uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-        uint32_t d = pos < n ? digit_of(key[i], shift) : RADIX;
-        uint32_t peers = __match_any_sync(FULL, d);
-        uint32_t leader = __ffs(peers) - 1;
-        uint32_t prior = 0;
-        if (lane == leader && d < RADIX) prior = whist[warp * RADIX + d];
-        prior = __shfl_sync(FULL, prior, leader);
-        rank[i] = prior + __popc(peers & lt);
-        if (lane == leader && d < RADIX) whist[warp * RADIX + d] = (uint16_t)(prior + __popc(peers));
-        __syncwarp();
-    }
+    if (full_tile) rank_warp<K, true>(key, rank, whist + warp * RADIX, wbase, n, shift);
+    else rank_warp<K, false>(key, rank, whist + warp * RADIX, wbase, n, shift);
     __syncthreads();
     uint32_t cnt = 0;
     if (threadIdx.x < RADIX) {
@@ -205,7 +264,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ k
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < OS_WARPS; w++) {
-            uint32_t c = whist[w * RADIX + d];
+            const uint32_t c = whist[w * RADIX + d];
             whist[w * RADIX + d] = (uint16_t)run;
             run += c;
         }
@@ -255,10 +314,10 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ k
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < OS_ITEMS; i++) {
-        uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-        if (pos < n) {
-            uint32_t d = digit_of(key[i], shift);
-            uint32_t r = whist[warp * RADIX + d] + rank[i];
+        const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+        if (full_tile || pos < n) {
+            const uint32_t d = digit_of(key[i], shift);
+            const uint32_t r = whist[warp * RADIX + d] + rank[i];
             sk[r] = key[i];
             sv[r] = val[i];
         }
@@ -266,10 +325,10 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* __restrict__ k
     __syncthreads();
     const uint32_t tile_n = (uint32_t)((n - base) < (uint64_t)OS_TILE ? (n - base) : OS_TILE);
     for (uint32_t j = threadIdx.x; j < tile_n; j += OS_THREADS) {
-        K k = sk[j];
-        uint32_t o = goff[digit_of(k, shift)] + j;
-        kout[o] = k;
-        vout[o] = sv[j];
+        const K k = sk[j];
+        const uint32_t o = goff[digit_of(k, shift)] + j;
+        io.kout[o] = k;
+        io.vout[o] = sv[j];
     }
 }
 
@@ -277,6 +336,286 @@ template <class K>
 size_t sweep_smem()
 {
     return (size_t)OS_TILE * (sizeof(K) + 4) + (size_t)OS_WARPS * RADIX * 2 + (RADIX + OS_WARPS + 4) * 4;
+}
+
+// ---- pass plan -----------------------------------------------------------------------------------
+//
+// A digit whose histogram has one bin holding every item is the same in every key and orders
+// nothing.  Of the others, the plan sorts by all of them (LSD order), unless a prefix of the
+// highest h of them already splits the batch into groups of about 4n / 2^(8h) <= 1/4 item on
+// average; then it sorts by that prefix only and leaves the groups of equal prefix to the finish
+// kernels.  A digit whose fullest bin holds more than 4x its uniform share (n/64 + 256 items) hints
+// at heavy keys, whose groups would be long: the plan then sorts by every digit.  In place, hist
+// rows become the digit bases (items with a smaller digit) of every digit position.
+template <class K>
+__global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist, uint64_t n, uint32_t h,
+                                                      SortPlan* __restrict__ plan)
+{
+    constexpr int P = sizeof(K);
+    __shared__ uint32_t sw[RADIX / 32];
+    __shared__ uint32_t s_const[P], s_max[P];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = 0; p < P; p++) {
+        uint32_t* hp = hist + (size_t)p * RADIX;
+        const uint32_t c = hp[threadIdx.x];
+        const int all_one_bin = __syncthreads_or((uint64_t)c == n);
+        uint32_t m = c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+        if (lane == 0) sw[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t mm = 0;
+            for (int w = 0; w < RADIX / 32; w++) mm = max(mm, sw[w]);
+            s_max[p] = mm;
+            s_const[p] = all_one_bin;
+        }
+        __syncthreads();
+        uint32_t tot;
+        hp[threadIdx.x] = block_excl_scan<uint32_t, RADIX / 32>(c, sw, tot);
+    }
+    if (threadIdx.x != 0) return;
+    int nc[P];
+    int m = 0;
+    for (int p = P - 1; p >= 0; p--)
+        if (!s_const[p]) nc[m++] = p;   // non-constant digits, most significant first
+    SortPlan pl;
+    pl.finish = 0;
+    pl.pmask = ~0ull;
+    pl.nbig = 0;
+    pl.cursor = 0;
+    for (int q = 0; q < 8; q++) pl.shift[q] = 0;
+    if (m == 0) {          // every key equal: one stable pass copies the batch to the output
+        pl.npass = 1;
+    } else {
+        int use = m;
+        if ((int)h < m) {
+            bool heavy = false;
+            for (int q = 0; q < (int)h; q++) heavy |= (uint64_t)s_max[nc[q]] > n / 64 + 256;
+            if (!heavy) {
+                use = (int)h;
+                pl.finish = 1;
+                pl.pmask = ~0ull << (8 * nc[use - 1]);
+            }
+        }
+        pl.npass = (uint32_t)use;
+        for (int q = 0; q < use; q++) pl.shift[q] = 8 * nc[use - 1 - q];
+    }
+    *plan = pl;
+}
+
+// ---- finishing the groups of equal prefix ----------------------------------------------------------
+//
+// After the prefix passes the batch is ordered by prefix, and inside a group of equal prefix by
+// position (the passes are stable).  The payload is the item's position in the input, so the
+// order the sort must produce is (key, payload) ascending, a strict total order; each group is
+// sorted by it in place.  Groups of up to SMALL_SEG items are sorted by the thread at their head;
+// longer ones are listed and sorted by a block each (bitonic in shared memory up to OS_TILE items,
+// beyond that a chunked stable radix sort of the digits under the prefix, through the scratch pair).
+
+constexpr int SMALL_SEG = 8;
+
+template <class K>
+__device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
+{
+    return ka < kb || (ka == kb && va < vb);
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals, uint64_t n,
+                                                     SortPlan* __restrict__ plan, uint64_t* __restrict__ list,
+                                                     uint64_t list_cap, uint32_t* __restrict__ err)
+{
+    if (!plan->finish) return;
+    const uint64_t pm = plan->pmask;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const K k0 = keys[i];
+        if (i > 0 && ((static_cast<uint64_t>(keys[i - 1] ^ k0) & pm) == 0)) continue;   // not a group head
+        uint32_t L = 1;
+        while (L <= SMALL_SEG && i + L < n && (static_cast<uint64_t>(keys[i + L] ^ k0) & pm) == 0) L++;
+        if (L == 1) continue;
+        if (L > SMALL_SEG) {
+            const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
+            if (slot < list_cap) list[slot] = i;
+            else atomicOr(err, ERR_SORT);
+            continue;
+        }
+        K sk[SMALL_SEG];
+        uint32_t sv[SMALL_SEG];
+#pragma unroll
+        for (int a = 0; a < SMALL_SEG; a++) {
+            if (a < (int)L) {
+                sk[a] = keys[i + a];
+                sv[a] = vals[i + a];
+            }
+        }
+        // insertion sort; every index is a constant after unrolling, so the group stays in registers
+#pragma unroll
+        for (int a = 1; a < SMALL_SEG; a++) {
+            if (a < (int)L) {
+#pragma unroll
+                for (int b = a; b > 0; b--) {
+                    if (kv_less(sk[b], sv[b], sk[b - 1], sv[b - 1])) {
+                        const K tk = sk[b]; sk[b] = sk[b - 1]; sk[b - 1] = tk;
+                        const uint32_t tv = sv[b]; sv[b] = sv[b - 1]; sv[b - 1] = tv;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < SMALL_SEG; a++) {
+            if (a < (int)L) {
+                keys[i + a] = sk[a];
+                vals[i + a] = sv[a];
+            }
+        }
+    }
+}
+
+// One block per listed group, taken from a shared cursor.
+template <class K>
+__global__ void __launch_bounds__(OS_THREADS, 1) k_sort_finish_big(K* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                                   K* __restrict__ tk, uint32_t* __restrict__ tv,
+                                                                   uint64_t n, SortPlan* __restrict__ plan,
+                                                                   const uint64_t* __restrict__ list, uint64_t list_cap)
+{
+    if (!plan->finish) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K* sk = reinterpret_cast<K*>(smem_raw);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(sk + OS_TILE);
+    uint16_t* whist = reinterpret_cast<uint16_t*>(sv + OS_TILE);                // [OS_WARPS][RADIX]
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(whist + OS_WARPS * RADIX);    // [RADIX]
+    __shared__ unsigned long long s_item, s_end;
+    __shared__ uint32_t s_off[RADIX], s_base[RADIX], s_skip;
+    const uint64_t pm = plan->pmask;
+    const int lo_shift = plan->shift[0];
+    const uint64_t nbig = min((uint64_t)plan->nbig, list_cap);
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->cursor), 1ull);
+            s_end = n;
+        }
+        __syncthreads();
+        const uint64_t item = s_item;
+        if (item >= nbig) break;
+        const uint64_t start = list[item];
+        const K k0 = keys[start];
+        // the group ends at the first position whose prefix differs
+        for (uint64_t b = start + SMALL_SEG; b < n; b += OS_THREADS) {
+            const uint64_t j = b + threadIdx.x;
+            const bool stop = j < n && (static_cast<uint64_t>(keys[j] ^ k0) & pm) != 0;
+            if (stop) atomicMin(&s_end, (unsigned long long)j);
+            if (__syncthreads_or(stop)) break;
+        }
+        const uint64_t L = s_end - start;
+        if (L <= (uint64_t)OS_TILE) {
+            uint32_t P2 = 2;
+            while (P2 < L) P2 <<= 1;
+            for (uint32_t j = threadIdx.x; j < P2; j += OS_THREADS) {
+                const bool ok = j < L;
+                sk[j] = ok ? keys[start + j] : ~K(0);
+                sv[j] = ok ? vals[start + j] : 0xFFFFFFFFu;   // positions are below 2^32 - 1: padding sorts last
+            }
+            __syncthreads();
+            for (uint32_t k = 2; k <= P2; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t t = threadIdx.x; t < P2 / 2; t += OS_THREADS) {
+                        const uint32_t a = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                        const uint32_t b = a + j;
+                        const bool up = (a & k) == 0;
+                        const K ka = sk[a], kb = sk[b];
+                        const uint32_t va = sv[a], vb = sv[b];
+                        if (up ? kv_less(kb, vb, ka, va) : kv_less(ka, va, kb, vb)) {
+                            sk[a] = kb; sk[b] = ka;
+                            sv[a] = vb; sv[b] = va;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t j = threadIdx.x; j < L; j += OS_THREADS) {
+                keys[start + j] = sk[j];
+                vals[start + j] = sv[j];
+            }
+            __syncthreads();
+            continue;
+        }
+        // Long group: stable LSD over the digits under the prefix, chunk by chunk (chunks in order,
+        // items of a chunk ranked as in a sweep tile), between the group's range of the output
+        // pair and the same range of the scratch pair.
+        K* srck = keys + start;
+        uint32_t* srcv = vals + start;
+        K* dstk = tk + start;
+        uint32_t* dstv = tv + start;
+        for (int shift = 0; shift < lo_shift; shift += 8) {
+            for (int d = threadIdx.x; d < RADIX; d += OS_THREADS) s_cnt[d] = 0;
+            __syncthreads();
+            for (uint64_t j = threadIdx.x; j < L; j += OS_THREADS) atomicAdd(&s_cnt[digit_of(srck[j], shift)], 1u);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t run = 0, skip = 0;
+                for (int d = 0; d < RADIX; d++) {
+                    s_off[d] = run;
+                    skip |= (uint64_t)s_cnt[d] == L;
+                    run += s_cnt[d];
+                }
+                s_skip = skip;
+            }
+            __syncthreads();
+            if (s_skip) continue;    // one digit value in the whole group: the pass moves nothing
+            for (uint64_t c0 = 0; c0 < L; c0 += OS_TILE) {
+                for (int i = threadIdx.x; i < OS_WARPS * RADIX / 2; i += OS_THREADS)
+                    reinterpret_cast<uint32_t*>(whist)[i] = 0;
+                __syncthreads();
+                K key[OS_ITEMS];
+                uint32_t val[OS_ITEMS];
+                uint32_t rank[OS_ITEMS];
+                const uint64_t wb = c0 + (uint64_t)warp * 32 * OS_ITEMS;
+#pragma unroll
+                for (int i = 0; i < OS_ITEMS; i++) {
+                    const uint64_t pos = wb + (uint64_t)i * 32 + lane;
+                    key[i] = pos < L ? srck[pos] : K(0);
+                    val[i] = pos < L ? srcv[pos] : 0u;
+                }
+                rank_warp<K, false>(key, rank, whist + warp * RADIX, wb, L, shift);
+                __syncthreads();
+                if (threadIdx.x < RADIX) {
+                    const uint32_t d = threadIdx.x;
+                    uint32_t run = 0;
+                    for (int w = 0; w < OS_WARPS; w++) {
+                        const uint32_t c = whist[w * RADIX + d];
+                        whist[w * RADIX + d] = (uint16_t)run;
+                        run += c;
+                    }
+                    s_base[d] = s_off[d];
+                    s_off[d] += run;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < OS_ITEMS; i++) {
+                    const uint64_t pos = wb + (uint64_t)i * 32 + lane;
+                    if (pos < L) {
+                        const uint32_t d = digit_of(key[i], shift);
+                        const uint64_t o = (uint64_t)s_base[d] + whist[warp * RADIX + d] + rank[i];
+                        dstk[o] = key[i];
+                        dstv[o] = val[i];
+                    }
+                }
+                __syncthreads();
+            }
+            K* t0 = srck; srck = dstk; dstk = t0;
+            uint32_t* t1 = srcv; srcv = dstv; dstv = t1;
+        }
+        if (srck != keys + start) {
+            for (uint64_t j = threadIdx.x; j < L; j += OS_THREADS) {
+                keys[start + j] = srck[j];
+                vals[start + j] = srcv[j];
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ---- exclusive scan ----------------------------------------------------------------------------
@@ -373,13 +712,26 @@ size_t sort_scratch_bytes(uint64_t n)
     const size_t pingpong = al(n * sizeof(K)) + al(n * 4);
     const size_t rts = 2 * al(T * RADIX * 4);                      // counts, offsets
     const size_t one = al(P * T * RADIX * 4) + al(P * 4);          // tile states, tile counters
-    return pingpong + al(P * RADIX * 4) + (rts > one ? rts : one) + 1024;
+    const size_t fin = al(sizeof(SortPlan)) + al((n / (SMALL_SEG + 1) + 1) * 8);   // plan, long-group list
+    return pingpong + al(P * RADIX * 4) + (rts > one ? rts : one) + fin + 1024;
+}
+
+// Prefix digits the plan may stop at: the fewest h with 2^(8h) >= 4n.
+template <class K>
+static uint32_t prefix_digits(uint64_t n)
+{
+    uint32_t h = 1;
+    while (h < sizeof(K) && (8 * h >= 64 || (1ull << (8 * h)) < 4 * n)) h++;
+    return h;
 }
 
 template <class K>
 cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, uint64_t n)
 {
     if (n == 0) return cudaSuccess;
+    // the payload is the input position: it is what makes (key, payload) a strict order for the
+    // finish kernels, and positions must stay below 2^32 - 1
+    if (vin != nullptr || n >= 0xFFFFFFFFull) return cudaErrorInvalidValue;
     constexpr int P = sizeof(K);
     Arena& A = c.h->arena;
     // one-sweep unless asked otherwise; 30-bit tile states need n < 2^30
@@ -392,7 +744,10 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     uint32_t* offsets = onesweep ? nullptr : A.take<uint32_t>((size_t)T * RADIX);
     K* tk = A.take<K>(n);
     uint32_t* tv = A.take<uint32_t>(n);
-    if (!bases || !tk || !tv || (onesweep ? (!status || !tile_ctr) : (!counts || !offsets)))
+    SortPlan* plan = A.take<SortPlan>(1);
+    const uint64_t list_cap = n / (SMALL_SEG + 1) + 1;
+    uint64_t* list = A.take<uint64_t>(list_cap);
+    if (!bases || !tk || !tv || !plan || !list || (onesweep ? (!status || !tile_ctr) : (!counts || !offsets)))
         return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMemsetAsync(bases, 0, P * RADIX * 4, c.st);
     if (e) return e;
@@ -405,37 +760,54 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     uint32_t hg = div_up(n, 256);
     if (hg > (uint32_t)nsm * 8) hg = nsm * 8;
     if ((e = launch(c, K_SORT_HIST, dim3(hg), dim3(256), 0, k_hist_all<K>, kin, n, bases))) return e;
-    if ((e = launch(c, K_SORT_SCAN, dim3(P), dim3(RADIX), 0, k_digit_bases, bases))) return e;
+    if ((e = launch(c, K_SORT_PLAN, dim3(1), dim3(RADIX), 0, k_sort_plan<K>, bases, n, prefix_digits<K>(n), plan)))
+        return e;
+    // The plan's pass count lives on the device; every possible pass is launched and those beyond
+    // it return at once.  When profiling, the count is read back so that idle passes are timed
+    // under their own name.
+    uint32_t active = P;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(c.st, &cap))) return e;
+    if (c.h->prof_on && cap == cudaStreamCaptureStatusNone) {
+        if ((e = cudaMemcpyAsync(&c.h->hpin[62], &plan->npass, 4, cudaMemcpyDeviceToHost, c.st))) return e;
+        if ((e = cudaStreamSynchronize(c.st))) return e;
+        memcpy(&active, &c.h->hpin[62], 4);
+    }
     const size_t smem = sweep_smem<K>();
     e = onesweep ? cudaFuncSetAttribute(k_sweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                  : cudaFuncSetAttribute(k_sweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    const K* sk = kin;
-    const uint32_t* sv = vin;
     for (int p = 0; p < P; p++) {
-        // the last pass writes kout; passes alternate between kout and the scratch pair
-        const bool to_out = ((P - 1 - p) & 1) == 0;
-        K* dk = to_out ? kout : tk;
-        uint32_t* dv = to_out ? vout : tv;
-        const int shift = 8 * p;
-        const uint32_t* bp = bases + p * RADIX;
+        const bool on = (uint32_t)p < active;
+        // algorithmic bytes: the first pass reads keys only (payload = position)
+        const double bytes = on ? (double)n * ((p == 0 ? sizeof(K) : sizeof(K) + 4) + sizeof(K) + 4) : 0.0;
         if (onesweep) {
-            e = launch(c, K_SORT_ONESWEEP, dim3(T), dim3(OS_THREADS), smem, k_sweep<K, true>, sk, sv, dk, dv, n, shift,
-                       bp, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX, tile_ctr + p, c.h->err);
+            e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem, k_sweep<K, true>,
+                         kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan, (const uint32_t*)bases,
+                         (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX, tile_ctr + p, c.h->err);
         } else {
-            e = launch(c, K_SORT_UP, dim3(T), dim3(UP_THREADS_S), 0, k_upsweep<K>, sk, n, shift, counts, T);
+            e = launch(c, on ? K_SORT_UP : K_SORT_IDLE, dim3(T), dim3(UP_THREADS_S), 0, k_upsweep<K>, kin, kout, vout,
+                       tk, tv, n, p, (const SortPlan*)plan, counts, T);
             if (!e)
-                e = launch(c, K_SORT_SCAN, dim3(RADIX), dim3(256), 0, k_scan_digits, (const uint32_t*)counts, T, bp,
-                           offsets);
+                e = launch(c, on ? K_SORT_SCAN : K_SORT_IDLE, dim3(RADIX), dim3(256), 0, k_scan_digits,
+                           (const uint32_t*)counts, T, p, (const SortPlan*)plan, (const uint32_t*)bases, offsets);
             if (!e)
-                e = launch(c, K_SORT_DOWN, dim3(T), dim3(OS_THREADS), smem, k_sweep<K, false>, sk, sv, dk, dv, n, shift,
-                           bp, (const uint32_t*)offsets, T, (uint32_t*)nullptr, (uint32_t*)nullptr, c.h->err);
+                e = launch_b(c, on ? K_SORT_DOWN : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem,
+                             k_sweep<K, false>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
+                             (const uint32_t*)bases, (const uint32_t*)offsets, T, (uint32_t*)nullptr,
+                             (uint32_t*)nullptr, c.h->err);
         }
         if (e) return e;
-        sk = dk;
-        sv = dv;
     }
-    return cudaSuccess;
+    uint32_t fg = div_up(n, 256);
+    if (fg > (uint32_t)nsm * 8) fg = nsm * 8;
+    if ((e = launch(c, K_SORT_FINISH, dim3(fg), dim3(256), 0, k_sort_finish<K>, kout, vout, n, plan, list, list_cap,
+                    c.h->err)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sort_finish_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    return launch(c, K_SORT_FINISH, dim3(nsm), dim3(OS_THREADS), smem, k_sort_finish_big<K>, kout, vout, tk, tv, n,
+                  plan, (const uint64_t*)list, list_cap);
 }
 
 template size_t sort_scratch_bytes<uint32_t>(uint64_t);

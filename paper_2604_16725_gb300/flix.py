@@ -63,7 +63,7 @@ SIGNATURES = {
     "flix_dump_layout": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "flix_profile_enable": (_INT, [_VP, _INT]),
     "flix_profile_reset": (_INT, [_VP]),
-    "flix_profile_read": (_INT, [_VP, _U32, _VP, _VP, _VP, _VP]),
+    "flix_profile_read": (_INT, [_VP, _U32, _VP, _VP, _VP, _VP, _VP]),
     "flix_launch_count": (_U64, [_VP]),
     "flix_strerror": (ctypes.c_char_p, [_INT]),
     "flix_last_error": (ctypes.c_char_p, [_VP]),
@@ -299,12 +299,13 @@ class Index:
         names = ctypes.create_string_buffer(48 * m)
         la = (ctypes.c_uint64 * m)()
         ms = (ctypes.c_double * m)()
+        by = (ctypes.c_double * m)()
         k = ctypes.c_uint32(0)
-        _check(L.flix_profile_read(self._h, m, names, la, ms, ctypes.byref(k)), "flix_profile_read", self._h)
+        _check(L.flix_profile_read(self._h, m, names, la, ms, by, ctypes.byref(k)), "flix_profile_read", self._h)
         out = {}
         for i in range(k.value):
             nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
-            out[nm] = dict(launches=int(la[i]), ms=float(ms[i]))
+            out[nm] = dict(launches=int(la[i]), ms=float(ms[i]), bytes=float(by[i]))
         return out
 
     def launch_count(self) -> int:

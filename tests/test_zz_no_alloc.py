@@ -49,7 +49,7 @@ def test_noalloc_rejects_oversized_batch():
     L = fx.load()
     idx = fx.Index(key_bits=64, node_size=64)
     idx.bulk_load(np.arange(1, 1000, dtype=np.uint64), np.arange(1, 1000, dtype=np.uint64))
-    n = 1 << 20                                   # about 28 MB of scratch, more than the 16 MiB array
+    n = 1 << 20                                   # about 31 MB of scratch, more than the 16 MiB array
     q = torch.zeros(n, dtype=torch.int64, device="cuda")
     v = torch.empty(n, dtype=torch.int64, device="cuda")
     before = idx.launch_count()
