@@ -248,7 +248,8 @@ int do_read_point(flix_index* h, int mode, const K* keys, uint64_t n, K* keys_ou
 {
     if (n == 0) return FLIX_OK;
     Ctx c{h, st};
-    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 2 + (1 << 16)));
+    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 2 + partition_scratch_bytes(h->nb, n) +
+                       (1 << 16)));
     h->arena.reset();
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);
@@ -270,7 +271,7 @@ int do_range(flix_index* h, const K* lo, const K* hi, uint64_t n, uint64_t* roff
         return FLIX_OK;
     }
     CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 5 + al(n * 8) +
-                       scan_scratch_bytes<uint64_t>(n) + (1 << 16)));
+                       scan_scratch_bytes<uint64_t>(n) + partition_scratch_bytes(h->nb, n) + (1 << 16)));
     h->arena.reset();
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);
@@ -298,7 +299,7 @@ size_t batch_scratch_bytes(uint64_t n, uint64_t nb)
 {
     return sort_scratch_bytes<K>(n) + al(n * sizeof(K)) * 3 + al(n * 4) * 16 + al(n * 8) * 2 + al((nb + 1) * 4) * 2 +
            al((nb + 1) * 8) * 2 + al(nb + 1) + scan_scratch_bytes<uint64_t>(n) * 4 +
-           scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + (1 << 16);
+           scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + partition_scratch_bytes(nb, n) * 2 + (1 << 16);
 }
 
 // Reads of a mixed batch (snapshot), then its updates.  hom_op != 0: homogeneous insert/delete.

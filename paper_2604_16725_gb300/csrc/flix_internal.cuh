@@ -226,6 +226,9 @@ size_t scan_scratch_bytes(uint64_t n);
 // of the sorted MKBA with the sorted batch.  m_dev (optional) holds the batch length on the device
 // (then m is an upper bound).
 // bk (optional): bk[j] = bucket of sorted key j.  off (optional) as above.
+// Scratch bytes partition takes from the arena.
+size_t partition_scratch_bytes(uint64_t nb, uint64_t m);
+
 template <class K>
 cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m,
                       const uint32_t* m_dev, uint32_t* off, uint32_t* bk);

@@ -58,7 +58,7 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 template <class K>
 size_t noalloc_need(uint64_t n, uint64_t nb)
 {
-    return sort_scratch_bytes<K>(n) + al256(n * sizeof(K)) + al256(n * 4) * 2;
+    return sort_scratch_bytes<K>(n) + al256(n * sizeof(K)) + al256(n * 4) * 2 + partition_scratch_bytes(nb, n);
 }
 
 template <class K>

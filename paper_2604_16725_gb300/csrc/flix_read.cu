@@ -37,51 +37,65 @@ __device__ __forceinline__ uint64_t corank(const K* __restrict__ A, uint64_t nA,
     return lo;
 }
 
-// off[i + 1] = number of batch keys <= mkba[i] (off may be null); bk[j] = bucket of batch key j (bk
-// may be null).
+// Merge-path split points: ca[t] = A items among the first min(t * PT_TILE, nA + m) items of the
+// merge of A = mkba and B = the sorted batch (B wins ties), for t = 0..ntiles.
 template <class K>
-__global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ mkba, uint64_t nA,
-                                                          const K* __restrict__ skeys, uint64_t mmax,
+__global__ void __launch_bounds__(256) k_corank(const K* __restrict__ mkba, uint64_t nA, const K* __restrict__ skeys,
+                                                uint64_t mmax, const uint32_t* __restrict__ m_dev,
+                                                uint64_t* __restrict__ ca, uint32_t ntiles)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
+    const uint64_t L = nA + m;
+    const uint64_t d = (uint64_t)t * PT_TILE < L ? (uint64_t)t * PT_TILE : L;
+    ca[t] = corank(mkba, nA, skeys, m, d);
+}
+
+// First index in s[0..len) whose value is >= q (lower) or > q (upper).
+template <class K, bool UPPER>
+__device__ __forceinline__ uint32_t smem_bound(const K* s, uint32_t len, K q)
+{
+    uint32_t base = 0;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        const K v = s[base + half];
+        if (UPPER ? !(q < v) : (v < q)) { base += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return base;
+}
+
+// One merge-path tile of PT_TILE merged items per block: off[i + 1] = number of batch keys <=
+// mkba[i] (off may be null); bk[j] = bucket of batch key j = number of mkba entries < key j (bk may
+// be null).  Inside the tile each item finds its rank among the other side's tile items by binary
+// search in shared memory; items are thread-strided, so the writes coalesce.
+template <class K>
+__global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ mkba, const K* __restrict__ skeys,
+                                                          const uint64_t* __restrict__ ca, uint64_t nA, uint64_t mmax,
                                                           const uint32_t* __restrict__ m_dev,
                                                           uint32_t* __restrict__ off, uint32_t* __restrict__ bk)
 {
     __shared__ K sA[PT_TILE];
     __shared__ K sB[PT_TILE];
-    __shared__ uint64_t s_a[2];
     const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
     const uint64_t L = nA + m;
     const uint64_t d0 = (uint64_t)blockIdx.x * PT_TILE;
     if (d0 >= L) return;
     const uint64_t d1 = d0 + PT_TILE < L ? d0 + PT_TILE : L;
     if (off && blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
-    if (threadIdx.x < 2) s_a[threadIdx.x] = corank(mkba, nA, skeys, m, threadIdx.x ? d1 : d0);
-    __syncthreads();
-    const uint64_t a0 = s_a[0], a1 = s_a[1];
+    const uint64_t a0 = ca[blockIdx.x], a1 = ca[blockIdx.x + 1];
     const uint64_t b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0);
     for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS) sA[t] = mkba[a0 + t];
     for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS) sB[t] = skeys[b0 + t];
     __syncthreads();
-    const uint32_t ld = threadIdx.x * PT_ITEMS;
-    if (ld >= la + lb) return;
-    uint32_t lo = ld > lb ? ld - lb : 0, hi = ld < la ? ld : la;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (sA[mid] >= sB[ld - 1 - mid]) hi = mid; else lo = mid + 1;
-    }
-    uint32_t a = lo, b = ld - lo;
-#pragma unroll
-    for (int k = 0; k < PT_ITEMS; k++) {
-        if (a + b >= la + lb) break;
-        const bool takeA = (b >= lb) || (a < la && sA[a] < sB[b]);
-        if (takeA) {
-            if (off) off[a0 + a + 1] = (uint32_t)(b0 + b);
-            a++;
-        } else {
-            if (bk) bk[b0 + b] = (uint32_t)(a0 + a);
-            b++;
-        }
-    }
+    if (bk)
+        for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS)
+            bk[b0 + t] = (uint32_t)(a0 + smem_bound<K, false>(sA, la, sB[t]));
+    if (off)
+        for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS)
+            off[a0 + t + 1] = (uint32_t)(b0 + smem_bound<K, true>(sB, lb, sA[t]));
 }
 
 // First position in nk[0..sz) whose key is >= q.
@@ -296,12 +310,23 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
 
 }  // namespace
 
+size_t partition_scratch_bytes(uint64_t nb, uint64_t m)
+{
+    return ((size_t)(div_up(nb + m, PT_TILE) + 1) * 8 + 255) & ~size_t(255);
+}
+
 template <class K>
 cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m, const uint32_t* m_dev,
                       uint32_t* off, uint32_t* bk)
 {
     const uint32_t grid = div_up(nb + m, PT_TILE);
-    return launch(c, K_PARTITION, dim3(grid), dim3(PT_THREADS), 0, k_partition<K>, mkba, nb, skeys, m, m_dev, off, bk);
+    uint64_t* ca = c.h->arena.take<uint64_t>((size_t)grid + 1);
+    if (!ca) return cudaErrorMemoryAllocation;
+    cudaError_t e = launch(c, K_PARTITION, dim3(div_up((uint64_t)grid + 1, 256)), dim3(256), 0, k_corank<K>, mkba, nb,
+                           skeys, m, m_dev, ca, grid);
+    if (e) return e;
+    return launch(c, K_PARTITION, dim3(grid), dim3(PT_THREADS), 0, k_partition<K>, mkba, skeys, (const uint64_t*)ca,
+                  nb, m, m_dev, off, bk);
 }
 
 template <class K>

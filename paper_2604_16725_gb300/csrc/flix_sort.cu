@@ -421,20 +421,53 @@ __device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
     return ka < kb || (ka == kb && va < vb);
 }
 
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_ITEMS = 8;
+constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
+
+// One tile of FIN_TILE positions per block: the tile's keys, the key before it and SMALL_SEG + 1
+// keys after it are staged in shared memory (independent coalesced loads), then each thread looks
+// at FIN_ITEMS positions (FIN_THREADS apart) for group heads; a head's group is sorted by that
+// thread or, if longer than SMALL_SEG, listed.
 template <class K>
-__global__ void __launch_bounds__(256) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals, uint64_t n,
-                                                     SortPlan* __restrict__ plan, uint64_t* __restrict__ list,
-                                                     uint64_t list_cap, uint32_t* __restrict__ err)
+__global__ void __launch_bounds__(FIN_THREADS) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                             uint64_t n, SortPlan* __restrict__ plan,
+                                                             uint64_t* __restrict__ list, uint64_t list_cap,
+                                                             uint32_t* __restrict__ err)
 {
     if (!plan->finish) return;
+    constexpr int HALO = SMALL_SEG + 1;
+    __shared__ K tile[1 + FIN_TILE + HALO];
     const uint64_t pm = plan->pmask;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const K k0 = keys[i];
-        if (i > 0 && ((static_cast<uint64_t>(keys[i - 1] ^ k0) & pm) == 0)) continue;   // not a group head
+    const uint64_t base = (uint64_t)blockIdx.x * FIN_TILE;
+    const uint64_t lim = n - base < (uint64_t)(FIN_TILE + HALO) ? n - base : (uint64_t)(FIN_TILE + HALO);
+#pragma unroll
+    for (int r = 0; r < FIN_ITEMS; r++) {
+        const uint32_t j = r * FIN_THREADS + threadIdx.x;
+        if (j < lim) tile[1 + j] = keys[base + j];
+    }
+    if (threadIdx.x < HALO && FIN_TILE + threadIdx.x < lim) tile[1 + FIN_TILE + threadIdx.x] = keys[base + FIN_TILE + threadIdx.x];
+    if (threadIdx.x == 0 && base > 0) tile[0] = keys[base - 1];
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < FIN_ITEMS; r++) {
+        const uint32_t j = r * FIN_THREADS + threadIdx.x;        // tile position
+        if (j >= lim || j >= (uint32_t)FIN_TILE) break;
+        const K k0 = tile[1 + j];
+        if (base + j > 0 && (static_cast<uint64_t>(tile[j] ^ k0) & pm) == 0) continue;   // not a group head
         uint32_t L = 1;
-        while (L <= SMALL_SEG && i + L < n && (static_cast<uint64_t>(keys[i + L] ^ k0) & pm) == 0) L++;
+        while (L <= SMALL_SEG && j + L < lim && (static_cast<uint64_t>(tile[1 + j + L] ^ k0) & pm) == 0) L++;
         if (L == 1) continue;
+        const uint64_t i = base + j;
+        if (L <= SMALL_SEG) {
+            // keys already non-decreasing: equal keys are in position order (the passes are
+            // stable), so the group is sorted and stays as it is (repeated keys, mostly)
+            bool sorted = true;
+#pragma unroll
+            for (int a = 1; a < SMALL_SEG; a++)
+                if (a < (int)L) sorted &= !(tile[1 + j + a] < tile[j + a]);
+            if (sorted) continue;
+        }
         if (L > SMALL_SEG) {
             const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
             if (slot < list_cap) list[slot] = i;
@@ -446,7 +479,7 @@ __global__ void __launch_bounds__(256) k_sort_finish(K* __restrict__ keys, uint3
 #pragma unroll
         for (int a = 0; a < SMALL_SEG; a++) {
             if (a < (int)L) {
-                sk[a] = keys[i + a];
+                sk[a] = tile[1 + j + a];
                 sv[a] = vals[i + a];
             }
         }
@@ -799,10 +832,8 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
         }
         if (e) return e;
     }
-    uint32_t fg = div_up(n, 256);
-    if (fg > (uint32_t)nsm * 8) fg = nsm * 8;
-    if ((e = launch(c, K_SORT_FINISH, dim3(fg), dim3(256), 0, k_sort_finish<K>, kout, vout, n, plan, list, list_cap,
-                    c.h->err)))
+    if ((e = launch(c, K_SORT_FINISH, dim3(div_up(n, FIN_TILE)), dim3(FIN_THREADS), 0, k_sort_finish<K>, kout, vout, n,
+                    plan, list, list_cap, c.h->err)))
         return e;
     if ((e = cudaFuncSetAttribute(k_sort_finish_big<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;

@@ -241,6 +241,97 @@ __device__ __forceinline__ void stage_regs(K* sk, K* sv, uint32_t sz, uint32_t l
     }
 }
 
+// A bucket whose chain is one node and that receives at most FAST_U updates is handled by one
+// lane (every lane of a warp on its own bucket at once) instead of by the whole warp: the count
+// pass looks each update up in the node, and, when the merged run still fits the node, the apply
+// pass merges in place (deletions compact forward, then insertions merge backward from the end).
+// The result is the layout the warp path gives.
+constexpr uint32_t FAST_U = 8;
+
+// position in nk[0..sz) (global memory) of the first key >= q
+template <class K>
+__device__ __forceinline__ uint32_t gmem_lower_bound(const K* nk, uint32_t sz, K q)
+{
+    uint32_t base = 0, len = sz;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (nk[base + half] < q) { base += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return base;
+}
+
+// merged size of a one-node bucket: sz + absent inserts/upserts - present deletes
+template <class K>
+__device__ __forceinline__ uint32_t lane_count(const K* nk, uint32_t sz, const K* __restrict__ ukey,
+                                               const uint32_t* __restrict__ uop, uint32_t us, uint32_t ue)
+{
+    uint32_t t = sz;
+    for (uint32_t u = us; u < ue; u++) {
+        const K key = ukey[u];
+        const uint32_t op = uop[u];
+        const uint32_t pos = gmem_lower_bound(nk, sz, key);
+        const bool present = pos < sz && nk[pos] == key;
+        if (!present && (op == EFF_INS || op == EFF_UPS)) t++;
+        if (present && op == EFF_DEL) t--;
+    }
+    return t;
+}
+
+// In-place merge of a one-node bucket's updates into its node; t = merged size (<= NS).
+template <class K>
+__device__ __forceinline__ void lane_apply(K* nk, K* nv, uint32_t sz, uint32_t t, const K* __restrict__ ukey,
+                                           const uint32_t* __restrict__ uop, const K* __restrict__ uval, uint32_t us,
+                                           uint32_t ue)
+{
+    // deletions of present keys close their slots; upserts of present keys take the new value
+    uint32_t first = us;
+    while (first < ue && uop[first] == EFF_INS) first++;
+    uint32_t sz1 = sz;
+    if (first < ue) {
+        const uint32_t p0 = gmem_lower_bound(nk, sz, ukey[first]);
+        uint32_t w = p0, u = first;
+        for (uint32_t r = p0; r < sz; r++) {
+            const K key = nk[r];
+            K val = nv[r];
+            while (u < ue && (uop[u] == EFF_INS || ukey[u] < key)) u++;
+            bool changed = false;
+            if (u < ue && ukey[u] == key) {
+                if (uop[u] == EFF_DEL) continue;
+                val = uval[u];     // upsert of a present key
+                changed = true;
+            }
+            if (w != r || changed) {
+                nk[w] = key;
+                nv[w] = val;
+            }
+            w++;
+        }
+        sz1 = w;
+    }
+    // inserts (and upserts) of absent keys, merged from the end: w - r counts the ones left
+    int64_t r = (int64_t)sz1 - 1, u = (int64_t)ue - 1, w = (int64_t)t - 1;
+    while (u >= (int64_t)us && w > r && w >= 0) {
+        const uint32_t op = uop[u];
+        if (op == EFF_DEL) { u--; continue; }
+        const K uk = ukey[u];
+        const K nkr = r >= 0 ? nk[r] : K(0);
+        if (r >= 0 && nkr > uk) {
+            nk[w] = nkr;
+            nv[w] = nv[r];
+            r--;
+            w--;
+        } else if (r >= 0 && nkr == uk) {
+            u--;           // present: an insert is a no-op, an upsert was applied above
+        } else {
+            nk[w] = uk;
+            nv[w] = uval[u];
+            w--;
+            u--;
+        }
+    }
+}
+
 template <class K>
 __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
                                                              const uint32_t* __restrict__ uop,
@@ -260,6 +351,15 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
         nf[b0 + lane] = 0;
         allgone[b0 + lane] = 0;
     }
+    const bool fast = ((mask >> lane) & 1u) && g.nx == NIL && g.ue - g.us <= FAST_U;
+    if (fast) {
+        const uint32_t t = lane_count<K>(ix.keys + (uint64_t)g.node * NS, g.sz, ukey, uop, g.us, g.ue);
+        tnode[g.node] = t;
+        const uint32_t q = pieces_of(t, NS);
+        nf[b0 + lane] = q > 1 ? q - 1 : 0;   // an emptied only node stays: nothing freed
+        allgone[b0 + lane] = t == 0;
+    }
+    mask &= ~__ballot_sync(FULL, fast);
     while (mask) {
         const uint32_t i = __ffs(mask) - 1;
         mask &= mask - 1;
@@ -362,6 +462,13 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
         ag_l = allgone[b0 + lane];
         t0_l = tnode[g.node];
     }
+    const bool fast = ((mask >> lane) & 1u) && g.nx == NIL && g.ue - g.us <= FAST_U && t0_l <= NS;
+    if (fast) {
+        lane_apply<K>(ix.keys + (uint64_t)g.node * NS, ix.vals + (uint64_t)g.node * NS, g.sz, t0_l, ukey, uop, uval,
+                      g.us, g.ue);
+        ix.size[g.node] = t0_l;
+    }
+    mask &= ~__ballot_sync(FULL, fast);
     const uint32_t lt = lanemask_lt();
     while (mask) {
         const uint32_t i = __ffs(mask) - 1;
