@@ -14,7 +14,7 @@ const char* kKernelNames[K_NUM] = {
     "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep", "sort_plan", "sort_pass_idle",
     "sort_finish",
     "scan_partials", "scan_top", "scan_apply",
-    "partition", "read_point", "range_count", "range_fill",
+    "partition", "read_point", "read_unsort", "range_count", "range_fill",
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
     "update_count", "alloc_copy", "update_apply", "admit",
     "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill",
@@ -249,7 +249,7 @@ int do_read_point(flix_index* h, int mode, const K* keys, uint64_t n, K* keys_ou
     if (n == 0) return FLIX_OK;
     Ctx c{h, st};
     CK(h->arena.ensure(sort_scratch_bytes<K>(n) + al(n * sizeof(K)) + al(n * 4) * 2 + partition_scratch_bytes(h->nb, n) +
-                       (1 << 16)));
+                       read_point_scratch_bytes<K>(n) + (1 << 16)));
     h->arena.reset();
     K* sk = h->arena.take<K>(n);
     uint32_t* si = h->arena.take<uint32_t>(n);

@@ -46,7 +46,7 @@ struct DevIdx {
 enum KernelId {
     K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP, K_SORT_PLAN, K_SORT_IDLE, K_SORT_FINISH,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
-    K_PARTITION, K_READ_POINT, K_RANGE_COUNT, K_RANGE_FILL,
+    K_PARTITION, K_READ_POINT, K_UNSORT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
     K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY, K_ADMIT,
     K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL,
@@ -232,6 +232,10 @@ size_t partition_scratch_bytes(uint64_t nb, uint64_t m);
 template <class K>
 cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64_t m,
                       const uint32_t* m_dev, uint32_t* off, uint32_t* bk);
+
+// Scratch bytes read_point may take from the arena (it scatters directly when they are missing).
+template <class K>
+size_t read_point_scratch_bytes(uint64_t m);
 
 template <class K>
 cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m,

@@ -18,6 +18,7 @@
 namespace flix {
 namespace {
 
+constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr int PT_THREADS = 256;
 constexpr int PT_ITEMS = 8;
 constexpr int PT_TILE = PT_THREADS * PT_ITEMS;
@@ -144,13 +145,34 @@ __device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, 
     return true;
 }
 
+// Windowed result delivery (see read_point): window regions of the results and their offsets,
+// passed by value.
+constexpr uint32_t RP_MAX_WIN = 256;
+template <class K>
+struct ReadWin {
+    int shift;               // window w holds input positions [w << shift, (w + 1) << shift)
+    const uint64_t* off;     // off[w * nblocks + b]: where block b's results of window w start
+    uint32_t* idx;           // input position of each windowed result
+    K* rk;
+    K* rv;
+    uint8_t* rf;
+};
+
+// Point reads, one thread per sorted query.  Results go to the query's input position, or, with
+// win, to its window's region for k_win_scatter.
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mode, const K* __restrict__ skeys,
                                                            const uint32_t* __restrict__ sidx, uint64_t m,
                                                            const uint32_t* __restrict__ bk,
                                                            const uint8_t* __restrict__ ops, K* __restrict__ keys_out,
-                                                           K* __restrict__ vals_out, uint8_t* __restrict__ found_out)
+                                                           K* __restrict__ vals_out, uint8_t* __restrict__ found_out,
+                                                           const ReadWin<K> win, uint32_t nwin)
 {
+    __shared__ uint32_t s_wcnt[RP_MAX_WIN];
+    if (nwin) {
+        for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) s_wcnt[w] = 0;
+        __syncthreads();
+    }
     const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
     if (j >= m) return;
     const uint32_t idx = sidx[j];
@@ -199,9 +221,50 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
             }
         }
     }
-    if (keys_out) keys_out[idx] = rk;
-    if (vals_out) vals_out[idx] = rv;
-    if (found_out) found_out[idx] = f;
+    if (!nwin) {
+        if (keys_out) keys_out[idx] = rk;
+        if (vals_out) vals_out[idx] = rv;
+        if (found_out) found_out[idx] = f;
+        return;
+    }
+    // windowed: the result goes, tagged with idx, to the next free place of its window's region
+    const uint32_t w = idx >> win.shift;
+    const uint32_t r = atomicAdd(&s_wcnt[w], 1u);
+    const uint64_t at = win.off[(uint64_t)w * gridDim.x + blockIdx.x] + r;
+    win.idx[at] = idx;
+    if (keys_out) win.rk[at] = rk;
+    if (vals_out) win.rv[at] = rv;
+    if (found_out) win.rf[at] = f;
+}
+
+// Windowed result delivery: counts[w * nblocks + b] = results of read block b whose input position
+// lies in window w (positions [w << shift, (w + 1) << shift)).
+__global__ void __launch_bounds__(RP_THREADS) k_win_count(const uint32_t* __restrict__ sidx, uint64_t m, int shift,
+                                                          uint32_t nwin, uint32_t* __restrict__ counts)
+{
+    __shared__ uint32_t c[RP_MAX_WIN];
+    for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) c[w] = 0;
+    __syncthreads();
+    const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
+    if (j < m) atomicAdd(&c[sidx[j] >> shift], 1u);
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) counts[(uint64_t)w * gridDim.x + blockIdx.x] = c[w];
+}
+
+// Second half of the windowed delivery: results are read in window order, so the scattered
+// writes of the blocks in flight fall in a few windows' worth of output and merge in L2.
+template <class K>
+__global__ void __launch_bounds__(RP_THREADS) k_win_scatter(const uint32_t* __restrict__ widx, uint64_t m,
+                                                            const K* __restrict__ rk, const K* __restrict__ rv,
+                                                            const uint8_t* __restrict__ rf, K* __restrict__ keys_out,
+                                                            K* __restrict__ vals_out, uint8_t* __restrict__ found_out)
+{
+    const uint64_t p = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
+    if (p >= m) return;
+    const uint32_t i = widx[p];
+    if (keys_out) keys_out[i] = rk[p];
+    if (vals_out) vals_out[i] = rv[p];
+    if (found_out) found_out[i] = rf[p];
 }
 
 // Range count: per range query, the start (bucket, node, position) and the number of stored keys
@@ -263,7 +326,12 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const 
     cnt[idx] = c;
 }
 
-// Range fill: one warp per sorted query copies its pairs node by node (coalesced).
+// Range fill: one warp per sorted query.  The warp takes the next nodes in chain order 32 at a
+// time: lane 0 the current node (from the current position), lane l > 0 the first node of bucket
+// bb + l; their sizes and node-links load in parallel, and the batch ends at the first node whose
+// chain continues (the walk goes on from its link).  A warp scan of the nodes' available counts
+// gives each node's output offset, and the batch's pairs are copied with one independent load per
+// pair (each lane finds its pair's node by a shuffle search over the offsets).
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const uint32_t* __restrict__ sidx,
                                                            uint64_t m, const uint8_t* __restrict__ ops,
@@ -283,28 +351,69 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
     uint64_t c = roff[idx + 1] - o;
     if (c == 0) return;
     const uint32_t NS = ix.NS;
-    uint32_t bb = start_bucket[j];
+    uint64_t bb = start_bucket[j];
     uint32_t node = start_node[j];
     uint32_t pos = start_pos[j];
     for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim && c > 0; guard++) {
-        const uint32_t sz = ix.size[node];
-        const uint32_t avail = sz > pos ? sz - pos : 0;
-        const uint32_t take = (uint64_t)avail < c ? avail : (uint32_t)c;
-        const K* nk = ix.keys + (uint64_t)node * NS + pos;
-        const K* nv = ix.vals + (uint64_t)node * NS + pos;
-        for (uint32_t t = lane; t < take; t += 32) {
-            rkeys[o + t] = nk[t];
-            rvals[o + t] = nv[t];
+        // lane 0: the current node; lane l > 0: the first node of bucket bb + l
+        uint32_t n_l = NIL, p_l = 0, sz_l = 0, nx_l = NIL;
+        if (lane == 0) {
+            n_l = node;
+            p_l = pos;
+        } else if (bb + lane < ix.nb) {
+            n_l = ix.head[bb + lane];
+        }
+        if (n_l != NIL) {
+            sz_l = ix.size[n_l];
+            nx_l = ix.next[n_l];
+        }
+        // the batch ends at the first node whose chain continues
+        const uint32_t cont = __ballot_sync(FULL, nx_l != NIL);
+        const uint32_t last = cont ? __ffs(cont) - 1 : 31;
+        const uint32_t avail = (lane <= last && sz_l > p_l) ? sz_l - p_l : 0u;
+        uint32_t incl = avail;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t take = (uint64_t)total < c ? total : (uint32_t)c;
+        for (uint32_t t0 = 0; t0 < take; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            // the pair's node: the first lane whose inclusive count exceeds t
+            uint32_t src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t probe = src + step - 1;
+                if (__shfl_sync(FULL, incl, probe) <= t) src += step;
+            }
+            const uint32_t base = __shfl_sync(FULL, incl - avail, src);
+            const uint32_t sn = __shfl_sync(FULL, n_l, src);
+            const uint32_t sp = __shfl_sync(FULL, p_l, src);
+            if (t < take) {
+                const uint64_t slot = (uint64_t)sn * NS + sp + (t - base);
+                rkeys[o + t] = ix.keys[slot];
+                rvals[o + t] = ix.vals[slot];
+            }
         }
         o += take;
         c -= take;
-        pos = 0;
         if (c == 0) break;
-        node = ix.next[node];
-        while (node == NIL) {
-            if (++bb >= ix.nb) { if (lane == 0) atomicOr(ix.err, ERR_RANGE); return; }
+        // continue after the batch's last node: along its link, or at the next bucket's first node
+        const uint32_t lnx = __shfl_sync(FULL, nx_l, last);
+        if (lnx != NIL) {
+            bb += last;
+            node = lnx;
+        } else {
+            bb += last + 1;
+            if (bb >= ix.nb) {
+                if (lane == 0) atomicOr(ix.err, ERR_RANGE);
+                return;
+            }
             node = ix.head[bb];
         }
+        pos = 0;
     }
 }
 
@@ -329,13 +438,63 @@ cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64
                   nb, m, m_dev, off, bk);
 }
 
+// Results scattered to random input positions cost a read-modify-write of a DRAM sector each once
+// they no longer fit in L2.  Above RP_WIN_BYTES of results, homogeneous reads deliver them in two
+// steps instead: the read kernel writes each result, tagged with its input position, into the
+// region of its window of input positions (about RP_WIN_TARGET bytes of output per window; the
+// regions' per-block offsets come from a count and a scan), and k_win_scatter reads the regions in
+// order and writes the results to their positions.
+constexpr uint64_t RP_WIN_BYTES = 96ull << 20;
+constexpr uint64_t RP_WIN_TARGET = 4ull << 20;
+
+template <class K>
+size_t read_point_scratch_bytes(uint64_t m)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t nblk = div_up(m ? m : 1, RP_THREADS);
+    return al(m * sizeof(K)) * 2 + al(m) + al(m * 4) + al(nblk * RP_MAX_WIN * 4) + al((nblk * RP_MAX_WIN + 1) * 8) +
+           scan_scratch_bytes<uint64_t>(nblk * RP_MAX_WIN) + 1024;
+}
+
 template <class K>
 cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, uint64_t m, const uint32_t* bk,
                        const uint8_t* ops, K* keys_out, K* vals_out, uint8_t* found_out)
 {
     if (m == 0) return cudaSuccess;
-    return launch(c, K_READ_POINT, dim3(div_up(m, RP_THREADS)), dim3(RP_THREADS), 0, k_read_point<K>,
-                  dev_view<K>(c.h), mode, skeys, sidx, m, bk, ops, keys_out, vals_out, found_out);
+    const uint32_t nblk = div_up(m, RP_THREADS);
+    const uint64_t per = (keys_out ? sizeof(K) : 0) + (vals_out ? sizeof(K) : 0) + (found_out ? 1 : 0);
+    if (!ops && m * per > RP_WIN_BYTES && m < (1ull << 32)) {
+        // window size: a power of two near RP_WIN_TARGET bytes of output, at most RP_MAX_WIN windows
+        int shift = 0;
+        while (shift < 31 && ((2ull << shift) * per <= RP_WIN_TARGET || ((m - 1) >> shift) + 1 > RP_MAX_WIN)) shift++;
+        const uint32_t nwin = (uint32_t)(((m - 1) >> shift) + 1);
+        Arena& A = c.h->arena;
+        const size_t mark = A.used;
+        ReadWin<K> hw;
+        hw.shift = shift;
+        uint32_t* counts = A.take<uint32_t>((size_t)nwin * nblk);
+        uint64_t* off = A.take<uint64_t>((size_t)nwin * nblk + 1);
+        hw.off = off;
+        hw.idx = A.take<uint32_t>(m);
+        hw.rk = keys_out ? A.take<K>(m) : nullptr;
+        hw.rv = vals_out ? A.take<K>(m) : nullptr;
+        hw.rf = found_out ? A.take<uint8_t>(m) : nullptr;
+        if (counts && off && hw.idx && (!keys_out || hw.rk) && (!vals_out || hw.rv) && (!found_out || hw.rf)) {
+            cudaError_t e =
+                launch(c, K_UNSORT, dim3(nblk), dim3(RP_THREADS), 0, k_win_count, sidx, m, shift, nwin, counts);
+            if (!e) e = scan_exclusive<uint32_t, uint64_t>(c, counts, off, (uint64_t)nwin * nblk);
+            if (!e)
+                e = launch(c, K_READ_POINT, dim3(nblk), dim3(RP_THREADS), 0, k_read_point<K>, dev_view<K>(c.h), mode,
+                           skeys, sidx, m, bk, ops, keys_out, vals_out, found_out, hw, nwin);
+            if (!e)
+                e = launch(c, K_UNSORT, dim3(nblk), dim3(RP_THREADS), 0, k_win_scatter<K>, (const uint32_t*)hw.idx, m,
+                           (const K*)hw.rk, (const K*)hw.rv, (const uint8_t*)hw.rf, keys_out, vals_out, found_out);
+            return e;
+        }
+        A.used = mark;   // no room for the windowed results: scatter directly
+    }
+    return launch(c, K_READ_POINT, dim3(nblk), dim3(RP_THREADS), 0, k_read_point<K>, dev_view<K>(c.h), mode, skeys,
+                  sidx, m, bk, ops, keys_out, vals_out, found_out, ReadWin<K>{}, 0u);
 }
 
 template <class K>
@@ -365,6 +524,7 @@ cudaError_t range_fill(Ctx& c, const uint32_t* sidx, uint64_t m, const uint8_t* 
                                       uint32_t*);                                                               \
     template cudaError_t read_point<K>(Ctx&, int, const K*, const uint32_t*, uint64_t, const uint32_t*,        \
                                        const uint8_t*, K*, K*, uint8_t*);                                      \
+    template size_t read_point_scratch_bytes<K>(uint64_t);                                                     \
     template cudaError_t range_count<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint32_t*,           \
                                         const uint8_t*, const K*, uint32_t*, uint32_t*, uint32_t*, uint64_t*); \
     template cudaError_t range_fill<K>(Ctx&, const uint32_t*, uint64_t, const uint8_t*, const uint32_t*,       \

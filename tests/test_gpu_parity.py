@@ -267,3 +267,25 @@ def test_read_scale_full_size_sampled(fx):
         b = np.searchsorted(sk_all, hi[i], "right")
         same(rkn[offn[i]:offn[i + 1]], sk_all[a:b], "range.keys")
         same(rvn[offn[i]:offn[i + 1]], sv_all[a:b], "range.vals")
+
+
+def test_large_read_batches_every_output(fx):
+    """2^24 lookups and successors on a small index: the results exceed L2, so they are delivered
+    through input-position windows; every output is checked, not a sample."""
+    kw = 64
+    rng = np.random.default_rng(9)
+    load = np.unique(rng.integers(0, 1 << 40, 1 << 16, dtype=np.uint64))
+    vals = load * np.uint64(7) + np.uint64(3)
+    idx = fx.Index(key_bits=kw, node_size=32)
+    idx.bulk_load(load, vals)
+    q = np.concatenate([load[rng.integers(0, load.size, 1 << 23)],
+                        rng.integers(0, 1 << 41, 1 << 23, dtype=np.uint64)])[rng.permutation(1 << 24)]
+    qd = torch.from_numpy(q.view(np.int64)).cuda()
+    v, f = idx.lookup(qd)
+    ev, ef = oracle.sorted_lookup(load, vals, q, kw)
+    same(np_of(v, kw), ev, "lookup.vals")
+    same(f.cpu().numpy(), ef, "lookup.found")
+    sk, sv = idx.successor(qd)
+    esk, esv, _ = oracle.sorted_successor(load, vals, q, kw)
+    same(np_of(sk, kw), esk, "succ.keys")
+    same(np_of(sv, kw), esv, "succ.vals")
