@@ -29,35 +29,89 @@ __global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt)
     cnt[b] = c;
 }
 
-// one warp per bucket copies its chain's pairs to out[goff[b] ...]
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+// One warp per 32 consecutive buckets copies their chains' pairs to out[goff[b] ...].  Lane l
+// loads bucket b0 + l's first node and its size and link in parallel; the first nodes of buckets
+// whose chains end there are copied together with one independent load per pair (each lane finds
+// its pair's bucket by a shuffle search over the prefix of their sizes); the other chains are then
+// walked node by node by the whole warp.
 template <class K>
 __global__ void k_gather(DevIdx<K> ix, const uint64_t* __restrict__ goff, K* __restrict__ ok, K* __restrict__ ov)
 {
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= ix.nb) return;
-    uint64_t o = goff[b];
+    const uint64_t b0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (b0 >= ix.nb) return;
     const uint32_t NS = ix.NS;
-    uint32_t steps = 0;
-    for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
-        if (++steps > ix.cap) break;
-        const uint32_t sz = ix.size[x];
-        for (uint32_t s = lane; s < sz; s += 32) {
-            ok[o + s] = ix.keys[(uint64_t)x * NS + s];
-            ov[o + s] = ix.vals[(uint64_t)x * NS + s];
+    const uint64_t b = b0 + lane;
+    uint32_t n_l = NIL, sz_l = 0, nx_l = NIL;
+    uint64_t o_l = 0;
+    if (b < ix.nb) {
+        n_l = ix.head[b];
+        o_l = goff[b];
+        sz_l = ix.size[n_l];
+        nx_l = ix.next[n_l];
+    }
+    // single-node chains: one flat copy
+    const uint32_t cnt = nx_l == NIL ? sz_l : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        uint32_t src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t probe = src + step - 1;
+            if (__shfl_sync(FULL, incl, probe) <= t) src += step;
         }
-        o += sz;
+        const uint32_t base = __shfl_sync(FULL, incl - cnt, src);
+        const uint32_t sn = __shfl_sync(FULL, n_l, src);
+        const uint64_t so = __shfl_sync(FULL, o_l, src);
+        if (t < total) {
+            const uint32_t k = t - base;
+            ok[so + k] = ix.keys[(uint64_t)sn * NS + k];
+            ov[so + k] = ix.vals[(uint64_t)sn * NS + k];
+        }
+    }
+    // longer chains, one bucket at a time
+    uint32_t rest = __ballot_sync(FULL, nx_l != NIL);
+    while (rest) {
+        const uint32_t i = __ffs(rest) - 1;
+        rest &= rest - 1;
+        uint64_t o = __shfl_sync(FULL, o_l, i);
+        uint32_t x = __shfl_sync(FULL, n_l, i);
+        uint32_t steps = 0;
+        while (x != NIL) {
+            if (++steps > ix.cap) break;
+            const uint32_t sz = ix.size[x];
+            for (uint32_t s2 = lane; s2 < sz; s2 += 32) {
+                ok[o + s2] = ix.keys[(uint64_t)x * NS + s2];
+                ov[o + s2] = ix.vals[(uint64_t)x * NS + s2];
+            }
+            o += sz;
+            x = ix.next[x];
+        }
     }
 }
 
 template <class K>
+// one warp per new node: node i takes pairs [i * p, min((i + 1) * p, n))
 __global__ void k_cut_keys(DevIdx<K> ix, const K* __restrict__ sk, const K* __restrict__ sv, uint64_t n, uint32_t p)
 {
-    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const uint64_t node = e / p, slot = e - node * p;
-    ix.keys[node * ix.NS + slot] = sk[e];
-    ix.vals[node * ix.NS + slot] = sv[e];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t node = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t lo = node * p;
+    if (lo >= n) return;
+    const uint32_t cnt = (uint32_t)(n - lo < p ? n - lo : p);
+    for (uint32_t s2 = lane; s2 < cnt; s2 += 32) {
+        ix.keys[node * ix.NS + s2] = sk[lo + s2];
+        ix.vals[node * ix.NS + s2] = sv[lo + s2];
+    }
 }
 
 template <class K>
@@ -127,8 +181,8 @@ cudaError_t live_count(Ctx& c, uint64_t* cnt)
 template <class K>
 cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v)
 {
-    return launch(c, K_GATHER, dim3(div_up(c.h->nb * 32, BT)), dim3(BT), 0, k_gather<K>, dev_view<K>(c.h), goff,
-                  out_k, out_v);
+    return launch(c, K_GATHER, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_gather<K>, dev_view<K>(c.h), goff, out_k,
+                  out_v);
 }
 
 template <class K>
@@ -137,7 +191,8 @@ cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t n
     flix_index* h = c.h;
     h->nb = nb_new;
     DevIdx<K> ix = dev_view<K>(h);
-    cudaError_t e = launch(c, K_CUT_KEYS, dim3(div_up(n, BT)), dim3(BT), 0, k_cut_keys<K>, ix, sk, sv, n, h->p);
+    cudaError_t e = launch(c, K_CUT_KEYS, dim3(div_up(div_up(n, h->p) * 32ull, BT)), dim3(BT), 0, k_cut_keys<K>, ix,
+                           sk, sv, n, h->p);
     if (e) return e;
     const uint64_t work = nb_new > h->cap - nb_new ? nb_new : h->cap - nb_new;
     e = launch(c, K_CUT_META, dim3(div_up(work, BT)), dim3(BT), 0, k_cut_meta<K>, ix, sk, n, h->p, nb_new, h->cap,

@@ -278,57 +278,87 @@ __device__ __forceinline__ uint32_t lane_count(const K* nk, uint32_t sz, const K
     return t;
 }
 
+// Moves node slots [lo, hi] to [lo + d, hi + d] (d > 0: from the top down) or to [lo - e, hi - e]
+// (e > 0, from the bottom up), eight slots per round: a round's loads are all issued before its
+// stores, and no store of a round touches a slot a later round reads.
+constexpr int MOVE_BATCH = 8;
+
+template <class K>
+__device__ __forceinline__ void move_up(K* nk, K* nv, int64_t lo, int64_t hi, uint32_t d)
+{
+    for (int64_t top = hi; top >= lo; top -= MOVE_BATCH) {
+        K tk[MOVE_BATCH], tv[MOVE_BATCH];
+#pragma unroll
+        for (int q = 0; q < MOVE_BATCH; q++)
+            if (top - q >= lo) { tk[q] = nk[top - q]; tv[q] = nv[top - q]; }
+#pragma unroll
+        for (int q = 0; q < MOVE_BATCH; q++)
+            if (top - q >= lo) { nk[top - q + d] = tk[q]; nv[top - q + d] = tv[q]; }
+    }
+}
+
+template <class K>
+__device__ __forceinline__ void move_down(K* nk, K* nv, uint32_t lo, uint32_t hi_excl, uint32_t e)
+{
+    for (uint32_t bot = lo; bot < hi_excl; bot += MOVE_BATCH) {
+        K tk[MOVE_BATCH], tv[MOVE_BATCH];
+#pragma unroll
+        for (int q = 0; q < MOVE_BATCH; q++)
+            if (bot + q < hi_excl) { tk[q] = nk[bot + q]; tv[q] = nv[bot + q]; }
+#pragma unroll
+        for (int q = 0; q < MOVE_BATCH; q++)
+            if (bot + q < hi_excl) { nk[bot + q - e] = tk[q]; nv[bot + q - e] = tv[q]; }
+    }
+}
+
 // In-place merge of a one-node bucket's updates into its node; t = merged size (<= NS).
 template <class K>
 __device__ __forceinline__ void lane_apply(K* nk, K* nv, uint32_t sz, uint32_t t, const K* __restrict__ ukey,
                                            const uint32_t* __restrict__ uop, const K* __restrict__ uval, uint32_t us,
                                            uint32_t ue)
 {
-    // deletions of present keys close their slots; upserts of present keys take the new value
-    uint32_t first = us;
-    while (first < ue && uop[first] == EFF_INS) first++;
-    uint32_t sz1 = sz;
-    if (first < ue) {
-        const uint32_t p0 = gmem_lower_bound(nk, sz, ukey[first]);
-        uint32_t w = p0, u = first;
-        for (uint32_t r = p0; r < sz; r++) {
-            const K key = nk[r];
-            K val = nv[r];
-            while (u < ue && (uop[u] == EFF_INS || ukey[u] < key)) u++;
-            bool changed = false;
-            if (u < ue && ukey[u] == key) {
-                if (uop[u] == EFF_DEL) continue;
-                val = uval[u];     // upsert of a present key
-                changed = true;
-            }
-            if (w != r || changed) {
-                nk[w] = key;
-                nv[w] = val;
-            }
-            w++;
-        }
-        sz1 = w;
-    }
-    // inserts (and upserts) of absent keys, merged from the end: w - r counts the ones left
-    int64_t r = (int64_t)sz1 - 1, u = (int64_t)ue - 1, w = (int64_t)t - 1;
-    while (u >= (int64_t)us && w > r && w >= 0) {
+    // Deletions of present keys close their slots (the run between two deletions moves down by the
+    // deletions so far); upserts of present keys take the new value in place.
+    uint32_t rc = 0, ndel = 0;   // slots below rc are final
+    for (uint32_t u = us; u < ue; u++) {
         const uint32_t op = uop[u];
-        if (op == EFF_DEL) { u--; continue; }
-        const K uk = ukey[u];
-        const K nkr = r >= 0 ? nk[r] : K(0);
-        if (r >= 0 && nkr > uk) {
-            nk[w] = nkr;
-            nv[w] = nv[r];
-            r--;
-            w--;
-        } else if (r >= 0 && nkr == uk) {
-            u--;           // present: an insert is a no-op, an upsert was applied above
-        } else {
-            nk[w] = uk;
-            nv[w] = uval[u];
-            w--;
-            u--;
+        if (op == EFF_INS) continue;
+        const K key = ukey[u];
+        const uint32_t pos = rc + gmem_lower_bound(nk + rc, sz - rc, key);
+        if (pos >= sz || nk[pos] != key) continue;
+        if (op == EFF_UPS) {
+            nv[pos] = uval[u];
+            continue;
         }
+        if (ndel) move_down(nk, nv, rc, pos, ndel);
+        rc = pos + 1;
+        ndel++;
+    }
+    if (ndel) move_down(nk, nv, rc, sz, ndel);
+    const uint32_t sz1 = sz - ndel;
+    // Insertions (and upserts) of absent keys, from the largest: the node keys above one move up by
+    // the insertions still to place, which leaves its slot free; w - (r + 1) insertions remain.
+    int64_t r = (int64_t)sz1 - 1;
+    int64_t w = t;
+    for (int64_t u = (int64_t)ue - 1; u >= (int64_t)us && w > r + 1; u--) {
+        const uint32_t op = uop[u];
+        if (op == EFF_DEL) continue;
+        const K uk = ukey[u];
+        // number of kept keys <= uk
+        uint32_t base = 0, len = (uint32_t)(r + 1);
+        while (len > 0) {
+            const uint32_t half = len >> 1;
+            if (!(uk < nk[base + half])) { base += half + 1; len -= half + 1; }
+            else len = half;
+        }
+        if (base > 0 && nk[base - 1] == uk) continue;   // present: no insertion
+        const uint32_t d = (uint32_t)(w - 1 - r);
+        if ((int64_t)base <= r) move_up(nk, nv, base, r, d);
+        w -= r + 1 - base;
+        nk[w - 1] = uk;
+        nv[w - 1] = uval[u];
+        w--;
+        r = (int64_t)base - 1;
     }
 }
 
