@@ -198,23 +198,52 @@ def run_step(torch, idx, bufs, stream, events=None):
     ev("restructure", 1)
 
 
-def run_step_e2e(torch, idx, host, stream):
-    """The same step through the public API from pinned host buffers; results read back to host."""
-    dev = lambda t: t.to("cuda", non_blocking=True)  # noqa: E731
+def upload_inputs(torch, host, h2d):
+    """One step's inputs, host -> device on the h2d stream; returns (tensors, ready event)."""
+    with torch.cuda.stream(h2d):
+        dev = {k: host[k].to("cuda", non_blocking=True) for k in ("q", "sq", "lo", "hi", "ik", "iv")}
+        ready = torch.cuda.Event()
+        ready.record(h2d)
+    return dev, ready
+
+
+def run_step_e2e(torch, idx, host, stream, h2d, d2h, outs, step, pending):
+    """The same step through the public API from pinned host buffers, results read back to host.
+    Each step copies its own inputs host -> device, one step ahead on the h2d stream (`pending`
+    holds this step's upload); each phase's results go device -> host on the d2h stream as soon as
+    the phase has run; the phases run on `stream`.  Device results are double-buffered: a step
+    writes buffer set step % 2 once the copies out of that set (two steps earlier) are done.
+    Returns the next step's upload."""
+    o = outs[step % 2]
+    dev, ready = pending
+    nxt = upload_inputs(torch, host, h2d)
+    for t in dev.values():
+        t.record_stream(stream)
+    stream.wait_event(ready)
+    if o["copied"] is not None:
+        stream.wait_event(o["copied"])
+
+    def down(pairs):
+        done = torch.cuda.Event()
+        done.record(stream)
+        d2h.wait_event(done)
+        with torch.cuda.stream(d2h):
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+
     with torch.cuda.stream(stream):
-        v, _ = idx.lookup(dev(host["q"]), stream=stream, found=False)
-        host["lv"].copy_(v, non_blocking=True)
-        sk, sv = idx.successor(dev(host["sq"]), stream=stream)
-        host["sk"].copy_(sk, non_blocking=True)
-        host["sv"].copy_(sv, non_blocking=True)
-        off, rk, rv = idx.range(dev(host["lo"]), dev(host["hi"]), capacity=host["rcap"], stream=stream)
-        host["roff"].copy_(off, non_blocking=True)
-        host["rk"][: rk.numel()].copy_(rk, non_blocking=True)
-        host["rv"][: rv.numel()].copy_(rv, non_blocking=True)
-        idx.insert(dev(host["ik"]), dev(host["iv"]), stream=stream)
-        idx.delete(dev(host["ik"]), stream=stream)
+        v, _ = idx.lookup(dev["q"], stream=stream, out=o["lv"], found=False)
+        down([(host["lv"], v)])
+        sk, sv = idx.successor(dev["sq"], stream=stream, out=(o["sk"], o["sv"]))
+        down([(host["sk"], sk), (host["sv"], sv)])
+        off, rk, rv = idx.range(dev["lo"], dev["hi"], stream=stream, out=(o["roff"], o["rk"], o["rv"]))
+        down([(host["roff"], off), (host["rk"][: rk.numel()], rk), (host["rv"][: rv.numel()], rv)])
+        idx.insert(dev["ik"], dev["iv"], stream=stream)
+        idx.delete(dev["ik"], stream=stream)
         idx.restructure(stream=stream)
-    stream.synchronize()
+    o["copied"] = torch.cuda.Event()
+    o["copied"].record(d2h)
+    return nxt
 
 
 def cpu_oracle_sample(c, scale_log=4):
@@ -415,17 +444,27 @@ def main():
                              ("sv", n, torch.int64), ("roff", (1 << LOG_R) + 1, torch.int64),
                              ("rk", bufs["rcap"], torch.int64), ("rv", bufs["rcap"], torch.int64)):
             host[k] = torch.empty(shape, dtype=dt).pin_memory()
-        for _ in range(3):
-            run_step_e2e(torch, idx, host, stream)
+        h2d_st, d2h_st = torch.cuda.Stream(), torch.cuda.Stream()
+        outs = [dict(lv=torch.empty(n, dtype=torch.int64, device="cuda"),
+                     sk=torch.empty(n, dtype=torch.int64, device="cuda"),
+                     sv=torch.empty(n, dtype=torch.int64, device="cuda"),
+                     roff=torch.empty((1 << LOG_R) + 1, dtype=torch.int64, device="cuda"),
+                     rk=torch.empty(bufs["rcap"], dtype=torch.int64, device="cuda"),
+                     rv=torch.empty(bufs["rcap"], dtype=torch.int64, device="cuda"), copied=None) for _ in range(2)]
+        pending = upload_inputs(torch, host, h2d_st)
+        for s in range(3):
+            pending = run_step_e2e(torch, idx, host, stream, h2d_st, d2h_st, outs, s, pending)
+        torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            run_step_e2e(torch, idx, host, stream)
+        pending = upload_inputs(torch, host, h2d_st)     # the first timed step's inputs
+        for s in range(args.steps):
+            pending = run_step_e2e(torch, idx, host, stream, h2d_st, d2h_st, outs, s, pending)
+        torch.cuda.synchronize()
         barrier()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
         e2e_ms = max_over_ranks(e2e_ms, world)
-        h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv")) + \
-            host["ik"].numel() * 8
+        h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv"))
         d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
         line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}

@@ -11,7 +11,7 @@
 namespace flix {
 
 const char* kKernelNames[K_NUM] = {
-    "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep", "sort_plan", "sort_pass_idle",
+    "readback", "sort_hist", "sort_upsweep", "sort_scan", "sort_downsweep", "sort_onesweep", "sort_plan", "sort_pass_idle",
     "sort_finish",
     "scan_partials", "scan_top", "scan_apply",
     "partition", "read_point", "read_unsort", "range_count", "range_fill",
@@ -81,25 +81,59 @@ int fail(flix_index* h, cudaError_t e)
 
 size_t al(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Read `words` 8-byte words from device addresses into h->hpin and synchronise the stream.
-int readback(flix_index* h, cudaStream_t st, std::initializer_list<std::pair<const void*, size_t>> items)
+// Small read-backs go through a kernel that stores into the mapped pinned buffer hpin, not through
+// a copy engine: a synchronising call then never waits behind bulk transfers that other streams
+// have queued on the copy engines.
+struct ReadItems {
+    const void* src[8];
+    uint32_t bytes[8];
+    uint32_t n;
+    uint32_t word0;
+    uint64_t* dst;
+};
+
+__global__ void k_readback(ReadItems it)
 {
-    size_t o = 0;
-    for (auto& it : items) {
-        CK(cudaMemcpyAsync(reinterpret_cast<char*>(h->hpin) + o, it.first, it.second, cudaMemcpyDeviceToHost, st));
-        o += 8;
+    for (uint32_t i = 0; i < it.n; i++) {
+        const unsigned char* s = static_cast<const unsigned char*>(it.src[i]);
+        uint64_t v = 0;
+        for (uint32_t b = 0; b < it.bytes[i]; b++) v |= (uint64_t)s[b] << (8 * b);
+        it.dst[it.word0 + i] = v;
     }
+    __threadfence_system();
+}
+
+// Read up to 8 device values (4 or 8 bytes each, zero-extended) into h->hpin[word0 + i] and
+// synchronise the stream.
+int readback_impl(flix_index* h, cudaStream_t st, uint32_t word0,
+                  std::initializer_list<std::pair<const void*, size_t>> items)
+{
+    ReadItems it{};
+    for (auto& x : items) {
+        if (it.n == 8) return fail(h, cudaErrorInvalidValue);
+        it.src[it.n] = x.first;
+        it.bytes[it.n] = (uint32_t)x.second;
+        it.n++;
+    }
+    it.word0 = word0;
+    it.dst = h->hpin_dev;
+    Ctx c{h, st};
+    CK(launch(c, K_READBACK, dim3(1), dim3(1), 0, k_readback, it));
     CK(cudaStreamSynchronize(st));
     return FLIX_OK;
+}
+
+int readback(flix_index* h, cudaStream_t st, std::initializer_list<std::pair<const void*, size_t>> items)
+{
+    return readback_impl(h, st, 0, items);
 }
 
 // Device error word: read, clear, report.
 int check_err(flix_index* h, cudaStream_t st)
 {
-    uint32_t v = 0;
-    CK(cudaMemcpyAsync(&h->hpin[63], h->err, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    memcpy(&v, &h->hpin[63], 4);
+    int r = readback_impl(h, st, 63, {{h->err, 4}});
+    if (r) return r;
+    const uint32_t v = (uint32_t)h->hpin[63];
     if (v) {
         CK(cudaMemsetAsync(h->err, 0, 4, st));
         h->last_error = "device consistency check failed (code " + std::to_string(v) + ")";
@@ -537,6 +571,13 @@ int do_dump(flix_index* h, uint64_t* counts, K* mkba, uint32_t* chain_len, uint3
 #undef CK
 
 }  // namespace
+
+int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
+                std::initializer_list<std::pair<const void*, size_t>> items)
+{
+    return readback_impl(h, st, word0, items);
+}
+
 }  // namespace flix
 
 using namespace flix;
@@ -584,7 +625,8 @@ int flix_create(const flix_config* cfg, flix_t* out)
     cudaError_t e;
     if ((e = cudaMalloc(&h->err, 64)) || (e = cudaMemset(h->err, 0, 64)) ||
         (e = cudaMalloc(&h->dstate, sizeof(DevState))) || (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
-        (e = cudaMallocHost(&h->hpin, 64 * sizeof(uint64_t)))) {
+        (e = cudaHostAlloc(&h->hpin, 64 * sizeof(uint64_t), cudaHostAllocMapped)) ||
+        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->hpin_dev), h->hpin, 0))) {
         int r = fail(h, e);
         flix_destroy(h);
         return r;

@@ -5,7 +5,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <initializer_list>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "flix.h"
@@ -44,7 +46,7 @@ struct DevIdx {
 };
 
 enum KernelId {
-    K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP, K_SORT_PLAN, K_SORT_IDLE, K_SORT_FINISH,
+    K_READBACK, K_SORT_HIST, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_SORT_ONESWEEP, K_SORT_PLAN, K_SORT_IDLE, K_SORT_FINISH,
     K_SCAN_PART, K_SCAN_TOP, K_SCAN_APPLY,
     K_PARTITION, K_READ_POINT, K_UNSORT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
@@ -133,7 +135,8 @@ struct flix_index {
     flix::DevState* dstate = nullptr;
 
     flix::Arena arena;
-    uint64_t* hpin = nullptr;      // small pinned host buffer for read-backs (64 words)
+    uint64_t* hpin = nullptr;      // small mapped pinned host buffer for read-backs (64 words)
+    uint64_t* hpin_dev = nullptr;  // its device address
 
     bool prof_on = false;
     std::vector<flix::ProfRec> prof;
@@ -201,6 +204,11 @@ DevIdx<K> dev_view(flix_index* h)
     d.err = h->err;
     return d;
 }
+
+// Read up to 8 device values (4 or 8 bytes each) into h->hpin[word0 + i] and synchronise the stream
+// (flix_capi.cu); returns a FLIX_ status.
+int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
+                std::initializer_list<std::pair<const void*, size_t>> items);
 
 // ---- sort and scan primitives (flix_sort.cu) -------------------------------------------------
 

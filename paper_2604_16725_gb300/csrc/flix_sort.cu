@@ -802,9 +802,8 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(c.st, &cap))) return e;
     if (c.h->prof_on && cap == cudaStreamCaptureStatusNone) {
-        if ((e = cudaMemcpyAsync(&c.h->hpin[62], &plan->npass, 4, cudaMemcpyDeviceToHost, c.st))) return e;
-        if ((e = cudaStreamSynchronize(c.st))) return e;
-        memcpy(&active, &c.h->hpin[62], 4);
+        if (readback_at(c.h, c.st, 62, {{&plan->npass, 4}}) != FLIX_OK) return cudaErrorUnknown;
+        active = (uint32_t)c.h->hpin[62];
     }
     const size_t smem = sweep_smem<K>();
     e = onesweep ? cudaFuncSetAttribute(k_sweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)

@@ -177,19 +177,29 @@ class Index:
                "flix_lookup", self._h)
         return vals, f
 
-    def successor(self, keys, stream=None):
+    def successor(self, keys, stream=None, out=None):
+        """out: optional (keys_out, vals_out) device tensors of at least len(keys) elements."""
         q = self._dev(keys)
-        ko, vo = self._empty(q.numel()), self._empty(q.numel())
+        ko, vo = out if out is not None else (self._empty(q.numel()), self._empty(q.numel()))
         _check(load().flix_successor(self._h, _ptr(q), q.numel(), _ptr(ko), _ptr(vo), _stream(stream)),
                "flix_successor", self._h)
         return ko, vo
 
-    def range(self, lo, hi, capacity=None, stream=None):
+    def range(self, lo, hi, capacity=None, stream=None, out=None):
+        """out: optional (offsets, keys, vals) device tensors: offsets of len(lo) + 1 int64, keys and
+        vals of `capacity` elements (default: their length)."""
         lo, hi = self._dev(lo), self._dev(hi)
         n = lo.numel()
-        off = self._empty(n + 1, torch.int64)
+        off = out[0] if out is not None else self._empty(n + 1, torch.int64)
         total = ctypes.c_uint64(0)
         L = load()
+        if out is not None:
+            rk, rv = out[1], out[2]
+            cap = min(rk.numel(), rv.numel()) if capacity is None else capacity
+            _check(L.flix_range(self._h, _ptr(lo), _ptr(hi), n, _ptr(off), _ptr(rk), _ptr(rv), cap,
+                                ctypes.byref(total), _stream(stream)), "flix_range", self._h)
+            t = int(total.value)
+            return off[:n + 1], rk[:t], rv[:t]
         if capacity is None:
             # size the output from the counts, then fill
             code = L.flix_range(self._h, _ptr(lo), _ptr(hi), n, _ptr(off), None, None, 0, ctypes.byref(total),
