@@ -121,8 +121,8 @@ int flix_lookup(flix_t h, const void* d_keys, uint64_t n, void* d_vals_out, uint
  * allocator this library cannot see.  Same arguments and results as flix_lookup.
  * Its scratch (sort buffers and bucket offsets) is one fixed array of FLIX_NOALLOC_SCRATCH_BYTES
  * compiled into the library; every GPU that loads the library holds it until the process exits.
- * A call needs about 31*n bytes (uint64 keys; 22*n for uint32) plus a few KB, whatever the index
- * size, so up to about 2^19 uint64 keys per call fit; a larger request returns
+ * A call needs about 31*n bytes (uint64 keys; 22*n for uint32) plus a few KB and 8 bytes per
+ * 2048 buckets, so up to about 2^19 uint64 keys per call fit; a larger request returns
  * FLIX_EINVAL before launching anything (flix_last_error gives the sizes).  The first call on a
  * device looks up the array's device address on that device, so make it before any stream capture.
  * All calls share the array: calls whose work overlaps on the GPU (other streams, threads or

@@ -56,6 +56,11 @@ class BatchedRunner:
         self.batches = 0
         self.flags = torch.zeros(1, dtype=torch.int64, device=dev)   # OR of every batch's status flags
         idx.reserve(S, free_nodes_min, stream=self.stream)
+        # run the flag accumulation once now: a first use inside the stream of batches would load
+        # its kernel then (measured at ~0.7 s under lazy module loading)
+        with torch.cuda.stream(self.stream):
+            self.flags.bitwise_or_(self.out["status"][:1])
+        self.stream.synchronize()
 
     def _views(self, s):
         o = self.out

@@ -172,6 +172,25 @@ __global__ void k_stats(DevIdx<K> ix, unsigned long long* __restrict__ out)
 
 }  // namespace
 
+// Forces the module loader to load every kernel of this file now (see preload_kernels).
+void preload_build_kernels()
+{
+    cudaFuncAttributes a;
+#define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
+#define FLIX_TOUCH_K(K)                      \
+    FLIX_TOUCH(k_live_count<K>);             \
+    FLIX_TOUCH(k_gather<K>);                 \
+    FLIX_TOUCH(k_cut_keys<K>);               \
+    FLIX_TOUCH(k_cut_meta<K>);               \
+    FLIX_TOUCH(k_dedupe_flags<K>);           \
+    FLIX_TOUCH(k_dedupe_write<K>);           \
+    FLIX_TOUCH(k_stats<K>)
+    FLIX_TOUCH_K(uint32_t);
+    FLIX_TOUCH_K(uint64_t);
+#undef FLIX_TOUCH_K
+#undef FLIX_TOUCH
+}
+
 template <class K>
 cudaError_t live_count(Ctx& c, uint64_t* cnt)
 {

@@ -3,6 +3,7 @@
 // kernels; the host only sizes launches, reads back a few words where the ABI says it
 // synchronises, and manages memory.
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 #include <vector>
 
@@ -572,6 +573,27 @@ int do_dump(flix_index* h, uint64_t* counts, K* mkba, uint32_t* chain_len, uint3
 
 }  // namespace
 
+// Loads every kernel of the library on the current device (once per device per process), so that
+// no call, and no replay of a captured graph, pays for loading a kernel at its first launch.
+void preload_kernels()
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    for (int d : done)
+        if (d == dev) return;
+    cudaFuncAttributes a;
+    cudaFuncGetAttributes(&a, k_fill_desc);
+    cudaFuncGetAttributes(&a, k_readback);
+    preload_sort_kernels();
+    preload_read_kernels();
+    preload_update_kernels();
+    preload_build_kernels();
+    done.push_back(dev);
+}
+
 int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
                 std::initializer_list<std::pair<const void*, size_t>> items)
 {
@@ -615,6 +637,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     if (cfg->fill_pct == 0 || cfg->fill_pct > 100) return FLIX_EINVAL;
     if (cfg->sort_digit_bits != 0 && cfg->sort_digit_bits != 8) return FLIX_ENOTIMPL;
     if (cfg->sort_variant > FLIX_SORT_REDUCE_SCAN) return FLIX_EINVAL;
+    preload_kernels();
     flix_index* h = new flix_index();
     h->cfg = *cfg;
     h->kw = cfg->key_type == FLIX_KEY_U32 ? 32 : 64;

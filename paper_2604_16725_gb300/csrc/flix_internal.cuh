@@ -210,6 +210,15 @@ DevIdx<K> dev_view(flix_index* h)
 int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
                 std::initializer_list<std::pair<const void*, size_t>> items);
 
+// Every kernel of the library, loaded at handle creation (flix_capi.cu: preload_kernels).  Under
+// lazy module loading a kernel is otherwise loaded at its first launch, and a first launch inside
+// a CUDA graph replay was measured at ~0.7 s.
+void preload_kernels();
+void preload_sort_kernels();
+void preload_read_kernels();
+void preload_update_kernels();
+void preload_build_kernels();
+
 // ---- sort and scan primitives (flix_sort.cu) -------------------------------------------------
 
 // Scratch bytes sort_pairs needs for n items.

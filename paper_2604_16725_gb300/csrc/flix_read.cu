@@ -419,6 +419,25 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
 
 }  // namespace
 
+// Forces the module loader to load every kernel of this file now (see preload_kernels).
+void preload_read_kernels()
+{
+    cudaFuncAttributes a;
+#define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
+    FLIX_TOUCH(k_win_count);
+#define FLIX_TOUCH_K(K)                      \
+    FLIX_TOUCH(k_corank<K>);                 \
+    FLIX_TOUCH(k_partition<K>);              \
+    FLIX_TOUCH(k_read_point<K>);             \
+    FLIX_TOUCH(k_win_scatter<K>);            \
+    FLIX_TOUCH(k_range_count<K>);            \
+    FLIX_TOUCH(k_range_fill<K>)
+    FLIX_TOUCH_K(uint32_t);
+    FLIX_TOUCH_K(uint64_t);
+#undef FLIX_TOUCH_K
+#undef FLIX_TOUCH
+}
+
 size_t partition_scratch_bytes(uint64_t nb, uint64_t m)
 {
     return ((size_t)(div_up(nb + m, PT_TILE) + 1) * 8 + 255) & ~size_t(255);

@@ -421,6 +421,42 @@ __device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
     return ka < kb || (ka == kb && va < vb);
 }
 
+// Sorts one group of 2..SMALL_SEG items by (key, payload), in place: insertion sort in registers
+// (every index is a constant after unrolling).  Kept out of line so that the rare call does not
+// raise the register count of the scan around it.
+template <class K>
+__device__ __noinline__ void sort_small_group(K* keys, uint32_t* vals, const K* staged, uint32_t L)
+{
+    K sk[SMALL_SEG];
+    uint32_t sv[SMALL_SEG];
+#pragma unroll
+    for (int a = 0; a < SMALL_SEG; a++) {
+        if (a < (int)L) {
+            sk[a] = staged[a];
+            sv[a] = vals[a];
+        }
+    }
+#pragma unroll
+    for (int a = 1; a < SMALL_SEG; a++) {
+        if (a < (int)L) {
+#pragma unroll
+            for (int b = a; b > 0; b--) {
+                if (kv_less(sk[b], sv[b], sk[b - 1], sv[b - 1])) {
+                    const K tk = sk[b]; sk[b] = sk[b - 1]; sk[b - 1] = tk;
+                    const uint32_t tv = sv[b]; sv[b] = sv[b - 1]; sv[b - 1] = tv;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < SMALL_SEG; a++) {
+        if (a < (int)L) {
+            keys[a] = sk[a];
+            vals[a] = sv[a];
+        }
+    }
+}
+
 constexpr int FIN_THREADS = 256;
 constexpr int FIN_ITEMS = 8;
 constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
@@ -430,7 +466,7 @@ constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 // at FIN_ITEMS positions (FIN_THREADS apart) for group heads; a head's group is sorted by that
 // thread or, if longer than SMALL_SEG, listed.
 template <class K>
-__global__ void __launch_bounds__(FIN_THREADS) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
                                                              uint64_t n, SortPlan* __restrict__ plan,
                                                              uint64_t* __restrict__ list, uint64_t list_cap,
                                                              uint32_t* __restrict__ err)
@@ -474,35 +510,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_sort_finish(K* __restrict__ key
             else atomicOr(err, ERR_SORT);
             continue;
         }
-        K sk[SMALL_SEG];
-        uint32_t sv[SMALL_SEG];
-#pragma unroll
-        for (int a = 0; a < SMALL_SEG; a++) {
-            if (a < (int)L) {
-                sk[a] = tile[1 + j + a];
-                sv[a] = vals[i + a];
-            }
-        }
-        // insertion sort; every index is a constant after unrolling, so the group stays in registers
-#pragma unroll
-        for (int a = 1; a < SMALL_SEG; a++) {
-            if (a < (int)L) {
-#pragma unroll
-                for (int b = a; b > 0; b--) {
-                    if (kv_less(sk[b], sv[b], sk[b - 1], sv[b - 1])) {
-                        const K tk = sk[b]; sk[b] = sk[b - 1]; sk[b - 1] = tk;
-                        const uint32_t tv = sv[b]; sv[b] = sv[b - 1]; sv[b - 1] = tv;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < SMALL_SEG; a++) {
-            if (a < (int)L) {
-                keys[i + a] = sk[a];
-                vals[i + a] = sv[a];
-            }
-        }
+        sort_small_group<K>(keys + i, vals + i, tile + 1 + j, L);
     }
 }
 
@@ -714,6 +722,36 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin* __restri
 }
 
 }  // namespace
+
+// Forces the module loader to load every kernel of this file now (see preload_kernels).
+void preload_sort_kernels()
+{
+    cudaFuncAttributes a;
+#define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
+    FLIX_TOUCH(k_scan_digits);
+    FLIX_TOUCH(k_scan_part<uint32_t, uint32_t>);
+    FLIX_TOUCH(k_scan_part<uint32_t, uint64_t>);
+    FLIX_TOUCH(k_scan_part<uint64_t, uint64_t>);
+    FLIX_TOUCH(k_scan_part<uint8_t, uint32_t>);
+    FLIX_TOUCH(k_scan_top<uint32_t>);
+    FLIX_TOUCH(k_scan_top<uint64_t>);
+    FLIX_TOUCH(k_scan_apply<uint32_t, uint32_t>);
+    FLIX_TOUCH(k_scan_apply<uint32_t, uint64_t>);
+    FLIX_TOUCH(k_scan_apply<uint64_t, uint64_t>);
+    FLIX_TOUCH(k_scan_apply<uint8_t, uint32_t>);
+#define FLIX_TOUCH_K(K)                      \
+    FLIX_TOUCH(k_hist_all<K>);               \
+    FLIX_TOUCH(k_sort_plan<K>);              \
+    FLIX_TOUCH(k_upsweep<K>);                \
+    FLIX_TOUCH(k_sweep<K, true>);            \
+    FLIX_TOUCH(k_sweep<K, false>);           \
+    FLIX_TOUCH(k_sort_finish<K>);            \
+    FLIX_TOUCH(k_sort_finish_big<K>)
+    FLIX_TOUCH_K(uint32_t);
+    FLIX_TOUCH_K(uint64_t);
+#undef FLIX_TOUCH_K
+#undef FLIX_TOUCH
+}
 
 template <class Tout>
 size_t scan_scratch_bytes(uint64_t n)

@@ -707,6 +707,32 @@ size_t apply_smem(uint32_t NS)
 
 }  // namespace
 
+// Forces the module loader to load every kernel of this file now (see preload_kernels).
+void preload_update_kernels()
+{
+    cudaFuncAttributes a;
+#define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
+    FLIX_TOUCH(k_fold_init);
+    FLIX_TOUCH(k_fold_del);
+    FLIX_TOUCH(k_fold_ins);
+    FLIX_TOUCH(k_fold_emit);
+    FLIX_TOUCH(k_alloc_copy);
+    FLIX_TOUCH(k_admit);
+    FLIX_TOUCH(k_commit);
+    FLIX_TOUCH(k_set_free_top);
+#define FLIX_TOUCH_K(K)                      \
+    FLIX_TOUCH(k_validate<K>);               \
+    FLIX_TOUCH(k_fold_flags<K>);             \
+    FLIX_TOUCH(k_fold_write_mixed<K>);       \
+    FLIX_TOUCH(k_fold_write_hom<K>);         \
+    FLIX_TOUCH(k_update_count<K>);           \
+    FLIX_TOUCH(k_update_apply<K>)
+    FLIX_TOUCH_K(uint32_t);
+    FLIX_TOUCH_K(uint64_t);
+#undef FLIX_TOUCH_K
+#undef FLIX_TOUCH
+}
+
 template <class K>
 cudaError_t validate_inserts(Ctx& c, const uint8_t* ops, const K* keys, uint64_t n, uint32_t* flag)
 {

@@ -9,9 +9,10 @@ results are copied back on the copy stream.  A request completes when its batch'
 the host; its latency is that time minus its scheduled arrival.
 
 Admission by memory: an insert adds one key, so a batch needs at most one new node per insert (two
-for node size 2); the loop keeps a budget of free nodes, refreshes it from the device when it runs
-low, and grows the pool (re-capturing the graphs) only when even a refreshed budget cannot admit the
-next request.
+for node size 2); the loop keeps a budget of free nodes, charges each batch that bound when it is
+dispatched and, when the batch completes, gives back the part its device status says it did not
+use; it refreshes the budget from the device when it runs low, and grows the pool (re-capturing
+the graphs) only when even a refreshed budget cannot admit the next request.
 
 Batches execute in order on one compute stream, so each batch sees the effects of every earlier
 batch; `log` records each batch's request range so the whole run can be replayed elsewhere.
@@ -49,6 +50,8 @@ class Server:
                 dfound=torch.empty(max_batch, dtype=torch.uint8, device=dev),
                 vals=torch.empty(max_batch, dtype=dt).pin_memory(),
                 found=torch.empty(max_batch, dtype=torch.uint8).pin_memory(),
+                dstatus=torch.zeros(4, dtype=torch.int64, device=dev),
+                status=torch.zeros(4, dtype=torch.int64).pin_memory(),
                 consumed=torch.cuda.Event()))
         self.per_insert = 1 if idx.node_size >= 4 else 2
         self.budget = self._free_nodes()
@@ -87,9 +90,12 @@ class Server:
         while nxt < R or inflight:
             # retire finished batches
             while inflight and inflight[0][5].query():
-                slot, a, b, lo, hi, _ = inflight.popleft()
+                slot, a, b, lo, hi, _, charged = inflight.popleft()
                 t = time.perf_counter() - t0
                 lat[a:b] = t - arrival_s[a:b]
+                st = slot["status"].numpy()
+                if st[0] == 0:                       # admitted: return the nodes it did not need
+                    self.budget += charged - int(st[2])
                 if collect:
                     n = hi - lo
                     res_vals[lo:hi] = slot["vals"][:n].numpy().view(res_vals.dtype)
@@ -137,14 +143,16 @@ class Server:
             with torch.cuda.stream(self.compute):
                 slot["dvals"][:n].copy_(r["vals"], non_blocking=True)
                 slot["dfound"][:n].copy_(r["found"], non_blocking=True)
+                slot["dstatus"].copy_(r["status"], non_blocking=True)
             slot["consumed"].record(self.compute)
             self.copy.wait_event(slot["consumed"])
             with torch.cuda.stream(self.copy):
                 slot["vals"][:n].copy_(slot["dvals"][:n], non_blocking=True)
                 slot["found"][:n].copy_(slot["dfound"][:n], non_blocking=True)
+                slot["status"].copy_(slot["dstatus"], non_blocking=True)
                 done = torch.cuda.Event()
                 done.record(self.copy)
-            inflight.append((slot, nxt, b, lo, hi, done))
+            inflight.append((slot, nxt, b, lo, hi, done, need))
             log.append((nxt, b))
             nxt = b
             nb += 1
