@@ -427,6 +427,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "node_size": NODE_SIZE, "key_bits": KW,
+                       "restructure": "one pass into a second key/value node array",
                        "l2": "inputs larger than L2: 2.2 GB of nodes and >3 GB touched per step",
                        "parallelism": "replicas" if world > 1 else "single", "sort_variant": args.sort_variant},
             "per_op": {p: {"mops": (ops[p] / (statistics.median(per_phase[p]) * 1e-3) / 1e6) if p in ops else None,

@@ -70,7 +70,11 @@ typedef struct {
     uint64_t pool_nodes;   /* initial node-pool capacity; 0 = sized by the first bulk load */
     uint32_t sort_digit_bits; /* radix digit width of the batch sort: 8 (default) */
     uint32_t sort_variant;    /* FLIX_SORT_*: how each radix pass finds its output offsets */
-    uint32_t reserved[6];
+    uint32_t restructure_in_one_pass; /* nonzero: flix_restructure writes every live pair straight
+                                 into its place in a second key/value node array, kept for later
+                                 restructures (doubles the pool's key and value memory, halves
+                                 the restructure's traffic); zero: gather to scratch, then cut */
+    uint32_t reserved[5];
 } flix_config;
 
 /* Batch-sort variants (same stable order, different speed): one-sweep passes with decoupled
@@ -86,10 +90,12 @@ typedef struct {
     uint64_t max_chain;       /* longest bucket chain, in nodes */
     uint64_t node_bytes;      /* bytes of one node: keys, values, maxKey, size, node-link */
     uint64_t used_bytes;      /* nodes_used * node_bytes + MKBA and bucket heads */
-    uint64_t reserved_bytes;  /* device bytes held by the pool and the bucket arrays */
+    uint64_t reserved_bytes;  /* device bytes held by the pool and the bucket arrays (and the
+                                 second key/value arrays of the one-pass restructure) */
 } flix_stats_t;
 
-/* Fill *cfg with defaults for key type kt: node_size 32 (u32) or 64 (u64), fill 50%, grow on. */
+/* Fill *cfg with defaults for key type kt: node_size 32 (u32) or 64 (u64), fill 50%, grow on,
+ * one-pass restructure on. */
 void flix_config_default(flix_config* cfg, flix_keytype kt);
 
 /* Create an empty index (one bucket with one empty node) on the current CUDA device.

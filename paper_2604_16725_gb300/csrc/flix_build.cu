@@ -99,6 +99,82 @@ __global__ void k_gather(DevIdx<K> ix, const uint64_t* __restrict__ goff, K* __r
     }
 }
 
+// One-pass restructure: like k_gather, but the pair of global rank e goes straight to slot e % p
+// of node e / p of the second node arrays (k2, v2); the last pair of every group but the last
+// also sets its node's maxKey and its bucket's maxBucket.
+template <class K>
+__device__ __forceinline__ void put_ranked(DevIdx<K>& ix, K* __restrict__ k2, K* __restrict__ v2, uint64_t e,
+                                           uint32_t p, uint64_t nb_new, K key, K val)
+{
+    const uint64_t node = e < (1ull << 32) ? (uint64_t)((uint32_t)e / p) : e / p;
+    const uint32_t slot = (uint32_t)(e - node * p);
+    k2[node * ix.NS + slot] = key;
+    v2[node * ix.NS + slot] = val;
+    if (slot == p - 1 && node + 1 < nb_new) {
+        ix.bound[node] = key;
+        ix.mkba[node] = key;
+    }
+}
+
+template <class K>
+__global__ void k_gather_cut(DevIdx<K> ix, const uint64_t* __restrict__ goff, uint32_t p, uint64_t nb_new,
+                             K* __restrict__ k2, K* __restrict__ v2)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t b0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (b0 >= ix.nb) return;
+    const uint32_t NS = ix.NS;
+    const uint64_t b = b0 + lane;
+    uint32_t n_l = NIL, sz_l = 0, nx_l = NIL;
+    uint64_t o_l = 0;
+    if (b < ix.nb) {
+        n_l = ix.head[b];
+        o_l = goff[b];
+        sz_l = ix.size[n_l];
+        nx_l = ix.next[n_l];
+    }
+    const uint32_t cnt = nx_l == NIL ? sz_l : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        uint32_t src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t probe = src + step - 1;
+            if (__shfl_sync(FULL, incl, probe) <= t) src += step;
+        }
+        const uint32_t base = __shfl_sync(FULL, incl - cnt, src);
+        const uint32_t sn = __shfl_sync(FULL, n_l, src);
+        const uint64_t so = __shfl_sync(FULL, o_l, src);
+        if (t < total) {
+            const uint32_t k = t - base;
+            put_ranked(ix, k2, v2, so + k, p, nb_new, ix.keys[(uint64_t)sn * NS + k], ix.vals[(uint64_t)sn * NS + k]);
+        }
+    }
+    uint32_t rest = __ballot_sync(FULL, nx_l != NIL);
+    while (rest) {
+        const uint32_t i = __ffs(rest) - 1;
+        rest &= rest - 1;
+        uint64_t o = __shfl_sync(FULL, o_l, i);
+        uint32_t x = __shfl_sync(FULL, n_l, i);
+        uint32_t steps = 0;
+        while (x != NIL) {
+            if (++steps > ix.cap) break;
+            const uint32_t sz = ix.size[x];
+            for (uint32_t s2 = lane; s2 < sz; s2 += 32)
+                put_ranked(ix, k2, v2, o + s2, p, nb_new, ix.keys[(uint64_t)x * NS + s2], ix.vals[(uint64_t)x * NS + s2]);
+            o += sz;
+            x = ix.next[x];
+        }
+    }
+}
+
 template <class K>
 // one warp per new node: node i takes pairs [i * p, min((i + 1) * p, n))
 __global__ void k_cut_keys(DevIdx<K> ix, const K* __restrict__ sk, const K* __restrict__ sv, uint64_t n, uint32_t p)
@@ -122,12 +198,15 @@ __global__ void k_cut_meta(DevIdx<K> ix, const K* __restrict__ sk, uint64_t n, u
     if (i < nb_new) {
         const uint64_t lo = i * p;
         const uint64_t hi = lo + p < n ? lo + p : n;
-        const K mb = (i + 1 == nb_new) ? key_max<K>() : sk[hi - 1];
         ix.size[i] = (uint32_t)(hi > lo ? hi - lo : 0);
-        ix.bound[i] = mb;
         ix.next[i] = NIL;
-        ix.mkba[i] = mb;
         ix.head[i] = (uint32_t)i;
+        // sk == nullptr: the one-pass restructure already set every maxKey but the last
+        if (sk || i + 1 == nb_new) {
+            const K mb = (i + 1 == nb_new) ? key_max<K>() : sk[hi - 1];
+            ix.bound[i] = mb;
+            ix.mkba[i] = mb;
+        }
     }
     // free stack: ids nb_new .. cap-1, smallest id on top
     if (i < cap - nb_new) free_ids[i] = (uint32_t)(cap - 1 - i);
@@ -180,6 +259,7 @@ void preload_build_kernels()
 #define FLIX_TOUCH_K(K)                      \
     FLIX_TOUCH(k_live_count<K>);             \
     FLIX_TOUCH(k_gather<K>);                 \
+    FLIX_TOUCH(k_gather_cut<K>);             \
     FLIX_TOUCH(k_cut_keys<K>);               \
     FLIX_TOUCH(k_cut_meta<K>);               \
     FLIX_TOUCH(k_dedupe_flags<K>);           \
@@ -205,14 +285,25 @@ cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v)
 }
 
 template <class K>
+cudaError_t gather_cut(Ctx& c, const uint64_t* goff, uint64_t n, uint64_t nb_new, K* k2, K* v2)
+{
+    (void)n;
+    return launch(c, K_GATHER, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_gather_cut<K>, dev_view<K>(c.h), goff, c.h->p,
+                  nb_new, k2, v2);
+}
+
+template <class K>
 cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t nb_new)
 {
     flix_index* h = c.h;
     h->nb = nb_new;
     DevIdx<K> ix = dev_view<K>(h);
-    cudaError_t e = launch(c, K_CUT_KEYS, dim3(div_up(div_up(n, h->p) * 32ull, BT)), dim3(BT), 0, k_cut_keys<K>, ix,
-                           sk, sv, n, h->p);
-    if (e) return e;
+    cudaError_t e = cudaSuccess;
+    if (sk) {
+        e = launch(c, K_CUT_KEYS, dim3(div_up(div_up(n, h->p) * 32ull, BT)), dim3(BT), 0, k_cut_keys<K>, ix, sk, sv, n,
+                   h->p);
+        if (e) return e;
+    }
     const uint64_t work = nb_new > h->cap - nb_new ? nb_new : h->cap - nb_new;
     e = launch(c, K_CUT_META, dim3(div_up(work, BT)), dim3(BT), 0, k_cut_meta<K>, ix, sk, n, h->p, nb_new, h->cap,
                h->free_ids);
@@ -249,6 +340,7 @@ cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
 #define FLIX_BUILD_INST(K)                                                                                 \
     template cudaError_t live_count<K>(Ctx&, uint64_t*);                                                   \
     template cudaError_t gather_live<K>(Ctx&, const uint64_t*, K*, K*);                                    \
+    template cudaError_t gather_cut<K>(Ctx&, const uint64_t*, uint64_t, uint64_t, K*, K*);                 \
     template cudaError_t cut_buckets<K>(Ctx&, const K*, const K*, uint64_t, uint64_t);                     \
     template cudaError_t dedupe_sorted<K>(Ctx&, const K*, const uint32_t*, const K*, uint64_t, K*, K*,     \
                                           uint32_t*);                                                      \

@@ -143,6 +143,15 @@ int check_err(flix_index* h, cudaStream_t st)
     return FLIX_OK;
 }
 
+// The second key/value node array of the one-pass restructure (sized like the pool).
+void pool_free_second(flix_index* h)
+{
+    if (h->keys2) cudaFree(h->keys2);
+    if (h->vals2) cudaFree(h->vals2);
+    h->keys2 = h->vals2 = nullptr;
+    h->cap2 = 0;
+}
+
 void pool_free(flix_index* h)
 {
     void* ptrs[] = {h->keys, h->vals, h->size, h->bound, h->next, h->tnode, h->mkba, h->head, h->free_ids};
@@ -151,6 +160,7 @@ void pool_free(flix_index* h)
     h->keys = h->vals = h->bound = h->mkba = nullptr;
     h->size = h->next = h->tnode = h->head = h->free_ids = nullptr;
     h->cap = 0;
+    pool_free_second(h);
 }
 
 struct PoolArrays {
@@ -470,10 +480,25 @@ int do_restructure(flix_index* h, cudaStream_t st)
             CK(h->arena.ensure(need + al((nb + 1) * 8) * 2));
             continue;  // the arena moved: recount
         }
+        const uint64_t nb_new = n ? (n + h->p - 1) / h->p : 1;
+        if (h->cfg.restructure_in_one_pass && h->cap >= nb_new) {
+            // every live pair goes straight to its place in the second node array, which then
+            // becomes the pool's key/value array
+            if (h->cap2 != h->cap) {
+                pool_free_second(h);
+                CK(cudaMalloc(&h->keys2, h->cap * h->NS * h->ks));
+                CK(cudaMalloc(&h->vals2, h->cap * h->NS * h->ks));
+                h->cap2 = h->cap;
+            }
+            CK(gather_cut<K>(c, goff, n, nb_new, static_cast<K*>(h->keys2), static_cast<K*>(h->vals2)));
+            std::swap(h->keys, h->keys2);
+            std::swap(h->vals, h->vals2);
+            CK(cut_buckets<K>(c, nullptr, nullptr, n, nb_new));
+            return check_err(h, st);
+        }
         K* tk = h->arena.take<K>(n + 1);
         K* tv = h->arena.take<K>(n + 1);
         CK(gather_live<K>(c, goff, tk, tv));
-        const uint64_t nb_new = n ? (n + h->p - 1) / h->p : 1;
         if (h->cap < nb_new) {
             // the gathered pairs live in the arena, so the pool can be replaced
             CK(cudaStreamSynchronize(st));
@@ -526,7 +551,7 @@ int do_stats(flix_index* h, flix_stats_t* o, cudaStream_t st)
     o->pool_nodes = h->cap;
     o->node_bytes = 2ull * h->NS * sizeof(K) + sizeof(K) + 8;
     o->used_bytes = o->nodes_used * o->node_bytes + h->nb * (sizeof(K) + 4);
-    o->reserved_bytes = h->cap * (o->node_bytes + 4 + sizeof(K) + 4 + 4);
+    o->reserved_bytes = h->cap * (o->node_bytes + 4 + sizeof(K) + 4 + 4) + h->cap2 * h->NS * sizeof(K) * 2;
     return check_err(h, st);
 }
 
@@ -626,6 +651,7 @@ void flix_config_default(flix_config* cfg, flix_keytype kt)
     cfg->grow = 1;
     cfg->pool_nodes = 0;
     cfg->sort_digit_bits = 8;
+    cfg->restructure_in_one_pass = 1;
 }
 
 int flix_create(const flix_config* cfg, flix_t* out)

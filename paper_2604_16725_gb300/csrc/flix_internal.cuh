@@ -131,6 +131,9 @@ struct flix_index {
     void* mkba = nullptr;
     uint32_t* head = nullptr;
     uint32_t* free_ids = nullptr;  // free stack: ids [0, free_top) are free nodes
+    void* keys2 = nullptr;         // second key/value node arrays of the one-pass restructure
+    void* vals2 = nullptr;
+    uint64_t cap2 = 0;             // their capacity in nodes (0: not allocated)
     uint32_t* err = nullptr;       // device error word
     flix::DevState* dstate = nullptr;
 
@@ -314,6 +317,13 @@ cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v);
 // Cut n sorted distinct pairs into single-node buckets of p keys (Sec. 3.2); resets the free list.
 template <class K>
 cudaError_t cut_buckets(Ctx& c, const K* sk, const K* sv, uint64_t n, uint64_t nb_new);
+
+// One-pass restructure: the live pairs (goff = global rank of every bucket's first pair) go to
+// their canonical node and slot in the second arrays k2/v2; maxKey and maxBucket of every group
+// but the last are set on the way.  Then cut_buckets(c, nullptr, nullptr, n, nb_new) writes the
+// rest of the metadata once k2/v2 have become the pool's arrays.
+template <class K>
+cudaError_t gather_cut(Ctx& c, const uint64_t* goff, uint64_t n, uint64_t nb_new, K* k2, K* v2);
 
 template <class K>
 cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K* vals, uint64_t n,

@@ -31,7 +31,8 @@ class FlixError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("key_type", ctypes.c_int), ("node_size", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32),
                 ("grow", ctypes.c_uint32), ("pool_nodes", ctypes.c_uint64), ("sort_digit_bits", ctypes.c_uint32),
-                ("sort_variant", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+                ("sort_variant", ctypes.c_uint32), ("restructure_in_one_pass", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -113,7 +114,8 @@ class Index:
     """
 
     def __init__(self, key_bits: int = 64, node_size: int | None = None, fill_pct: int = 50,
-                 pool_nodes: int = 0, grow: bool = True, device=None, sort_variant: int = 0):
+                 pool_nodes: int = 0, grow: bool = True, device=None, sort_variant: int = 0,
+                 restructure_in_one_pass: bool = True):
         if not torch.cuda.is_available():
             raise RuntimeError("FliX needs a CUDA device; none is available")
         L = load()
@@ -129,6 +131,7 @@ class Index:
         cfg.pool_nodes = pool_nodes
         cfg.grow = 1 if grow else 0
         cfg.sort_variant = sort_variant
+        cfg.restructure_in_one_pass = 1 if restructure_in_one_pass else 0
         self.node_size = cfg.node_size
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -68,12 +68,22 @@ def test_config1_homogeneous_batches(fx):
 
 @pytest.mark.parametrize("kw,NS", [(32, 2), (64, 4), (32, 8), (64, 16), (32, 32), (64, 64), (32, 128), (64, 128)])
 def test_random_mixed_sequences(fx, kw, NS):
+    _random_mixed_sequence(fx, kw, NS, one_pass=True)
+
+
+@pytest.mark.parametrize("kw,NS", [(32, 8), (64, 64)])
+def test_random_mixed_sequences_two_pass_restructure(fx, kw, NS):
+    """The same sequences with the restructure that gathers to scratch, then cuts."""
+    _random_mixed_sequence(fx, kw, NS, one_pass=False)
+
+
+def _random_mixed_sequence(fx, kw, NS, one_pass):
     rng = np.random.default_rng(NS * 7 + kw)
     dom = 1 << 16 if kw == 32 else 1 << 40
     load = np.unique(rng.integers(0, dom, 3000, dtype=np.uint64))
     load = load[rng.permutation(load.size)].astype(np.uint64)
     fill = 50 if NS > 2 else 100
-    idx = fx.Index(key_bits=kw, node_size=NS, fill_pct=fill)
+    idx = fx.Index(key_bits=kw, node_size=NS, fill_pct=fill, restructure_in_one_pass=one_pass)
     idx.bulk_load(load.astype(np.uint32 if kw == 32 else np.uint64), (load * 3 + 1).astype(np.uint32 if kw == 32 else np.uint64))
     mp, md = oracle_pair(kw, NS, fill, load, load * 3 + 1)
     compare_layout(idx, md)
