@@ -7,7 +7,10 @@
 // top, so nodes allocated later stay near their buckets.
 //
 // Restructure: every bucket's live count (a walk of its chain), a scan, a gather of the live pairs
-// in bucket and chain order (globally sorted), then the same cut.
+// in bucket and chain order (globally sorted), then the same cut.  Chains are walked node by node
+// only up to SHORT_CHAIN nodes; when a longer chain exists, the nodes in use (the ids not on the
+// free stack) are put in chain order by sorting them by maxKey instead (maxKeys increase strictly
+// along a chain and from bucket to bucket), and a scan of their sizes gives each node's first rank.
 #include "flix_internal.cuh"
 
 namespace flix {
@@ -15,18 +18,70 @@ namespace {
 
 constexpr int BT = 256;
 
+constexpr uint32_t SHORT_CHAIN = 64;
+
+// Live pairs per bucket; a chain longer than SHORT_CHAIN nodes sets *long_flag instead.
 template <class K>
-__global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt)
+__global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt, uint32_t* __restrict__ long_flag)
 {
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     uint64_t c = 0;
     uint32_t steps = 0;
     for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
-        if (++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); break; }
+        if (++steps > SHORT_CHAIN) { atomicOr(long_flag, 1u); break; }
         c += ix.size[x];
     }
     cnt[b] = c;
+}
+
+// ---- nodes in chain order without walking chains ----------------------------------------------
+
+__global__ void k_unmark_free(const uint32_t* __restrict__ free_ids, const DevState* __restrict__ ds,
+                              uint8_t* __restrict__ mark)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ds->free_top) mark[free_ids[i]] = 0;
+}
+
+template <class K>
+__global__ void k_used_compact(DevIdx<K> ix, const uint8_t* __restrict__ mark, const uint32_t* __restrict__ pos,
+                               uint64_t cap, K* __restrict__ ubound, uint32_t* __restrict__ uid)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap || !mark[i]) return;
+    ubound[pos[i]] = ix.bound[i];
+    uid[pos[i]] = (uint32_t)i;
+}
+
+template <class K>
+__global__ void k_node_sizes(DevIdx<K> ix, const uint32_t* __restrict__ uid, const uint32_t* __restrict__ perm,
+                             uint64_t m, uint32_t* __restrict__ order, uint32_t* __restrict__ osz)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const uint32_t nd = uid[perm[j]];
+    order[j] = nd;
+    osz[j] = ix.size[nd];
+}
+
+// one warp per node in chain order: its pairs to ranks noff[j] ... (flat, or straight into the
+// second node arrays with CUT)
+template <class K, bool CUT>
+__global__ void k_gather_nodes(DevIdx<K> ix, const uint32_t* __restrict__ order, const uint64_t* __restrict__ noff,
+                               uint64_t m, uint32_t p, uint64_t nb_new, K* __restrict__ ok, K* __restrict__ ov);
+
+// chain[b] += 1 for every node of bucket b (bk: bucket of every node in chain order)
+__global__ void k_chain_count(const uint32_t* __restrict__ bk, uint64_t m, uint32_t* __restrict__ chain)
+{
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) atomicAdd(&chain[bk[j]], 1u);
+}
+
+__global__ void k_chain_max(const uint32_t* __restrict__ chain, uint64_t nb, unsigned long long* __restrict__ out)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) atomicMax(out, (unsigned long long)chain[b]);
 }
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -175,8 +230,30 @@ __global__ void k_gather_cut(DevIdx<K> ix, const uint64_t* __restrict__ goff, ui
     }
 }
 
-template <class K>
+template <class K, bool CUT>
+__global__ void k_gather_nodes(DevIdx<K> ix, const uint32_t* __restrict__ order, const uint64_t* __restrict__ noff,
+                               uint64_t m, uint32_t p, uint64_t nb_new, K* __restrict__ ok, K* __restrict__ ov)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= m) return;
+    const uint32_t nd = order[j];
+    const uint64_t o = noff[j];
+    const uint32_t sz = ix.size[nd];
+    for (uint32_t s2 = lane; s2 < sz; s2 += 32) {
+        const K key = ix.keys[(uint64_t)nd * ix.NS + s2];
+        const K val = ix.vals[(uint64_t)nd * ix.NS + s2];
+        if (CUT) {
+            put_ranked(ix, ok, ov, o + s2, p, nb_new, key, val);
+        } else {
+            ok[o + s2] = key;
+            ov[o + s2] = val;
+        }
+    }
+}
+
 // one warp per new node: node i takes pairs [i * p, min((i + 1) * p, n))
+template <class K>
 __global__ void k_cut_keys(DevIdx<K> ix, const K* __restrict__ sk, const K* __restrict__ sv, uint64_t n, uint32_t p)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -232,15 +309,16 @@ __global__ void k_dedupe_write(const K* __restrict__ skeys, const uint32_t* __re
     ov[pos[j]] = vals[sidx[j]];
 }
 
-// counts[0] = longest chain, counts[1] = live keys, counts[2] = nodes in chains
+// counts[0] = longest chain, counts[1] = live keys, counts[2] = nodes in chains; counts[3] = 1 if a
+// chain is longer than SHORT_CHAIN nodes (the other counts are then incomplete)
 template <class K>
 __global__ void k_stats(DevIdx<K> ix, unsigned long long* __restrict__ out)
 {
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     unsigned long long c = 0, k = 0;
-    uint32_t steps = 0;
-    for (uint32_t x = ix.head[b]; x != NIL && steps <= ix.cap; x = ix.next[x], steps++) {
+    for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
+        if (c == SHORT_CHAIN) { atomicOr(&out[3], 1ull); break; }
         c++;
         k += ix.size[x];
     }
@@ -256,10 +334,17 @@ void preload_build_kernels()
 {
     cudaFuncAttributes a;
 #define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
+    FLIX_TOUCH(k_unmark_free);
+    FLIX_TOUCH(k_chain_count);
+    FLIX_TOUCH(k_chain_max);
 #define FLIX_TOUCH_K(K)                      \
     FLIX_TOUCH(k_live_count<K>);             \
     FLIX_TOUCH(k_gather<K>);                 \
     FLIX_TOUCH(k_gather_cut<K>);             \
+    FLIX_TOUCH(k_used_compact<K>);           \
+    FLIX_TOUCH(k_node_sizes<K>);             \
+    FLIX_TOUCH((k_gather_nodes<K, false>));  \
+    FLIX_TOUCH((k_gather_nodes<K, true>));   \
     FLIX_TOUCH(k_cut_keys<K>);               \
     FLIX_TOUCH(k_cut_meta<K>);               \
     FLIX_TOUCH(k_dedupe_flags<K>);           \
@@ -272,9 +357,91 @@ void preload_build_kernels()
 }
 
 template <class K>
-cudaError_t live_count(Ctx& c, uint64_t* cnt)
+cudaError_t live_count(Ctx& c, uint64_t* cnt, uint32_t* long_flag)
 {
-    return launch(c, K_LIVE_COUNT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_live_count<K>, dev_view<K>(c.h), cnt);
+    cudaError_t e = cudaMemsetAsync(long_flag, 0, 4, c.st);
+    if (e) return e;
+    return launch(c, K_LIVE_COUNT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_live_count<K>, dev_view<K>(c.h), cnt,
+                  long_flag);
+}
+
+template <class K>
+size_t node_order_scratch_bytes(uint64_t cap)
+{
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return al(cap) + al((cap + 1) * 4) + al(cap * sizeof(K)) * 2 + al(cap * 4) * 4 + al((cap + 1) * 8) +
+           sort_scratch_bytes<K>(cap) + scan_scratch_bytes<uint32_t>(cap) + scan_scratch_bytes<uint64_t>(cap) + 4096;
+}
+
+template <class K>
+int node_order(Ctx& c, NodeOrder<K>& no)
+{
+    flix_index* h = c.h;
+    Arena& A = h->arena;
+    const uint64_t cap = h->cap;
+    uint8_t* mark = A.take<uint8_t>(cap);
+    uint32_t* pos = A.take<uint32_t>(cap + 1);
+    K* ubound = A.take<K>(cap);
+    uint32_t* uid = A.take<uint32_t>(cap);
+    if (!mark || !pos || !ubound || !uid) return FLIX_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(mark, 1, cap, c.st);
+    if (!e)
+        e = launch(c, K_LIVE_COUNT, dim3(div_up(cap, BT)), dim3(BT), 0, k_unmark_free, (const uint32_t*)h->free_ids,
+                   (const DevState*)h->dstate, mark);
+    if (!e) e = scan_exclusive<uint8_t, uint32_t>(c, mark, pos, cap);
+    if (!e)
+        e = launch(c, K_LIVE_COUNT, dim3(div_up(cap, BT)), dim3(BT), 0, k_used_compact<K>, dev_view<K>(h),
+                   (const uint8_t*)mark, (const uint32_t*)pos, cap, ubound, uid);
+    if (e) return FLIX_ECUDA;
+    int r = readback_at(h, c.st, 0, {{pos + cap, 4}});
+    if (r) return r;
+    const uint64_t m = h->hpin[0];
+    no.m = m;
+    no.bound = A.take<K>(m ? m : 1);
+    uint32_t* perm = A.take<uint32_t>(m ? m : 1);
+    no.order = A.take<uint32_t>(m ? m : 1);
+    uint32_t* osz = A.take<uint32_t>(m ? m : 1);
+    no.noff = A.take<uint64_t>(m + 1);
+    if (!no.bound || !perm || !no.order || !osz || !no.noff) return FLIX_ENOMEM;
+    e = sort_pairs<K>(c, ubound, nullptr, no.bound, perm, m);
+    if (!e && m)
+        e = launch(c, K_LIVE_COUNT, dim3(div_up(m, BT)), dim3(BT), 0, k_node_sizes<K>, dev_view<K>(h),
+                   (const uint32_t*)uid, (const uint32_t*)perm, m, no.order, osz);
+    if (!e) e = scan_exclusive<uint32_t, uint64_t>(c, osz, no.noff, m);
+    return e ? FLIX_ECUDA : FLIX_OK;
+}
+
+template <class K>
+cudaError_t gather_nodes(Ctx& c, const NodeOrder<K>& no, K* out_k, K* out_v)
+{
+    return launch(c, K_GATHER, dim3(div_up(no.m * 32, BT)), dim3(BT), 0, k_gather_nodes<K, false>, dev_view<K>(c.h),
+                  (const uint32_t*)no.order, (const uint64_t*)no.noff, no.m, c.h->p, (uint64_t)0, out_k, out_v);
+}
+
+template <class K>
+cudaError_t gather_nodes_cut(Ctx& c, const NodeOrder<K>& no, uint64_t nb_new, K* k2, K* v2)
+{
+    return launch(c, K_GATHER, dim3(div_up(no.m * 32, BT)), dim3(BT), 0, k_gather_nodes<K, true>, dev_view<K>(c.h),
+                  (const uint32_t*)no.order, (const uint64_t*)no.noff, no.m, c.h->p, nb_new, k2, v2);
+}
+
+template <class K>
+cudaError_t chain_max_by_nodes(Ctx& c, const NodeOrder<K>& no, uint64_t* out_max)
+{
+    flix_index* h = c.h;
+    Arena& A = h->arena;
+    uint32_t* bk = A.take<uint32_t>(no.m ? no.m : 1);
+    uint32_t* chain = A.take<uint32_t>(h->nb);
+    if (!bk || !chain) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(chain, 0, h->nb * 4, c.st);
+    if (!e) e = cudaMemsetAsync(out_max, 0, 8, c.st);
+    if (!e && no.m) e = partition<K>(c, static_cast<const K*>(h->mkba), h->nb, no.bound, no.m, nullptr, nullptr, bk);
+    if (!e && no.m)
+        e = launch(c, K_STATS, dim3(div_up(no.m, BT)), dim3(BT), 0, k_chain_count, (const uint32_t*)bk, no.m, chain);
+    if (!e)
+        e = launch(c, K_STATS, dim3(div_up(h->nb, BT)), dim3(BT), 0, k_chain_max, (const uint32_t*)chain, h->nb,
+                   reinterpret_cast<unsigned long long*>(out_max));
+    return e;
 }
 
 template <class K>
@@ -331,14 +498,19 @@ cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K*
 template <class K>
 cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
 {
-    cudaError_t e = cudaMemsetAsync(out3, 0, 3 * sizeof(uint64_t), c.st);
+    cudaError_t e = cudaMemsetAsync(out3, 0, 4 * sizeof(uint64_t), c.st);
     if (e) return e;
     return launch(c, K_STATS, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_stats<K>, dev_view<K>(c.h),
                   reinterpret_cast<unsigned long long*>(out3));
 }
 
 #define FLIX_BUILD_INST(K)                                                                                 \
-    template cudaError_t live_count<K>(Ctx&, uint64_t*);                                                   \
+    template cudaError_t live_count<K>(Ctx&, uint64_t*, uint32_t*);                                         \
+    template size_t node_order_scratch_bytes<K>(uint64_t);                                                 \
+    template int node_order<K>(Ctx&, NodeOrder<K>&);                                                       \
+    template cudaError_t gather_nodes<K>(Ctx&, const NodeOrder<K>&, K*, K*);                               \
+    template cudaError_t gather_nodes_cut<K>(Ctx&, const NodeOrder<K>&, uint64_t, K*, K*);                 \
+    template cudaError_t chain_max_by_nodes<K>(Ctx&, const NodeOrder<K>&, uint64_t*);                      \
     template cudaError_t gather_live<K>(Ctx&, const uint64_t*, K*, K*);                                    \
     template cudaError_t gather_cut<K>(Ctx&, const uint64_t*, uint64_t, uint64_t, K*, K*);                 \
     template cudaError_t cut_buckets<K>(Ctx&, const K*, const K*, uint64_t, uint64_t);                     \

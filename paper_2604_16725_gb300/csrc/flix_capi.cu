@@ -344,7 +344,8 @@ size_t batch_scratch_bytes(uint64_t n, uint64_t nb)
 {
     return sort_scratch_bytes<K>(n) + al(n * sizeof(K)) * 3 + al(n * 4) * 16 + al(n * 8) * 2 + al((nb + 1) * 4) * 2 +
            al((nb + 1) * 8) * 2 + al(nb + 1) + scan_scratch_bytes<uint64_t>(n) * 4 +
-           scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + partition_scratch_bytes(nb, n) * 2 + (1 << 16);
+           scan_scratch_bytes<uint64_t>(nb + 1) * 2 + al(2 * n * 4 + 64) + partition_scratch_bytes(nb, n) * 2 +
+           heavy_scratch_bytes(n) + (1 << 16);
 }
 
 // Reads of a mixed batch (snapshot), then its updates.  hom_op != 0: homogeneous insert/delete.
@@ -408,20 +409,23 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     if (!ukey || !uop || !uval || !uoff || !nf || !nf_off || !allgone || !alloc_ids) return FLIX_ENOMEM;
     CK(fold_updates<K>(c, sk, si, n, ops, hom_op, aux, ukey, uop, uval, udev));
     CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff, nullptr));
-    CK(update_count<K>(c, ukey, uop, uoff, nf, allgone));
+    const HeavyList hl = heavy_list(c, n);
+    if (!hl.list || !hl.n) return FLIX_ENOMEM;
+    CK(update_count<K>(c, ukey, uop, uoff, nf, allgone, hl));
     CK(scan_exclusive<uint64_t, uint64_t>(c, nf, nf_off, nb));
     const uint64_t* nf_total = nf_off + nb;
     const uint64_t* rtot_dev = (mixed && roff) ? roff + n : nullptr;
-    uint64_t need = 0, freed = 0, rtotal = 0;
+    uint64_t need = 0, freed = 0, rtotal = 0, heavy_nodes = 1;   // async: the heavy kernel always runs
     if (sync) {
         int r = readback(h, st, {{status, 4}, {nf_total, 8}, {rtot_dev ? (const void*)rtot_dev : (const void*)status, 8},
-                                 {&h->dstate->free_top, 8}});
+                                 {&h->dstate->free_top, 8}, {hl.n, 4}});
         if (r) return r;
         const uint32_t flag = (uint32_t)(h->hpin[0] & 0xFFFFFFFFu);
         need = h->hpin[1] & 0xFFFFFFFFull;
         freed = h->hpin[1] >> 32;
         rtotal = rtot_dev ? h->hpin[2] : 0;
         h->free_top = h->hpin[3];
+        heavy_nodes = h->hpin[4];
         if (flag & ERR_BADKEY) return FLIX_EINVAL;
         if (h_rtotal) *h_rtotal = rtotal;
         if (mixed && rtotal > rcap) return FLIX_ENOMEM;
@@ -437,6 +441,7 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     if (mixed && (!sync || rtotal)) CK(range_fill<K>(c, si, n, ops, sb, sn, sp, roff, rk, rv, true));
     CK(alloc_copy(c, h->free_ids, alloc_ids, alloc_cap));
     CK(update_apply<K>(c, ukey, uop, uval, uoff, nf_off, allgone, alloc_ids));
+    if (heavy_nodes) CK(update_heavy<K>(c, ukey, uop, uval, nf_off, alloc_ids, hl));
     CK(commit(c));
     if (sync) h->free_top = h->free_top - need + freed;
     return FLIX_OK;
@@ -460,6 +465,60 @@ int do_reserve(flix_index* h, uint64_t batch_max, uint64_t free_nodes_min, cudaS
     return FLIX_OK;
 }
 
+// Makes the second key/value node arrays of the one-pass restructure as large as the pool.
+int ensure_second(flix_index* h)
+{
+    if (h->cap2 == h->cap) return FLIX_OK;
+    pool_free_second(h);
+    CK(cudaMalloc(&h->keys2, h->cap * h->NS * h->ks));
+    CK(cudaMalloc(&h->vals2, h->cap * h->NS * h->ks));
+    h->cap2 = h->cap;
+    return FLIX_OK;
+}
+
+// Restructure with the nodes put in chain order by their maxKeys (some chain is long).
+template <class K>
+int restructure_by_nodes(flix_index* h, cudaStream_t st)
+{
+    Ctx c{h, st};
+    size_t extra = 0;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        CK(h->arena.ensure(node_order_scratch_bytes<K>(h->cap) + extra + (1 << 16)));
+        h->arena.reset();
+        NodeOrder<K> no;
+        int r = node_order<K>(c, no);
+        if (r) return r;
+        r = readback(h, st, {{no.noff + no.m, 8}});
+        if (r) return r;
+        const uint64_t n = h->hpin[0];
+        const uint64_t nb_new = n ? (n + h->p - 1) / h->p : 1;
+        if (h->cfg.restructure_in_one_pass && h->cap >= nb_new) {
+            r = ensure_second(h);
+            if (r) return r;
+            CK(gather_nodes_cut<K>(c, no, nb_new, static_cast<K*>(h->keys2), static_cast<K*>(h->vals2)));
+            std::swap(h->keys, h->keys2);
+            std::swap(h->vals, h->vals2);
+            CK(cut_buckets<K>(c, nullptr, nullptr, n, nb_new));
+            return check_err(h, st);
+        }
+        K* tk = h->arena.take<K>(n + 1);
+        K* tv = h->arena.take<K>(n + 1);
+        if (!tk || !tv) {
+            extra = al((n + 1) * sizeof(K)) * 2;
+            continue;   // the arena moves: order the nodes again
+        }
+        CK(gather_nodes<K>(c, no, tk, tv));
+        if (h->cap < nb_new) {
+            CK(cudaStreamSynchronize(st));
+            int rr = pool_reset(h, default_cap(h, nb_new));
+            if (rr) return rr;
+        }
+        CK(cut_buckets<K>(c, tk, tv, n, nb_new));
+        return check_err(h, st);
+    }
+    return FLIX_EINTERNAL;
+}
+
 template <class K>
 int do_restructure(flix_index* h, cudaStream_t st)
 {
@@ -470,10 +529,12 @@ int do_restructure(flix_index* h, cudaStream_t st)
         h->arena.reset();
         uint64_t* cnt = h->arena.take<uint64_t>(nb + 1);
         uint64_t* goff = h->arena.take<uint64_t>(nb + 1);
-        CK(live_count<K>(c, cnt));
+        uint32_t* long_flag = h->arena.take<uint32_t>(1);
+        CK(live_count<K>(c, cnt, long_flag));
         CK(scan_exclusive<uint64_t, uint64_t>(c, cnt, goff, nb));
-        int r = readback(h, st, {{goff + nb, 8}});
+        int r = readback(h, st, {{goff + nb, 8}, {long_flag, 4}});
         if (r) return r;
+        if (h->hpin[1]) return restructure_by_nodes<K>(h, st);
         const uint64_t n = h->hpin[0];
         const size_t need = h->arena.used + al(n * sizeof(K)) * 2 + (1 << 16);
         if (need > h->arena.cap) {
@@ -484,12 +545,8 @@ int do_restructure(flix_index* h, cudaStream_t st)
         if (h->cfg.restructure_in_one_pass && h->cap >= nb_new) {
             // every live pair goes straight to its place in the second node array, which then
             // becomes the pool's key/value array
-            if (h->cap2 != h->cap) {
-                pool_free_second(h);
-                CK(cudaMalloc(&h->keys2, h->cap * h->NS * h->ks));
-                CK(cudaMalloc(&h->vals2, h->cap * h->NS * h->ks));
-                h->cap2 = h->cap;
-            }
+            r = ensure_second(h);
+            if (r) return r;
             CK(gather_cut<K>(c, goff, n, nb_new, static_cast<K*>(h->keys2), static_cast<K*>(h->vals2)));
             std::swap(h->keys, h->keys2);
             std::swap(h->vals, h->vals2);
@@ -520,13 +577,27 @@ int do_export(flix_index* h, K* dk, K* dv, uint64_t cap_out, uint64_t* h_n, cuda
     h->arena.reset();
     uint64_t* cnt = h->arena.take<uint64_t>(nb + 1);
     uint64_t* goff = h->arena.take<uint64_t>(nb + 1);
-    CK(live_count<K>(c, cnt));
+    uint32_t* long_flag = h->arena.take<uint32_t>(1);
+    CK(live_count<K>(c, cnt, long_flag));
     CK(scan_exclusive<uint64_t, uint64_t>(c, cnt, goff, nb));
-    int r = readback(h, st, {{goff + nb, 8}});
+    int r = readback(h, st, {{goff + nb, 8}, {long_flag, 4}});
     if (r) return r;
-    if (h_n) *h_n = h->hpin[0];
-    if (h->hpin[0] > cap_out) return FLIX_ENOMEM;
-    CK(gather_live<K>(c, goff, dk, dv));
+    if (h->hpin[1]) {
+        CK(h->arena.ensure(node_order_scratch_bytes<K>(h->cap) + (1 << 16)));
+        h->arena.reset();
+        NodeOrder<K> no;
+        r = node_order<K>(c, no);
+        if (r) return r;
+        r = readback(h, st, {{no.noff + no.m, 8}});
+        if (r) return r;
+        if (h_n) *h_n = h->hpin[0];
+        if (h->hpin[0] > cap_out) return FLIX_ENOMEM;
+        CK(gather_nodes<K>(c, no, dk, dv));
+    } else {
+        if (h_n) *h_n = h->hpin[0];
+        if (h->hpin[0] > cap_out) return FLIX_ENOMEM;
+        CK(gather_live<K>(c, goff, dk, dv));
+    }
     CK(cudaStreamSynchronize(st));
     return check_err(h, st);
 }
@@ -539,7 +610,7 @@ int do_stats(flix_index* h, flix_stats_t* o, cudaStream_t st)
     h->arena.reset();
     uint64_t* s3 = h->arena.take<uint64_t>(4);
     CK(stats_kernel<K>(c, s3));
-    int r = readback(h, st, {{s3, 8}, {s3 + 1, 8}, {s3 + 2, 8}, {&h->dstate->free_top, 8}});
+    int r = readback(h, st, {{s3, 8}, {s3 + 1, 8}, {s3 + 2, 8}, {&h->dstate->free_top, 8}, {s3 + 3, 8}});
     if (r) return r;
     memset(o, 0, sizeof(*o));
     o->buckets = h->nb;
@@ -547,6 +618,21 @@ int do_stats(flix_index* h, flix_stats_t* o, cudaStream_t st)
     o->live_keys = h->hpin[1];
     o->nodes_used = h->hpin[2];
     h->free_top = h->hpin[3];
+    if (h->hpin[4]) {
+        // a chain longer than the walk bound: count from the nodes in use instead
+        CK(h->arena.ensure(node_order_scratch_bytes<K>(h->cap) + al(h->nb * 4) + al(h->cap * 4) + (1 << 16)));
+        h->arena.reset();
+        uint64_t* mx = h->arena.take<uint64_t>(1);
+        NodeOrder<K> no;
+        r = node_order<K>(c, no);
+        if (r) return r;
+        CK(chain_max_by_nodes<K>(c, no, mx));
+        r = readback(h, st, {{mx, 8}, {no.noff + no.m, 8}});
+        if (r) return r;
+        o->max_chain = h->hpin[0];
+        o->live_keys = h->hpin[1];
+        o->nodes_used = no.m;
+    }
     o->nodes_free = h->free_top;
     o->pool_nodes = h->cap;
     o->node_bytes = 2ull * h->NS * sizeof(K) + sizeof(K) + 8;

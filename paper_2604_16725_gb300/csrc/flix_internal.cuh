@@ -286,14 +286,28 @@ template <class K>
 cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t m, const uint8_t* ops,
                          int hom_op, const K* aux, K* ukey, uint32_t* uop, K* uval, uint32_t* u_dev);
 
+// Nodes that receive more than 2048 updates of a batch ("heavy"): listed by the count pass,
+// skipped by update_apply's key placement, merged by update_heavy (a block per node).
+struct HeavyList {
+    void* list = nullptr;
+    uint32_t* n = nullptr;   // device count
+    uint32_t cap = 0;
+};
 template <class K>
 cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff,
-                         uint64_t* nf, uint8_t* allgone);
+                         uint64_t* nf, uint8_t* allgone,
+                         const HeavyList& hl);
 
 template <class K>
 cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval,
                          const uint32_t* uoff, const uint64_t* nf_off, const uint8_t* allgone,
                          const uint32_t* alloc_ids);
+
+size_t heavy_scratch_bytes(uint64_t n);
+HeavyList heavy_list(Ctx& c, uint64_t n);   // from the arena, for a batch of n updates
+template <class K>
+cudaError_t update_heavy(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint64_t* nf_off,
+                         const uint32_t* alloc_ids, const HeavyList& hl);
 
 // Device admission of an update batch: node demand nf_total (need | freed << 32) against free_top,
 // the reserved-key flag, and the range total against range_cap.  status (optional, 4 words):
@@ -308,8 +322,33 @@ cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint32_t* out, uint64_t
 
 // ---- build / restructure / export (flix_build.cu) --------------------------------------------
 
+// Live pairs per bucket by walking each chain up to 64 nodes; *long_flag = 1 if a chain is longer
+// (cnt is then incomplete and the node-order functions below must be used instead).
 template <class K>
-cudaError_t live_count(Ctx& c, uint64_t* cnt);
+cudaError_t live_count(Ctx& c, uint64_t* cnt, uint32_t* long_flag);
+
+// The nodes in use in chain order, found without walking chains: order[0..m) node ids sorted by
+// maxKey (bound[] the sorted maxKeys), noff[0..m] the exclusive prefix of their sizes (noff[m] =
+// live pairs).  Synchronises once (to read m).  Scratch from the arena.
+template <class K>
+struct NodeOrder {
+    uint64_t m = 0;
+    uint32_t* order = nullptr;
+    uint64_t* noff = nullptr;
+    K* bound = nullptr;
+};
+template <class K>
+size_t node_order_scratch_bytes(uint64_t cap);
+template <class K>
+int node_order(Ctx& c, NodeOrder<K>& no);
+// The live pairs in key order, by node (flat, or straight into the second node arrays).
+template <class K>
+cudaError_t gather_nodes(Ctx& c, const NodeOrder<K>& no, K* out_k, K* out_v);
+template <class K>
+cudaError_t gather_nodes_cut(Ctx& c, const NodeOrder<K>& no, uint64_t nb_new, K* k2, K* v2);
+// Longest chain (in nodes), from the buckets of the nodes in chain order.
+template <class K>
+cudaError_t chain_max_by_nodes(Ctx& c, const NodeOrder<K>& no, uint64_t* out_max);
 
 template <class K>
 cudaError_t gather_live(Ctx& c, const uint64_t* goff, K* out_k, K* out_v);

@@ -157,18 +157,22 @@ __device__ __forceinline__ uint32_t smem_lower_bound(const K* nk, uint32_t sz, K
     return base;
 }
 
-// number of updates in [j, ue) whose key <= bd (the prefix routed to the current node)
+// End of the prefix of the sorted updates [j, ue) whose key <= bd (the updates routed to the
+// current node): a 32-way search by the whole warp, 32 independent probes per round.
 template <class K>
 __device__ __forceinline__ uint32_t routed_end(const K* __restrict__ ukey, uint32_t j, uint32_t ue, K bd)
 {
-    uint32_t k = j;
-    for (;;) {
-        const uint32_t u = k + (threadIdx.x & 31);
-        const bool in = u < ue && ukey[u] <= bd;
-        const uint32_t n = __popc(__ballot_sync(FULL, in));
-        k += n;
-        if (n < 32) return k;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t lo = j, hi = ue;   // keys below lo are <= bd, keys from hi on are > bd
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo) / 32;
+        const uint32_t c = __popc(__ballot_sync(FULL, ukey[lo + (lane + 1) * step - 1] <= bd));
+        // probes 0..c-1 hold keys <= bd, probe c (if any) a key > bd
+        if (c < 32) hi = lo + (c + 1) * step - 1;
+        lo += c * step;
     }
+    const bool in = lo + lane < hi && ukey[lo + lane] <= bd;
+    return lo + __popc(__ballot_sync(FULL, in));
 }
 
 template <class K>
@@ -362,12 +366,28 @@ __device__ __forceinline__ void lane_apply(K* nk, K* nv, uint32_t sz, uint32_t t
     }
 }
 
+// A node that receives more than HEAVY_U updates (a whole batch landing in one bucket, as sorted
+// or clustered keys do) is merged by a block of its own (k_update_heavy) rather than by the warp
+// that owns its bucket; the warp still writes the node's chain metadata.
+constexpr uint32_t HEAVY_U = 2048;
+constexpr int HV_THREADS = 256;
+constexpr int HV_ITEMS = 8;
+constexpr int HV_CHUNK = HV_THREADS * HV_ITEMS;
+
+struct HeavyNode {
+    uint32_t node, j, k, t, sz;
+    uint32_t need_before;   // nodes the bucket's earlier chain nodes allocate in this batch
+    uint64_t b;             // its bucket
+};
+
 template <class K>
 __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
                                                              const uint32_t* __restrict__ uop,
                                                              const uint32_t* __restrict__ uoff,
                                                              uint32_t* __restrict__ tnode, uint64_t* __restrict__ nf,
-                                                             uint8_t* __restrict__ allgone)
+                                                             uint8_t* __restrict__ allgone,
+                                                             HeavyNode* __restrict__ heavy, uint32_t* __restrict__ heavy_n,
+                                                             uint32_t heavy_cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -412,21 +432,36 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
                 stage_regs<K>(sk, nullptr, sz, lane, rk, rv);
                 __syncwarp();
                 uint32_t add = 0, del = 0;
-                for (uint32_t c0 = j; c0 < k; c0 += 32) {
-                    const uint32_t u = c0 + lane;
-                    if (u < k) {
-                        const K key = ukey[u];
-                        const uint32_t op = uop[u];
-                        const uint32_t pos = smem_lower_bound(sk, sz, key);
-                        const bool present = pos < sz && sk[pos] == key;
-                        if (!present && (op == EFF_INS || op == EFF_UPS)) add++;
-                        if (present && op == EFF_DEL) del++;
+                // four rounds of 32 updates per step: their loads are independent
+                for (uint32_t c0 = j; c0 < k; c0 += 128) {
+                    K key[4];
+                    uint32_t op[4];
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        const uint32_t u = c0 + r * 32 + lane;
+                        op[r] = u < k ? uop[u] : EFF_NONE;
+                        key[r] = u < k ? ukey[u] : K(0);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; r++) {
+                        if (op[r] == EFF_NONE) continue;
+                        const uint32_t pos = smem_lower_bound(sk, sz, key[r]);
+                        const bool present = pos < sz && sk[pos] == key[r];
+                        if (!present && (op[r] == EFF_INS || op[r] == EFF_UPS)) add++;
+                        if (present && op[r] == EFF_DEL) del++;
                     }
                 }
                 add = warp_sum<K>(add);
                 del = warp_sum<K>(del);
                 const uint32_t t = sz + add - del;
-                if (lane == 0) tnode[node] = t;
+                if (lane == 0) {
+                    tnode[node] = t;
+                    if (k - j > HEAVY_U) {   // merged later by a block of its own (k_update_heavy)
+                        const uint32_t slot = atomicAdd(heavy_n, 1u);
+                        if (slot < heavy_cap) heavy[slot] = HeavyNode{node, j, k, t, sz, (uint32_t)need, b0 + i};
+                        else atomicOr(ix.err, ERR_STEPS);
+                    }
+                }
                 const uint32_t q = pieces_of(t, NS);
                 if (q > 1) need += q - 1;
                 if (t == 0) dropped++;
@@ -528,6 +563,9 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
                 last_dropped = false;
             } else {
                 const uint32_t q = pieces_of(t, NS);
+                if (k - j > HEAVY_U) {
+                    // a heavy node: its keys are placed by k_update_heavy, its chain metadata here
+                } else {
                 stage_regs<K>(sk, sv, sz, lane, rk, rv);
                 for (uint32_t s = lane; s <= NS; s += 32) addcnt[s] = 0;
                 if (lane <= NS / 32) delmask[lane] = 0;
@@ -600,6 +638,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
                     }
                     carry += __shfl_sync(FULL, a, 31);
                 }
+                }
                 // chain metadata
                 if (t == 0) {
                     if (ag && first) {
@@ -646,6 +685,140 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
             t = tnode[node];
         }
         if (last_dropped && lane == 0 && prev_tail != NIL) ix.bound[prev_tail] = ix.mkba[b];
+    }
+}
+
+// A heavy node merged by one block: its keys and values are staged in shared memory; its updates
+// stream through in chunks of HV_CHUNK (present deletions marked, upserts of present keys noted,
+// inserted updates placed at (surviving node keys below) + (inserted updates before), the latter
+// from a block scan and a running carry); each node key counts the inserted updates below it as
+// the chunks pass; at the end the surviving node keys are placed.  Same positions and pieces as
+// the warp path.
+template <class K>
+__global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const K* __restrict__ ukey,
+                                                             const uint32_t* __restrict__ uop,
+                                                             const K* __restrict__ uval,
+                                                             const uint32_t* __restrict__ alloc_ids,
+                                                             const uint64_t* __restrict__ nf_off,
+                                                             const HeavyNode* __restrict__ heavy,
+                                                             const uint32_t* __restrict__ heavy_n, uint32_t heavy_cap,
+                                                             const DevState* __restrict__ ds)
+{
+    if (!ds->admitted) return;
+    __shared__ K nk[128], nv[128], newv[128];
+    __shared__ uint32_t ins_below[128];
+    __shared__ uint8_t ups[128];
+    __shared__ uint32_t delm[4];
+    __shared__ K ck[HV_CHUNK];
+    __shared__ uint32_t cex[HV_CHUNK + 1];
+    __shared__ uint32_t sw[HV_THREADS / 32];
+    const uint32_t NS = ix.NS, S2 = NS >> 1;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nh = min(*heavy_n, heavy_cap);
+    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const HeavyNode hn = heavy[h];
+        const uint32_t sz = hn.sz;
+        const uint32_t hq = pieces_of(hn.t, NS);
+        const uint64_t abase = (nf_off[hn.b] & 0xFFFFFFFFull) + hn.need_before;   // alloc_ids of its pieces 1..
+        for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
+            nk[s2] = ix.keys[(uint64_t)hn.node * NS + s2];
+            nv[s2] = ix.vals[(uint64_t)hn.node * NS + s2];
+            ins_below[s2] = 0;
+            ups[s2] = 0;
+        }
+        if (threadIdx.x < 4) delm[threadIdx.x] = 0;
+        __syncthreads();
+        auto place = [&](uint32_t p, K key, K val) {
+            uint32_t r = 0;
+            if (hq > 1) { r = p / S2; if (r > hq - 1) r = hq - 1; }
+            const uint32_t slot = p - r * S2;
+            const uint32_t dn = r == 0 ? hn.node : alloc_ids[abase + r - 1];
+            ix.keys[(uint64_t)dn * NS + slot] = key;
+            ix.vals[(uint64_t)dn * NS + slot] = val;
+            if (hq > 1 && r < hq - 1 && slot == S2 - 1) ix.bound[dn] = key;
+        };
+        auto dels_below = [&](uint32_t pos) {
+            uint32_t d = 0;
+            for (uint32_t wd = 0; wd < (pos >> 5); wd++) d += __popc(delm[wd]);
+            if (pos & 31) d += __popc(delm[pos >> 5] & ((1u << (pos & 31)) - 1));
+            return d;
+        };
+        uint32_t carry = 0;
+        for (uint32_t c0 = hn.j; c0 < hn.k; c0 += HV_CHUNK) {
+            const uint32_t cn = min((uint32_t)HV_CHUNK, hn.k - c0);
+            // items i = threadIdx.x * HV_ITEMS + r: consecutive per thread, for the scan
+            uint32_t pos[HV_ITEMS];
+            bool add[HV_ITEMS];
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int r = 0; r < HV_ITEMS; r++) {
+                const uint32_t i = threadIdx.x * HV_ITEMS + r;
+                add[r] = false;
+                pos[r] = 0;
+                if (i < cn) {
+                    const K key = ukey[c0 + i];
+                    const uint32_t op = uop[c0 + i];
+                    uint32_t lo = 0, len = sz;
+                    while (len > 0) {
+                        const uint32_t half = len >> 1;
+                        if (nk[lo + half] < key) { lo += half + 1; len -= half + 1; }
+                        else len = half;
+                    }
+                    pos[r] = lo;
+                    const bool present = lo < sz && nk[lo] == key;
+                    if (present && op == EFF_DEL) atomicOr(&delm[lo >> 5], 1u << (lo & 31));
+                    if (present && op == EFF_UPS) { newv[lo] = uval[c0 + i]; ups[lo] = 1; }
+                    add[r] = !present && (op == EFF_INS || op == EFF_UPS);
+                    ck[i] = key;
+                    cnt += add[r];
+                }
+            }
+            // block exclusive scan of the per-thread counts
+            uint32_t x = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (lane == 31) sw[w] = x;
+            __syncthreads();
+            uint32_t wbase = 0, total = 0;
+            for (int q2 = 0; q2 < HV_THREADS / 32; q2++) {
+                if (q2 < (int)w) wbase += sw[q2];
+                total += sw[q2];
+            }
+            uint32_t ex = wbase + x - cnt;
+#pragma unroll
+            for (int r = 0; r < HV_ITEMS; r++) {
+                const uint32_t i = threadIdx.x * HV_ITEMS + r;
+                if (i < cn) cex[i] = ex;
+                ex += add[r];
+            }
+            if (threadIdx.x == 0) cex[cn] = total;
+            __syncthreads();   // deletion marks and cex complete
+#pragma unroll
+            for (int r = 0; r < HV_ITEMS; r++) {
+                const uint32_t i = threadIdx.x * HV_ITEMS + r;
+                if (add[r]) place(pos[r] - dels_below(pos[r]) + carry + cex[i], ck[i], uval[c0 + i]);
+            }
+            // each node key counts the inserted updates of this chunk below it
+            for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
+                uint32_t lo = 0, len = cn;
+                while (len > 0) {
+                    const uint32_t half = len >> 1;
+                    if (ck[lo + half] < nk[s2]) { lo += half + 1; len -= half + 1; }
+                    else len = half;
+                }
+                ins_below[s2] += cex[lo];
+            }
+            carry += total;
+            __syncthreads();   // ck, cex and sw are rewritten by the next chunk
+        }
+        for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
+            if ((delm[s2 >> 5] >> (s2 & 31)) & 1u) continue;
+            place(s2 - dels_below(s2) + ins_below[s2], nk[s2], ups[s2] ? newv[s2] : nv[s2]);
+        }
+        __syncthreads();   // shared state is reset for the next heavy node
     }
 }
 
@@ -726,7 +899,8 @@ void preload_update_kernels()
     FLIX_TOUCH(k_fold_write_mixed<K>);       \
     FLIX_TOUCH(k_fold_write_hom<K>);         \
     FLIX_TOUCH(k_update_count<K>);           \
-    FLIX_TOUCH(k_update_apply<K>)
+    FLIX_TOUCH(k_update_apply<K>);           \
+    FLIX_TOUCH(k_update_heavy<K>)
     FLIX_TOUCH_K(uint32_t);
     FLIX_TOUCH_K(uint64_t);
 #undef FLIX_TOUCH_K
@@ -785,11 +959,30 @@ cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t 
 
 template <class K>
 cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff, uint64_t* nf,
-                         uint8_t* allgone)
+                         uint8_t* allgone, const HeavyList& hl)
 {
     const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
+    cudaError_t e = cudaMemsetAsync(hl.n, 0, 4, c.st);
+    if (e) return e;
     return launch(c, K_UPD_COUNT, dim3(grid), dim3(UP_THREADS), count_smem<K>(c.h->NS), k_update_count<K>,
-                  dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone);
+                  dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone, static_cast<HeavyNode*>(hl.list),
+                  hl.n, hl.cap);
+}
+
+uint32_t heavy_cap_of(uint64_t n) { return (uint32_t)(n / HEAVY_U + 2); }   // disjoint runs of > HEAVY_U updates
+
+HeavyList heavy_list(Ctx& c, uint64_t n)
+{
+    HeavyList hl;
+    hl.cap = heavy_cap_of(n);
+    hl.list = c.h->arena.take<HeavyNode>(hl.cap);
+    hl.n = c.h->arena.take<uint32_t>(1);
+    return hl;
+}
+
+size_t heavy_scratch_bytes(uint64_t n)
+{
+    return ((size_t)heavy_cap_of(n) * sizeof(HeavyNode) + 255) / 256 * 256 + 256;
 }
 
 template <class K>
@@ -800,6 +993,17 @@ cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uv
     return launch(c, K_UPD_APPLY, dim3(grid), dim3(UP_THREADS), apply_smem<K>(c.h->NS), k_update_apply<K>,
                   dev_view<K>(c.h), ukey, uop, uval, uoff, (const uint32_t*)c.h->tnode, nf_off, allgone, alloc_ids,
                   c.h->free_ids, (const DevState*)c.h->dstate);
+}
+
+template <class K>
+cudaError_t update_heavy(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint64_t* nf_off,
+                         const uint32_t* alloc_ids, const HeavyList& hl)
+{
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.h->device);
+    return launch(c, K_UPD_APPLY, dim3(nsm), dim3(HV_THREADS), 0, k_update_heavy<K>, dev_view<K>(c.h), ukey, uop, uval,
+                  alloc_ids, nf_off, (const HeavyNode*)hl.list, (const uint32_t*)hl.n, hl.cap,
+                  (const DevState*)c.h->dstate);
 }
 
 cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint32_t* out, uint64_t cap_out)
@@ -827,9 +1031,11 @@ cudaError_t set_free_top(Ctx& c, uint64_t value)
     template cudaError_t validate_inserts<K>(Ctx&, const uint8_t*, const K*, uint64_t, uint32_t*);             \
     template cudaError_t fold_updates<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint8_t*, int,       \
                                          const K*, K*, uint32_t*, K*, uint32_t*);                              \
-    template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const uint32_t*, uint64_t*, uint8_t*); \
+    template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const uint32_t*, uint64_t*, uint8_t*, const HeavyList&); \
     template cudaError_t update_apply<K>(Ctx&, const K*, const uint32_t*, const K*, const uint32_t*,           \
-                                         const uint64_t*, const uint8_t*, const uint32_t*);
+                                         const uint64_t*, const uint8_t*, const uint32_t*);                    \
+    template cudaError_t update_heavy<K>(Ctx&, const K*, const uint32_t*, const K*, const uint64_t*,           \
+                                         const uint32_t*, const HeavyList&);
 
 FLIX_UPD_INST(uint32_t)
 FLIX_UPD_INST(uint64_t)

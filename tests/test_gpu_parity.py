@@ -299,3 +299,73 @@ def test_large_read_batches_every_output(fx):
     esk, esv, _ = oracle.sorted_successor(load, vals, q, kw)
     same(np_of(sk, kw), esk, "succ.keys")
     same(np_of(sv, kw), esv, "succ.vals")
+
+
+@pytest.mark.parametrize("one_pass", [True, False])
+def test_long_chain_paths(fx, one_pass):
+    """A bucket whose chain is far longer than the chain-walk bound (64 nodes): stats, export and
+    restructure then put the nodes in chain order by their maxKeys instead of walking the chain."""
+    kw, NS = 32, 4
+    load = np.arange(10, 2000, 10, dtype=np.uint64)
+    vals = load * np.uint64(3)
+    idx = fx.Index(key_bits=kw, node_size=NS, restructure_in_one_pass=one_pass)
+    idx.bulk_load(load.astype(np.uint32), vals.astype(np.uint32))
+    mp, md = oracle_pair(kw, NS, 50, load, vals)
+    # 600 keys above every stored key all land in the last bucket: a chain of ~300 nodes
+    ins = np.arange(5000, 5600, dtype=np.uint64)
+    iv = ins + np.uint64(1)
+    for o, k, v in ((W.OP_INSERT, ins, iv), (W.OP_DELETE, ins[::7], None)):
+        ops = np.full(k.size, o, np.uint8)
+        if o == W.OP_INSERT:
+            idx.insert(k.astype(np.uint32), v.astype(np.uint32))
+        else:
+            idx.delete(k.astype(np.uint32))
+        mp.update(ops, k, v)
+        md.update(ops, k, v)
+        compare_layout(idx, md)
+    s, e = idx.stats(), md.stats()
+    assert s["max_chain"] > 64
+    assert (s["max_chain"], s["live_keys"], s["nodes_used"]) == (e["max_chain"], e["keys"], e["nodes"])
+    compare_contents(idx, mp, kw)
+    idx.restructure()
+    md.restructure()
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+    assert idx.stats()["max_chain"] == 1
+
+
+@pytest.mark.parametrize("kw,NS", [(32, 16), (64, 64), (32, 128)])
+def test_heavy_node_batches(fx, kw, NS):
+    """More than 2048 updates routed to one node (keys above every stored key land in the last
+    bucket): the node is merged by a block of its own.  Mixed ops: inserts of present and absent
+    keys, deletes of present and absent keys, upserts (delete then insert) of both."""
+    rng = np.random.default_rng(NS + kw)
+    dt = np.uint32 if kw == 32 else np.uint64
+    load = np.arange(10, 4000, 10, dtype=np.uint64)
+    vals = load * np.uint64(3)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    idx.bulk_load(load.astype(dt), vals.astype(dt))
+    mp, md = oracle_pair(kw, NS, 50, load, vals)
+    hi_keys = np.arange(100000, 100000 + 20000, 2, dtype=np.uint64)          # above every stored key
+    for b in range(3):
+        keys = rng.choice(hi_keys, 6000)
+        ops = rng.choice([W.OP_INSERT, W.OP_INSERT, W.OP_DELETE], keys.size).astype(np.uint8)
+        aux = rng.integers(1, 1 << 30, keys.size).astype(np.uint64)
+        apply_both(idx, mp, md, ops, keys.astype(dt), aux.astype(dt), kw)
+        compare_layout(idx, md)
+        if b == 1:
+            idx.restructure()
+            md.restructure()
+            compare_layout(idx, md)
+    # homogeneous heavy batches too
+    ins = np.arange(200001, 200001 + 2 * 5000, 2, dtype=np.uint64)
+    idx.insert(ins.astype(dt), (ins * np.uint64(5)).astype(dt))
+    mp.update(np.full(ins.size, W.OP_INSERT, np.uint8), ins, ins * np.uint64(5))
+    md.update(np.full(ins.size, W.OP_INSERT, np.uint8), ins, ins * np.uint64(5))
+    compare_layout(idx, md)
+    dk = ins[::3]
+    idx.delete(dk.astype(dt))
+    mp.update(np.full(dk.size, W.OP_DELETE, np.uint8), dk)
+    md.update(np.full(dk.size, W.OP_DELETE, np.uint8), dk)
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
