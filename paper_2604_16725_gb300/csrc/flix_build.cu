@@ -359,7 +359,7 @@ void preload_build_kernels()
 template <class K>
 cudaError_t live_count(Ctx& c, uint64_t* cnt, uint32_t* long_flag)
 {
-    cudaError_t e = cudaMemsetAsync(long_flag, 0, 4, c.st);
+    cudaError_t e = fill_bytes(c, long_flag, 0, 4);
     if (e) return e;
     return launch(c, K_LIVE_COUNT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_live_count<K>, dev_view<K>(c.h), cnt,
                   long_flag);
@@ -384,7 +384,7 @@ int node_order(Ctx& c, NodeOrder<K>& no)
     K* ubound = A.take<K>(cap);
     uint32_t* uid = A.take<uint32_t>(cap);
     if (!mark || !pos || !ubound || !uid) return FLIX_ENOMEM;
-    cudaError_t e = cudaMemsetAsync(mark, 1, cap, c.st);
+    cudaError_t e = fill_bytes(c, mark, 1, cap);
     if (!e)
         e = launch(c, K_LIVE_COUNT, dim3(div_up(cap, BT)), dim3(BT), 0, k_unmark_free, (const uint32_t*)h->free_ids,
                    (const DevState*)h->dstate, mark);
@@ -433,8 +433,8 @@ cudaError_t chain_max_by_nodes(Ctx& c, const NodeOrder<K>& no, uint64_t* out_max
     uint32_t* bk = A.take<uint32_t>(no.m ? no.m : 1);
     uint32_t* chain = A.take<uint32_t>(h->nb);
     if (!bk || !chain) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMemsetAsync(chain, 0, h->nb * 4, c.st);
-    if (!e) e = cudaMemsetAsync(out_max, 0, 8, c.st);
+    cudaError_t e = fill_bytes(c, chain, 0, h->nb * 4);
+    if (!e) e = fill_bytes(c, out_max, 0, 8);
     if (!e && no.m) e = partition<K>(c, static_cast<const K*>(h->mkba), h->nb, no.bound, no.m, nullptr, nullptr, bk);
     if (!e && no.m)
         e = launch(c, K_STATS, dim3(div_up(no.m, BT)), dim3(BT), 0, k_chain_count, (const uint32_t*)bk, no.m, chain);
@@ -486,11 +486,11 @@ cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K*
     uint32_t* head = A.take<uint32_t>(n + 1);
     uint32_t* pos = A.take<uint32_t>(n + 1);
     if (!head || !pos) return cudaErrorMemoryAllocation;
-    if (n == 0) return cudaMemsetAsync(n_dev, 0, 4, c.st);
+    if (n == 0) return fill_bytes(c, n_dev, 0, 4);
     cudaError_t e = launch(c, K_DEDUPE, dim3(div_up(n, BT)), dim3(BT), 0, k_dedupe_flags<K>, skeys, n, head);
     if (e) return e;
     if ((e = scan_exclusive<uint32_t, uint32_t>(c, head, pos, n))) return e;
-    if ((e = cudaMemcpyAsync(n_dev, pos + n, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+    if ((e = copy_words(c, n_dev, pos + n, 1))) return e;
     return launch(c, K_DEDUPE, dim3(div_up(n, BT)), dim3(BT), 0, k_dedupe_write<K>, skeys, sidx, vals, n,
                   (const uint32_t*)head, (const uint32_t*)pos, ok, ov);
 }
@@ -498,7 +498,7 @@ cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K*
 template <class K>
 cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
 {
-    cudaError_t e = cudaMemsetAsync(out3, 0, 4 * sizeof(uint64_t), c.st);
+    cudaError_t e = fill_bytes(c, out3, 0, 4 * sizeof(uint64_t));
     if (e) return e;
     return launch(c, K_STATS, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_stats<K>, dev_view<K>(c.h),
                   reinterpret_cast<unsigned long long*>(out3));

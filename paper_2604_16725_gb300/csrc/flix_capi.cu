@@ -136,7 +136,7 @@ int check_err(flix_index* h, cudaStream_t st)
     if (r) return r;
     const uint32_t v = (uint32_t)h->hpin[63];
     if (v) {
-        CK(cudaMemsetAsync(h->err, 0, 4, st));
+        { Ctx c0{h, st}; CK(fill_bytes(c0, h->err, 0, 4)); }
         h->last_error = "device consistency check failed (code " + std::to_string(v) + ")";
         return FLIX_EINTERNAL;
     }
@@ -265,7 +265,7 @@ int do_bulk_load(flix_index* h, const K* keys, const K* vals, uint64_t n, cudaSt
     uint32_t* si = h->arena.take<uint32_t>(n + 1);
     K* ok = h->arena.take<K>(n + 1);
     K* ov = h->arena.take<K>(n + 1);
-    CK(cudaMemsetAsync(status, 0, 64, st));
+    CK(fill_bytes(c, status, 0, 64));
     if (n) {
         CK(validate_inserts<K>(c, nullptr, keys, n, status));
         CK(sort_pairs<K>(c, keys, nullptr, sk, si, n));
@@ -311,7 +311,7 @@ int do_range(flix_index* h, const K* lo, const K* hi, uint64_t n, uint64_t* roff
 {
     Ctx c{h, st};
     if (n == 0) {
-        CK(cudaMemsetAsync(roff, 0, 8, st));
+        CK(fill_bytes(c, roff, 0, 8));
         if (h_total) *h_total = 0;
         return FLIX_OK;
     }
@@ -359,8 +359,9 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
 {
     if (h_rtotal) *h_rtotal = 0;
     if (n == 0) {
-        if (roff_user) CK(cudaMemsetAsync(roff_user, 0, 8, st));
-        if (d_status) CK(cudaMemsetAsync(d_status, 0, 4 * sizeof(uint64_t), st));
+        Ctx c0{h, st};
+        if (roff_user) CK(fill_bytes(c0, roff_user, 0, 8));
+        if (d_status) CK(fill_bytes(c0, d_status, 0, 4 * sizeof(uint64_t)));
         return FLIX_OK;
     }
     Ctx c{h, st};
@@ -378,7 +379,7 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     uint32_t* status = A.take<uint32_t>(16);
     K* sk = A.take<K>(n);
     uint32_t* si = A.take<uint32_t>(n);
-    CK(cudaMemsetAsync(status, 0, 64, st));
+    CK(fill_bytes(c, status, 0, 64));
     CK(validate_inserts<K>(c, mixed ? ops : nullptr, keys, mixed || hom_op == FLIX_OP_INSERT ? n : 0, status));
     CK(sort_pairs<K>(c, keys, nullptr, sk, si, n));
     uint64_t* roff = roff_user;
@@ -682,7 +683,41 @@ int do_dump(flix_index* h, uint64_t* counts, K* mkba, uint32_t* chain_len, uint3
 
 #undef CK
 
+__global__ void k_fill_bytes(uint32_t* __restrict__ dst, uint32_t pattern, uint64_t words, uint8_t* __restrict__ tail,
+                             uint32_t tail_bytes, uint8_t value)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = i0; i < words; i += stride) dst[i] = pattern;
+    if (i0 < tail_bytes) tail[i0] = value;
+}
+
+__global__ void k_copy_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint32_t words)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < words) dst[i] = src[i];
+}
+
 }  // namespace
+
+cudaError_t fill_bytes(Ctx& c, void* dst, uint8_t value, size_t bytes)
+{
+    if (bytes == 0) return cudaSuccess;
+    // dst is at least 4-byte aligned (arena and allocations are 256-byte aligned); the tail is
+    // filled byte by byte
+    const uint64_t words = bytes / 4;
+    const uint32_t tail = (uint32_t)(bytes - words * 4);
+    const uint32_t pattern = 0x01010101u * value;
+    uint32_t grid = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(div_up(words, 256), 1), 1216);
+    return launch(c, K_FILL, dim3(grid), dim3(256), 0, k_fill_bytes, static_cast<uint32_t*>(dst), pattern, words,
+                  static_cast<uint8_t*>(dst) + words * 4, tail, value);
+}
+
+cudaError_t copy_words(Ctx& c, void* dst, const void* src, uint32_t words)
+{
+    return launch(c, K_FILL, dim3(div_up(words, 256)), dim3(256), 0, k_copy_words, static_cast<uint32_t*>(dst),
+                  static_cast<const uint32_t*>(src), words);
+}
 
 // Loads every kernel of the library on the current device (once per device per process), so that
 // no call, and no replay of a captured graph, pays for loading a kernel at its first launch.
@@ -698,6 +733,8 @@ void preload_kernels()
     cudaFuncAttributes a;
     cudaFuncGetAttributes(&a, k_fill_desc);
     cudaFuncGetAttributes(&a, k_readback);
+    cudaFuncGetAttributes(&a, k_fill_bytes);
+    cudaFuncGetAttributes(&a, k_copy_words);
     preload_sort_kernels();
     preload_read_kernels();
     preload_update_kernels();

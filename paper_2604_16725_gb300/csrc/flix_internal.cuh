@@ -222,6 +222,12 @@ void preload_read_kernels();
 void preload_update_kernels();
 void preload_build_kernels();
 
+// Device fills and small copies as kernels on the call's stream (flix_capi.cu): a cudaMemsetAsync
+// or cudaMemcpyAsync may be carried out by a copy engine, where it would wait behind bulk transfers
+// that other streams have queued.
+cudaError_t fill_bytes(Ctx& c, void* dst, uint8_t value, size_t bytes);
+cudaError_t copy_words(Ctx& c, void* dst, const void* src, uint32_t words);
+
 // ---- sort and scan primitives (flix_sort.cu) -------------------------------------------------
 
 // Scratch bytes sort_pairs needs for n items.

@@ -762,7 +762,7 @@ size_t scan_scratch_bytes(uint64_t n)
 template <class Tin, class Tout>
 cudaError_t scan_exclusive(Ctx& c, const Tin* in, Tout* out, uint64_t n)
 {
-    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(Tout), c.st);
+    if (n == 0) return fill_bytes(c, out, 0, sizeof(Tout));
     const uint32_t ntiles = div_up(n, SCAN_TILE);
     Tout* part = c.h->arena.take<Tout>(ntiles);
     if (!part) return cudaErrorMemoryAllocation;
@@ -820,11 +820,11 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     uint64_t* list = A.take<uint64_t>(list_cap);
     if (!bases || !tk || !tv || !plan || !list || (onesweep ? (!status || !tile_ctr) : (!counts || !offsets)))
         return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMemsetAsync(bases, 0, P * RADIX * 4, c.st);
+    cudaError_t e = fill_bytes(c, bases, 0, P * RADIX * 4);
     if (e) return e;
     if (onesweep) {
-        if ((e = cudaMemsetAsync(status, 0, (size_t)P * T * RADIX * 4, c.st))) return e;
-        if ((e = cudaMemsetAsync(tile_ctr, 0, P * 4, c.st))) return e;
+        if ((e = fill_bytes(c, status, 0, (size_t)P * T * RADIX * 4))) return e;
+        if ((e = fill_bytes(c, tile_ctr, 0, P * 4))) return e;
     }
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.h->device);

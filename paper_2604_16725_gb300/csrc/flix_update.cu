@@ -923,12 +923,12 @@ cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t 
     if (!head || !hex) return cudaErrorMemoryAllocation;
     const uint32_t g = div_up(m ? m : 1, 256);
     cudaError_t e;
-    if (m == 0) return cudaMemsetAsync(u_dev, 0, 4, c.st);
+    if (m == 0) return fill_bytes(c, u_dev, 0, 4);
     if ((e = launch(c, K_FOLD_FLAGS, dim3(g), dim3(256), 0, k_fold_flags<K>, skeys, m, head))) return e;
     if ((e = scan_exclusive<uint32_t, uint32_t>(c, head, hex, m))) return e;
     if (hom_op) {
         // U = number of distinct keys = hex[m]
-        if ((e = cudaMemcpyAsync(u_dev, hex + m, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+        if ((e = copy_words(c, u_dev, hex + m, 1))) return e;
         const uint32_t eff = hom_op == FLIX_OP_INSERT ? EFF_INS : EFF_DEL;
         return launch(c, K_FOLD_WRITE, dim3(g), dim3(256), 0, k_fold_write_hom<K>, m, eff, skeys, sidx, aux,
                       (const uint32_t*)head, (const uint32_t*)hex, ukey, uop, uval);
@@ -951,7 +951,7 @@ cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t 
                     (const uint32_t*)hex, (const uint32_t*)lastdel, (const uint32_t*)firstins, emit, eff, hpos)))
         return e;
     if ((e = scan_exclusive<uint32_t, uint32_t>(c, emit, epos, m))) return e;
-    if ((e = cudaMemcpyAsync(u_dev, epos + m, 4, cudaMemcpyDeviceToDevice, c.st))) return e;
+    if ((e = copy_words(c, u_dev, epos + m, 1))) return e;
     return launch(c, K_FOLD_WRITE, dim3(g), dim3(256), 0, k_fold_write_mixed<K>, m, skeys, sidx, aux,
                   (const uint32_t*)emit, (const uint32_t*)epos, (const uint32_t*)eff, (const uint32_t*)hpos,
                   (const uint32_t*)firstins, ukey, uop, uval);
@@ -962,7 +962,7 @@ cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint3
                          uint8_t* allgone, const HeavyList& hl)
 {
     const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
-    cudaError_t e = cudaMemsetAsync(hl.n, 0, 4, c.st);
+    cudaError_t e = fill_bytes(c, hl.n, 0, 4);
     if (e) return e;
     return launch(c, K_UPD_COUNT, dim3(grid), dim3(UP_THREADS), count_smem<K>(c.h->NS), k_update_count<K>,
                   dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone, static_cast<HeavyNode*>(hl.list),
