@@ -393,6 +393,17 @@ def main():
     prof = idx.profile_read()
     idx.profile(False)
 
+    # predecessor (not part of the step): 2^24 queries of the successor recipe, timed alone
+    pred_ms = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        idx.predecessor(bufs["sq"], stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            pred_ms.append(a.elapsed_time(b))
+
     # roofline of the dominant kernel: the radix-sort scatter pass
     peak, peak_kind = measured_peaks()
     down = prof.get("sort_onesweep", {"launches": 0, "ms": 0.0, "bytes": 0.0})
@@ -433,6 +444,8 @@ def main():
             "per_op": {p: {"mops": (ops[p] / (statistics.median(per_phase[p]) * 1e-3) / 1e6) if p in ops else None,
                            "ms_p50": statistics.median(per_phase[p]),
                            "ms_p99": float(np.percentile(per_phase[p], 99))} for p in phases},
+            "outside_step": {"predecessor": {"mops": (1 << LOG_Q) / (statistics.median(pred_ms) * 1e-3) / 1e6,
+                                             "ms_p50": statistics.median(pred_ms), "queries": 1 << LOG_Q}},
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
             "roofline": roofline, "apply_roofline": apply_roofline, "gpu_launches": launches,
             "clocks": clocks}

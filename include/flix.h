@@ -59,7 +59,9 @@ enum {
     FLIX_OP_SUCC = 2,      /* successor: smallest stored key >= key (Sec. 6.5) */
     FLIX_OP_RANGE = 3,     /* all pairs with lo <= key <= hi; lo = key, hi = aux (named in Sec. 2.1) */
     FLIX_OP_INSERT = 4,    /* insert (key, aux) if key is absent (Sec. 3.2, Sec. 4.3.2) */
-    FLIX_OP_DELETE = 5     /* physical delete (Sec. 3.2, Sec. 4.4) */
+    FLIX_OP_DELETE = 5,    /* physical delete (Sec. 3.2, Sec. 4.4) */
+    FLIX_OP_PRED = 6       /* predecessor: largest stored key <= key (named in Sec. 2.1; the mirror
+                              of the successor of Sec. 6.5) */
 };
 
 typedef struct {
@@ -141,6 +143,12 @@ int flix_lookup_noalloc(flix_t h, const void* d_keys, uint64_t n, void* d_vals_o
 int flix_successor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out,
                    void* stream);
 
+/* Predecessor queries (largest stored key <= key; the paper names predecessor in Sec. 2.1 without
+ * defining it, and this is the mirror of Sec. 6.5's successor): d_keys_out[i], d_vals_out[i], or
+ * (KEY_MAX, VAL_NONE) when none exists.  Asynchronous. */
+int flix_predecessor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out,
+                     void* stream);
+
 /* Range queries [d_lo[i], d_hi[i]] (inclusive; empty when lo > hi): pairs ascending per query,
  * concatenated in query order; d_offsets_out[n+1] (uint64) holds each query's start and the total.
  * d_keys_out/d_vals_out hold out_capacity pairs.  Synchronises to read the total into
@@ -162,6 +170,7 @@ int flix_delete(flix_t h, const void* d_keys, uint64_t n, void* stream);
  * Reads see the pre-batch state.  Per op i:
  *   LOOKUP: d_vals_out[i] = value or VAL_NONE, d_found[i] = hit, d_keys_out[i] = key or KEY_MAX
  *   SUCC  : d_keys_out[i], d_vals_out[i] = successor pair or (KEY_MAX, VAL_NONE), d_found[i]
+ *   PRED  : d_keys_out[i], d_vals_out[i] = predecessor pair or (KEY_MAX, VAL_NONE), d_found[i]
  *   others: (KEY_MAX, VAL_NONE, 0)
  * d_range_off[n+1]: exclusive prefix of range result counts (0 for non-range ops); the pairs go to
  * d_range_keys/d_range_vals (capacity range_cap).  Any output pointer may be NULL if the batch has

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "flix_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE = 0, 1, 2, 3, 4, 5
+OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE, OP_PRED = 0, 1, 2, 3, 4, 5, 6
 
 _lib = None
 
@@ -252,6 +252,18 @@ def sorted_lookup(sorted_keys: np.ndarray, sorted_vals: np.ndarray, q: np.ndarra
     none = np.uint64(key_max(kw))
     vals = np.where(hit, sorted_vals[pc] if sorted_keys.size else none, none).astype(np.uint64)
     return vals, hit.astype(np.uint8)
+
+
+def sorted_predecessor(sorted_keys: np.ndarray, sorted_vals: np.ndarray, q: np.ndarray, kw: int):
+    """Largest stored key <= q (KEY_MAX, VAL_NONE, not found when none), by binary search."""
+    p = np.searchsorted(sorted_keys, q, side="right")
+    ok = p > 0
+    pc = np.maximum(p - 1, 0)
+    none = np.uint64(key_max(kw))
+    if sorted_keys.size == 0:
+        return np.full(q.size, none), np.full(q.size, none), np.zeros(q.size, np.uint8)
+    return (np.where(ok, sorted_keys[pc], none).astype(np.uint64),
+            np.where(ok, sorted_vals[pc], none).astype(np.uint64), ok.astype(np.uint8))
 
 
 def sorted_successor(sorted_keys: np.ndarray, sorted_vals: np.ndarray, q: np.ndarray, kw: int):

@@ -43,7 +43,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OP_NOP = 0, OP_LOOKUP = 1, OP_SUCC = 2, OP_RANGE = 3, OP_INSERT = 4, OP_DELETE = 5 };
+enum { OP_NOP = 0, OP_LOOKUP = 1, OP_SUCC = 2, OP_RANGE = 3, OP_INSERT = 4, OP_DELETE = 5, OP_PRED = 6 };
 /* Net effect of a key's update run (composition of its inserts and deletes in submission order). */
 enum { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
 
@@ -183,6 +183,8 @@ int om_map_bulk_load(om_map* m, const uint64_t* keys, const uint64_t* vals, size
  *   LOOKUP: out_val = value or VAL_NONE, out_found = hit, out_key = key if hit else KEY_MAX
  *   SUCC  : out_key = smallest stored key >= key (KEY_MAX if none), out_val its value (VAL_NONE),
  *           out_found = exists
+ *   PRED  : out_key = largest stored key <= key (KEY_MAX if none), out_val its value (VAL_NONE),
+ *           out_found = exists (the mirror of SUCC; the paper names predecessor without defining it)
  *   other : out_key = KEY_MAX, out_val = VAL_NONE, out_found = 0
  * range_off[n+1] (if non-NULL): exclusive prefix of the per-op range counts |{k : lo <= k <= hi}|
  * for RANGE ops (lo = key, hi = aux; empty when lo > hi) and 0 for all other ops. */
@@ -203,6 +205,9 @@ void om_map_read(const om_map* m, size_t n, const uint8_t* ops, const uint64_t* 
         } else if (ops[i] == OP_SUCC) {
             size_t p = lower_bound_u64(m->k, m->n, keys[i]);
             if (p < m->n) { ok = m->k[p]; ov = m->v[p]; of = 1; }
+        } else if (ops[i] == OP_PRED) {
+            size_t p = upper_bound_u64(m->k, m->n, keys[i]);
+            if (p > 0) { ok = m->k[p - 1]; ov = m->v[p - 1]; of = 1; }
         } else if (ops[i] == OP_RANGE) {
             if (keys[i] <= aux[i]) {
                 size_t a = lower_bound_u64(m->k, m->n, keys[i]);
@@ -647,7 +652,7 @@ int64_t om_model_restructure(om_model* m)
 
 /* Reads through the structure.  Queries are sorted by key and each bucket pulls its sublist by a
  * binary search for maxBucket_{i-1} (Sec. 3.3); each query walks to the first node with
- * k <= maxKey.  Output conventions match om_map_read (LOOKUP and SUCC only). */
+ * k <= maxKey.  Output conventions match om_map_read (LOOKUP, SUCC and PRED only). */
 void om_model_read(const om_model* m, uint64_t n, const uint8_t* ops, const uint64_t* keys,
                    uint64_t* out_val, uint8_t* out_found, uint64_t* out_key)
 {
@@ -686,6 +691,25 @@ void om_model_read(const om_model* m, uint64_t n, const uint8_t* ops, const uint
                     if (x == NIL) break;
                 }
                 if (x != NIL) { out_key[i] = m->keys[x * m->NS + p]; out_val[i] = m->vals[x * m->NS + p]; out_found[i] = 1; }
+            } else if (r[j].op == OP_PRED) {
+                /* the largest stored key <= q: in this node below the first key > q, else the last
+                 * key of the nearest non-empty node before it in chain and bucket order */
+                uint32_t pu = (uint32_t)upper_bound_u64(nk, sz, q);
+                int64_t px = NIL;
+                uint32_t pp = 0;
+                if (pu > 0) {
+                    px = x;
+                    pp = pu - 1;
+                } else {
+                    /* earlier nodes of this bucket's chain */
+                    for (int64_t y = m->head[b]; y != x; y = m->next[y])
+                        if (m->size[y] > 0) { px = y; pp = m->size[y] - 1; }
+                    /* else the last non-empty node of an earlier bucket */
+                    for (int64_t bb = (int64_t)b - 1; px == NIL && bb >= 0; bb--)
+                        for (int64_t y = m->head[bb]; y != NIL; y = m->next[y])
+                            if (m->size[y] > 0) { px = y; pp = m->size[y] - 1; }
+                }
+                if (px != NIL) { out_key[i] = m->keys[px * m->NS + pp]; out_val[i] = m->vals[px * m->NS + pp]; out_found[i] = 1; }
             }
         }
     }

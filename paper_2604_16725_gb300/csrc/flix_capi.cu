@@ -853,6 +853,15 @@ int flix_successor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, v
                                             (uint64_t*)d_vals_out, nullptr, S(stream)));
 }
 
+int flix_predecessor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out, void* stream)
+{
+    if (!h || (n && (!d_keys || !d_keys_out || !d_vals_out)) || too_big(n)) return FLIX_EINVAL;
+    return DISPATCH(do_read_point<uint32_t>(h, FLIX_OP_PRED, (const uint32_t*)d_keys, n, (uint32_t*)d_keys_out,
+                                            (uint32_t*)d_vals_out, nullptr, S(stream)),
+                    do_read_point<uint64_t>(h, FLIX_OP_PRED, (const uint64_t*)d_keys, n, (uint64_t*)d_keys_out,
+                                            (uint64_t*)d_vals_out, nullptr, S(stream)));
+}
+
 int flix_range(flix_t h, const void* d_lo, const void* d_hi, uint64_t n, uint64_t* d_offsets_out, void* d_keys_out,
                void* d_vals_out, uint64_t out_capacity, uint64_t* h_total_out, void* stream)
 {

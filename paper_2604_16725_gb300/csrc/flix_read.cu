@@ -125,11 +125,13 @@ __device__ __forceinline__ uint32_t node_upper_bound(const K* __restrict__ nk, u
     return base;
 }
 
-// From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1).
+// From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1);
+// prev = the node walked past last (NIL when the walk ends at the first node).
 template <class K>
 __device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, uint32_t& node, uint32_t& sz, K& bd,
-                                          uint32_t& nx)
+                                          uint32_t& nx, uint32_t& prev)
 {
+    prev = NIL;
     node = __ldg(ix.head + b);
     sz = __ldg(ix.size + node);
     bd = __ldg(ix.bound + node);
@@ -137,6 +139,7 @@ __device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, 
     uint32_t steps = 0;
     while (q > bd) {
         if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return false; }
+        prev = node;
         node = nx;
         sz = __ldg(ix.size + node);
         bd = __ldg(ix.bound + node);
@@ -180,13 +183,50 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
     const K KM = key_max<K>();
     K rk = KM, rv = KM;
     uint8_t f = 0;
-    if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC) {
+    if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC || op == FLIX_OP_PRED) {
         const K q = skeys[j];
         const uint32_t b = bk[j];
         const uint32_t NS = ix.NS;
-        uint32_t node, sz, nx;
+        uint32_t node, sz, nx, prev;
         K bd;
-        if (find_node(ix, b, q, node, sz, bd, nx)) {
+        if (!find_node(ix, b, q, node, sz, bd, nx, prev)) {
+            // chain error flagged; default results
+        } else if (op == FLIX_OP_PRED) {
+            // the largest stored key <= q: below the node's first key > q, else the last key of
+            // the node walked past (chain nodes other than a bucket's only node are never empty),
+            // else of the nearest earlier bucket whose chain holds a key
+            const K* nk = ix.keys + (uint64_t)node * NS;
+            const uint32_t pu = node_upper_bound(nk, 0, sz, q);
+            uint32_t pn = NIL, pp = 0;
+            if (pu > 0) {
+                pn = node;
+                pp = pu - 1;
+            } else if (prev != NIL && ix.size[prev] > 0) {
+                pn = prev;
+                pp = ix.size[prev] - 1;
+            } else {
+                uint64_t guard = 0;
+                const uint64_t lim = (uint64_t)ix.cap + ix.nb + 1;
+                for (int64_t bb = (int64_t)b - 1; bb >= 0 && pn == NIL && guard < lim; bb--) {
+                    uint32_t x = ix.head[bb];
+                    uint32_t last = x;
+                    while (x != NIL && guard++ < lim) {
+                        last = x;
+                        x = ix.next[x];
+                    }
+                    const uint32_t ls = ix.size[last];
+                    if (ls > 0) {
+                        pn = last;
+                        pp = ls - 1;
+                    }
+                }
+            }
+            if (pn != NIL) {
+                rk = ix.keys[(uint64_t)pn * NS + pp];
+                rv = ix.vals[(uint64_t)pn * NS + pp];
+                f = 1;
+            }
+        } else {
             const K* nk = ix.keys + (uint64_t)node * NS;
             const uint32_t pos = node_lower_bound(nk, sz, q);
             if (op == FLIX_OP_LOOKUP) {
@@ -292,7 +332,8 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const 
     uint32_t node, sz, nx;
     K bd;
     uint64_t c = 0;
-    if (!find_node(ix, bb, lo, node, sz, bd, nx)) {
+    uint32_t prev;
+    if (!find_node(ix, bb, lo, node, sz, bd, nx, prev)) {
         cnt[idx] = 0;
         start_bucket[j] = bb;
         start_node[j] = ix.head[bb];

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE = 0, 1, 2, 3, 4, 5
+OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE, OP_PRED = 0, 1, 2, 3, 4, 5, 6
 KEY_U32, KEY_U64 = 0, 1
 
 _STATUS = {0: "FLIX_OK", -1: "FLIX_EINVAL", -2: "FLIX_ENOMEM", -3: "FLIX_ECUDA", -4: "FLIX_ETYPE",
@@ -52,6 +52,7 @@ SIGNATURES = {
     "flix_lookup": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_lookup_noalloc": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_successor": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "flix_predecessor": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_range": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_insert": (_INT, [_VP, _VP, _VP, _U64, _VP]),
     "flix_delete": (_INT, [_VP, _VP, _U64, _VP]),
@@ -186,6 +187,14 @@ class Index:
         ko, vo = out if out is not None else (self._empty(q.numel()), self._empty(q.numel()))
         _check(load().flix_successor(self._h, _ptr(q), q.numel(), _ptr(ko), _ptr(vo), _stream(stream)),
                "flix_successor", self._h)
+        return ko, vo
+
+    def predecessor(self, keys, stream=None, out=None):
+        """out: optional (keys_out, vals_out) device tensors of at least len(keys) elements."""
+        q = self._dev(keys)
+        ko, vo = out if out is not None else (self._empty(q.numel()), self._empty(q.numel()))
+        _check(load().flix_predecessor(self._h, _ptr(q), q.numel(), _ptr(ko), _ptr(vo), _stream(stream)),
+               "flix_predecessor", self._h)
         return ko, vo
 
     def range(self, lo, hi, capacity=None, stream=None, out=None):

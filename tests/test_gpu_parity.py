@@ -93,8 +93,8 @@ def _random_mixed_sequence(fx, kw, NS, one_pass):
         center = int(rng.integers(0, dom))
         width = dom if b % 3 else max(dom // 200, 64)
         keys = ((center + rng.integers(0, width, n)) % dom).astype(np.uint64)
-        ops = rng.choice([W.OP_LOOKUP, W.OP_SUCC, W.OP_RANGE, W.OP_INSERT, W.OP_INSERT, W.OP_DELETE, W.OP_DELETE,
-                          W.OP_NOP], n).astype(np.uint8)
+        ops = rng.choice([W.OP_LOOKUP, W.OP_SUCC, W.OP_PRED, W.OP_RANGE, W.OP_INSERT, W.OP_INSERT, W.OP_DELETE,
+                          W.OP_DELETE, W.OP_NOP], n).astype(np.uint8)
         # some deletes and lookups of stored keys, some repeated keys inside the batch
         kk, _ = mp.export()
         if kk.size and n:
@@ -267,6 +267,10 @@ def test_read_scale_full_size_sampled(fx):
     esk, esv, _ = oracle.sorted_successor(sk_all, sv_all, q[samp], kw)
     same(np_of(sk, kw)[samp], esk, "succ.keys")
     same(np_of(sv, kw)[samp], esv, "succ.vals")
+    pk, pv = idx.predecessor(qd)
+    epk, epv, _ = oracle.sorted_predecessor(sk_all, sv_all, q[samp], kw)
+    same(np_of(pk, kw)[samp], epk, "pred.keys")
+    same(np_of(pv, kw)[samp], epv, "pred.vals")
     lo, hi = c["range_lo"], c["range_hi"]
     off, rk, rv = idx.range(lo, hi)
     offn = off.cpu().numpy().view(np.uint64)
@@ -299,6 +303,10 @@ def test_large_read_batches_every_output(fx):
     esk, esv, _ = oracle.sorted_successor(load, vals, q, kw)
     same(np_of(sk, kw), esk, "succ.keys")
     same(np_of(sv, kw), esv, "succ.vals")
+    pk, pv = idx.predecessor(qd)
+    epk, epv, _ = oracle.sorted_predecessor(load, vals, q, kw)
+    same(np_of(pk, kw), epk, "pred.keys")
+    same(np_of(pv, kw), epv, "pred.vals")
 
 
 @pytest.mark.parametrize("one_pass", [True, False])
@@ -369,3 +377,28 @@ def test_heavy_node_batches(fx, kw, NS):
     md.update(np.full(dk.size, W.OP_DELETE, np.uint8), dk)
     compare_layout(idx, md)
     compare_contents(idx, mp, kw)
+
+
+@pytest.mark.parametrize("kw,NS", [(32, 2), (64, 8)])
+def test_predecessor_edges(fx, kw, NS):
+    """Predecessor below every key, at every stored key, between keys, and across buckets emptied by
+    deletes (their only node stays empty, so the walk continues into earlier buckets)."""
+    dt = np.uint32 if kw == 32 else np.uint64
+    load = np.arange(100, 100 + 10 * 400, 10, dtype=np.uint64)
+    vals = load + np.uint64(7)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    idx.bulk_load(load.astype(dt), vals.astype(dt))
+    mp, md = oracle_pair(kw, NS, 50, load, vals)
+    # empty a run of buckets in the middle and some single keys elsewhere
+    dk = np.concatenate([load[100:260], load[::37]])
+    idx.delete(dk.astype(dt))
+    mp.update(np.full(dk.size, W.OP_DELETE, np.uint8), dk)
+    md.update(np.full(dk.size, W.OP_DELETE, np.uint8), dk)
+    compare_layout(idx, md)
+    q = np.concatenate([np.arange(0, 4200, 3, dtype=np.uint64), load, np.array([0, 99, 100, 101], np.uint64)])
+    pk, pv = idx.predecessor(q.astype(dt))
+    e = mp.read(np.full(q.size, W.OP_PRED, np.uint8), q)
+    same(np_of(pk, kw), e["keys"], "pred.keys")
+    same(np_of(pv, kw), e["vals"], "pred.vals")
+    em = md.read(np.full(q.size, W.OP_PRED, np.uint8), q)
+    same(em["keys"], e["keys"], "model.pred.keys")

@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 
-L, S, R, I, D = oracle.OP_LOOKUP, oracle.OP_SUCC, oracle.OP_RANGE, oracle.OP_INSERT, oracle.OP_DELETE
+L, S, R, I, D, P = (oracle.OP_LOOKUP, oracle.OP_SUCC, oracle.OP_RANGE, oracle.OP_INSERT, oracle.OP_DELETE,
+                    oracle.OP_PRED)
 
 
 def brute(state, ops, keys, aux, kw):
@@ -27,6 +28,10 @@ def brute(state, ops, keys, aux, kw):
                 if kk >= k:
                     ok, ov, of = kk, vv, 1
                     break
+        elif op == P:
+            for kk, vv in items:
+                if kk <= k:
+                    ok, ov, of = kk, vv, 1
         elif op == R:
             for kk, vv in items:
                 if k <= kk <= a:
@@ -47,14 +52,14 @@ def brute(state, ops, keys, aux, kw):
 def check_batch(mp, md, state, ops, keys, aux, kw):
     r_map, st = mp.apply(ops, keys, aux)
     assert st == 0
-    # the structural model answers lookups and successors through its buckets and chains
+    # the structural model answers lookups, successors and predecessors through its buckets and chains
     rm = md.read(ops, keys)
     md.update(ops, keys, aux)
     exp = brute(state, ops, keys, aux, kw)
     for f in ("keys", "vals", "found", "range_off", "range_keys", "range_vals"):
         assert r_map[f].tolist() == exp[f], f
     for i, op in enumerate(ops):
-        if op in (L, S):
+        if op in (L, S, P):
             assert int(rm["keys"][i]) == exp["keys"][i]
             assert int(rm["vals"][i]) == exp["vals"][i]
             assert int(rm["found"][i]) == exp["found"][i]
@@ -86,12 +91,12 @@ def test_single_key_runs_exhaustive():
 def test_all_two_op_batches_small_domain(NS):
     """Every prior subset of a 5-key domain x every batch of two ops over it."""
     dom = [1, 3, 5, 7, 9]
-    singles = [(op, k) for op in (L, S, R, I, D) for k in range(0, 11)]
+    singles = [(op, k) for op in (L, S, P, R, I, D) for k in range(0, 11)]
     rng = random.Random(NS)
     for mask in range(1 << len(dom)):
         prior = {k: 10 * k for j, k in enumerate(dom) if mask >> j & 1}
         for (o1, k1), (o2, k2) in itertools.product(singles, repeat=2):
-            if rng.random() > 0.08:          # a fixed, seeded 8% of the 3,872 pairs per subset
+            if rng.random() > 0.08:          # a fixed, seeded 8% of the 4,356 pairs per subset
                 continue
             mp = oracle.Map(64)
             mp.bulk_load(list(prior), list(prior.values()))
@@ -122,7 +127,7 @@ def test_random_batch_sequences(seed):
         width = dom if b % 2 else max(2, dom // 10)
         ops, keys, aux = [], [], []
         for _ in range(n):
-            op = rng.choice([L, S, R, I, I, D, D])
+            op = rng.choice([L, S, P, R, I, I, D, D])
             k = (lo + rng.randrange(width)) % dom
             ops.append(op)
             keys.append(k)

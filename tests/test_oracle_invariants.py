@@ -82,7 +82,7 @@ def test_update_rounds_with_skew_and_restructure(NS, kw):
             assert np.array_equal(k, d2["keys"]) and np.array_equal(v, d2["vals"])
 
 
-def test_successor_and_range_vs_linear_scan():
+def test_successor_predecessor_and_range_vs_linear_scan():
     rng = np.random.default_rng(7)
     for kw in (32, 64):
         keys = np.unique(rng.integers(0, 5000, 700).astype(np.uint64))
@@ -105,9 +105,20 @@ def test_successor_and_range_vs_linear_scan():
             inr = [x for x in allk if q[i] <= x <= hi[i]]
             a, b = int(rr["range_off"][i]), int(rr["range_off"][i + 1])
             assert rr["range_keys"][a:b].tolist() == inr
+        # predecessor: the largest stored key <= q, by a linear scan
+        rp = mp.read(np.full(400, W.OP_PRED, np.uint8), q)
+        for i in range(400):
+            pred = [j for j, x in enumerate(allk) if x <= q[i]]
+            if pred:
+                assert int(rp["keys"][i]) == allk[pred[-1]] and int(rp["vals"][i]) == allv[pred[-1]]
+                assert rp["found"][i] == 1
+            else:
+                assert int(rp["keys"][i]) == km and int(rp["vals"][i]) == km and rp["found"][i] == 0
         # the numpy sampled helpers agree with the map (they serve the full-size sampled checks)
         sk, sv, sf = oracle.sorted_successor(keys, vals, q, kw)
         assert np.array_equal(sk, r["keys"]) and np.array_equal(sv, r["vals"])
+        pk, pv, pf = oracle.sorted_predecessor(keys, vals, q, kw)
+        assert np.array_equal(pk, rp["keys"]) and np.array_equal(pv, rp["vals"]) and np.array_equal(pf, rp["found"])
         cnt = oracle.sorted_range_counts(keys, q, hi)
         assert np.array_equal(cnt, np.diff(rr["range_off"]))
 

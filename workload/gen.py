@@ -21,13 +21,13 @@ import math
 
 import numpy as np
 
-OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE = 0, 1, 2, 3, 4, 5
+OP_NOP, OP_LOOKUP, OP_SUCC, OP_RANGE, OP_INSERT, OP_DELETE, OP_PRED = 0, 1, 2, 3, 4, 5, 6
 
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 
 __all__ = [
-    "OP_NOP", "OP_LOOKUP", "OP_SUCC", "OP_RANGE", "OP_INSERT", "OP_DELETE",
+    "OP_NOP", "OP_LOOKUP", "OP_SUCC", "OP_RANGE", "OP_INSERT", "OP_DELETE", "OP_PRED",
     "key_max", "mix64", "mix32", "uniform01", "universe", "values_for", "zipf",
     "scramble30", "scramble_bits", "universe_at", "log_uniform_sizes", "permutation",
     "config1", "read_scale", "update_heavy", "mixed_stream", "serving_requests",
