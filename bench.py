@@ -299,7 +299,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="flix", choices=["flix", "reference"])
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "update_heavy"],
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "update_heavy", "xy"],
                     help="plain: the read-scale step (default); batched: mixed-batch stream through CUDA "
                          "graphs vs plain launches; served: continuous batching under Poisson arrivals")
     ap.add_argument("--batches", type=int, default=300, help="batched form: stream length")
@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
     ap.add_argument("--log-q", type=int, default=LOG_Q, help="log2 of the lookup/successor batch")
     ap.add_argument("--sort-variant", type=int, default=0, help="0 auto, 1 one-sweep, 2 reduce-then-scan")
+    ap.add_argument("--xy-max-build", type=int, default=100_000_000,
+                    help="xy form: largest build of the restructure accounting (1M, 33M, 100M)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -318,6 +320,8 @@ def main():
         return bench_served(args)
     if args.form == "update_heavy":
         return bench_update_heavy(args)
+    if args.form == "xy":
+        return bench_xy(args)
 
     import torch
     rank, world, local = dist_env()
@@ -702,6 +706,111 @@ def bench_update_heavy(args):
             "config": {"workload": "update heavy: uint32, node size 32, start empty; %d insert batches of 2^20 per "
                                    "distribution, then 32 delete batches removing 50%%, final restructure" % n_batches},
             "distributions": out}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_xy(args):
+    """Dense-range (X/Y) update rounds, uint64 keys, node size 32 (Sec. 5.2.1 workloads).
+
+    Rounds: build 2^24 uniform keys; 8 insert rounds of 3 * 2^21 keys (300% growth), Y = 90% of each
+    round inside a hot interval covering X of the key range, X from 90% (uniform) down to 2%; after
+    every insert round a batch of 2^25 lookups of stored keys (the skew experiment of Sec. 6.4); then
+    8 delete rounds removing the inserted keys.  Restructure accounting (Sec. 6.6, Tab. 2): builds
+    of 1M, 33M and 100M keys, 8 insert rounds to 4x the build at X25Y90 and X90Y90, 8 delete rounds,
+    then one restructure: nodes before and after, and the share recovered.  Every call is timed with
+    CUDA events on its stream, inputs resident on the device."""
+    import torch
+    import paper_2604_16725_gb300 as fx
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()  # noqa: E731
+    st = torch.cuda.Stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    rounds_out = {}
+    tot_ops, tot_ms = 0, 0.0
+    build = 1 << 24
+    for X in (0.9, 0.5, 0.25, 0.12, 0.03, 0.02):
+        w = W.xy_rounds(X, 0.9, build, 3 * build, 8, seed=6000, kw=64)
+        idx = fx.Index(key_bits=64, node_size=32)
+        idx.bulk_load(td(w["build_keys"]), td(w["build_vals"]), stream=st)
+        present = [w["build_keys"]]
+        ins_ms, q_ms, del_ms, chains = [], [], [], []
+        outv = torch.empty(1 << 25, dtype=torch.int64, device="cuda")
+        for r, (k, v) in enumerate(w["insert"]):
+            kd, vd = td(k), td(v)
+            ins_ms.append(timed(lambda: idx.insert(kd, vd, stream=st)))
+            present.append(k)
+            allk = np.concatenate(present)
+            q = td(allk[(W.uniform01(6000 + r, 6, 1 << 25) * allk.size).astype(np.int64)])   # hits, repeats allowed
+            idx.lookup(q, stream=st, out=outv, found=False)           # warm (first touch of new nodes)
+            q_ms.append(timed(lambda: idx.lookup(q, stream=st, out=outv, found=False)))
+            chains.append(idx.stats(stream=st)["max_chain"])
+        for k in w["delete"]:
+            kd = td(k)
+            del_ms.append(timed(lambda: idx.delete(kd, stream=st)))
+        n_ins = sum(k.size for k, _ in w["insert"])
+        n_del = sum(k.size for k in w["delete"])
+        tot_ops += n_ins + n_del
+        tot_ms += sum(ins_ms) + sum(del_ms)
+        rounds_out["X%dY90" % round(100 * X)] = {
+            "insert_mops_per_round": [round(k.size / (t * 1e-3) / 1e6, 1) for (k, _), t in zip(w["insert"], ins_ms)],
+            "lookup_2e25_ms_per_round": [round(t, 3) for t in q_ms],
+            "delete_mops_per_round": [round(k.size / (t * 1e-3) / 1e6, 1) for k, t in zip(w["delete"], del_ms)],
+            "max_chain_per_round": chains,
+            "insert_mops": n_ins / (sum(ins_ms) * 1e-3) / 1e6, "delete_mops": n_del / (sum(del_ms) * 1e-3) / 1e6}
+        log("X=%g: %s" % (X, rounds_out["X%dY90" % round(100 * X)]))
+        idx.close()
+        torch.cuda.empty_cache()
+
+    table = []
+    for b in (1 << 20, 1 << 25, 100_000_000):
+        if b > args.xy_max_build:
+            continue
+        for X in (0.25, 0.9):
+            w = W.xy_rounds(X, 0.9, b, 3 * b, 8, seed=6100, kw=64)
+            idx = fx.Index(key_bits=64, node_size=32)
+            idx.bulk_load(td(w["build_keys"]), td(w["build_vals"]), stream=st)
+            t_ins = t_del = 0.0
+            for k, v in w["insert"]:
+                kd, vd = td(k), td(v)
+                t_ins += timed(lambda: idx.insert(kd, vd, stream=st))
+                del kd, vd
+            s_ins = idx.stats(stream=st)
+            for k in w["delete"]:
+                kd = td(k)
+                t_del += timed(lambda: idx.delete(kd, stream=st))
+                del kd
+            s_del = idx.stats(stream=st)
+            t_res = timed(lambda: idx.restructure(stream=st))
+            s_res = idx.stats(stream=st)
+            row = {"workload": "X%dY90" % round(100 * X), "build": b, "final": s_ins["live_keys"],
+                   "nodes_after_inserts": s_ins["nodes_used"], "max_chain": s_ins["max_chain"],
+                   "nodes_before_restructure": s_del["nodes_used"], "nodes_after_restructure": s_res["nodes_used"],
+                   "nodes_recovered": s_del["nodes_used"] - s_res["nodes_used"],
+                   "recovered_pct": 100.0 * (s_del["nodes_used"] - s_res["nodes_used"]) / max(s_del["nodes_used"], 1),
+                   "restructure_ms": t_res, "insert_mops": 3 * b / (t_ins * 1e-3) / 1e6,
+                   "delete_mops": 3 * b / (t_del * 1e-3) / 1e6}
+            log("restructure accounting: %s" % row)
+            table.append(row)
+            idx.close()
+            del w
+            torch.cuda.empty_cache()
+
+    line = {"form": "xy", "metric": METRIC, "value": tot_ops / (tot_ms * 1e-3) / 1e6, "unit": "Mops/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "dense-range updates: uint64, node size 32, build 2^24 uniform, 8 insert rounds "
+                                   "of 3*2^21 keys with 90% in a hot interval of X of the key range, 8 delete "
+                                   "rounds of the same keys; value = all insert and delete ops / their time"},
+            "rounds": rounds_out, "restructure_accounting": table}
     print(json.dumps(line))
     return 0
 

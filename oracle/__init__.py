@@ -71,6 +71,11 @@ def lib():
         L.om_model_update.argtypes = [vp, u64, vp, vp, vp]
         L.om_model_restructure.restype = ctypes.c_int64
         L.om_model_restructure.argtypes = [vp]
+        L.om_model_split_chains.restype = u64
+        L.om_model_split_chains.argtypes = [vp, u64]
+        L.om_model_merge_underfull_all.restype = u64
+        L.om_model_merge_underfull_all.argtypes = [vp]
+        L.om_model_set_policy.argtypes = [vp, u64, i32]
         L.om_model_read.argtypes = [vp, u64, vp, vp, vp, vp, vp]
         L.om_model_dump.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         L.om_model_check.restype = i32
@@ -182,6 +187,19 @@ class Model:
 
     def restructure(self) -> int:
         return int(lib().om_model_restructure(self._h))
+
+    def split_chains(self, max_chain: int) -> int:
+        """Elastic split of every bucket whose chain is longer than max_chain; returns buckets added."""
+        return int(lib().om_model_split_chains(self._h, max_chain))
+
+    def merge_underfull_all(self) -> int:
+        """Underfull-neighbour merge in every bucket; returns nodes freed."""
+        return int(lib().om_model_merge_underfull_all(self._h))
+
+    def set_policy(self, split_over: int = 0, merge_underfull: bool = False):
+        """Maintenance after every update batch, in the buckets the batch touched: merge underfull
+        neighbours, then split chains longer than split_over (0: off)."""
+        lib().om_model_set_policy(self._h, split_over, 1 if merge_underfull else 0)
 
     def read(self, ops, keys):
         o, k = _u8(ops), _u64(keys)

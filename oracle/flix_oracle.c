@@ -353,6 +353,9 @@ typedef struct {
     uint64_t nb, nb_cap;
     uint64_t* mkba;
     int64_t* head;
+    /* maintenance after every update batch (0: off) */
+    uint64_t split_over;      /* elastic split of touched buckets with chains longer than this */
+    int merge_underfull;      /* merge underfull neighbours in touched buckets */
 } om_model;
 
 static void model_grow(om_model* m, uint64_t want)
@@ -568,9 +571,101 @@ static void model_apply_bucket(om_model* m, uint64_t b, const uint64_t* uk, cons
     free(dropped);
 }
 
+/* Underfull-node merge (the paper names it as a possible addition to deletion, Sec. 5.4.1, and
+ * restructuring merges underfull nodes into half-full ones, Sec. 6.6).  Reading: walk the bucket's
+ * chain; while the current node and the next one hold at most NS/2 pairs together, the next node's
+ * pairs are appended to the current node (they are all larger), the current node takes over its
+ * maxKey and node-link, and the next node is freed; otherwise the walk moves on to the next node.
+ * The merged node is at most half full.  Returns the number of nodes freed. */
+static uint64_t model_merge_underfull(om_model* m, uint64_t b)
+{
+    const uint32_t NS = m->NS;
+    uint64_t freed = 0;
+    int64_t a = m->head[b];
+    while (a != NIL && m->next[a] != NIL) {
+        int64_t x = m->next[a];
+        if (m->size[a] + m->size[x] <= NS / 2) {
+            for (uint32_t s = 0; s < m->size[x]; s++) {
+                m->keys[a * NS + m->size[a] + s] = m->keys[x * NS + s];
+                m->vals[a * NS + m->size[a] + s] = m->vals[x * NS + s];
+            }
+            m->size[a] += m->size[x];
+            m->bound[a] = m->bound[x];
+            m->next[a] = m->next[x];
+            node_free(m, x);
+            freed++;
+        } else {
+            a = x;
+        }
+    }
+    return freed;
+}
+
+/* Elastic bucket split (Sec. 3.4: buckets with long chains of nodes may be split, which narrows the
+ * key range each bucket covers).  Reading: a bucket whose chain holds more than T nodes (among the
+ * flagged buckets; all of them when flags is NULL) becomes one bucket per node, in chain order, and
+ * each new bucket's maxBucket is its node's maxKey (the chain's last node already carries the old
+ * maxBucket).  No pair moves.  Returns the number of buckets added. */
+static uint64_t model_split(om_model* m, uint64_t T, const uint8_t* flags)
+{
+    uint64_t nb2 = 0;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint64_t L = 0;
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x]) L++;
+        nb2 += ((!flags || flags[b]) && L > T) ? L : 1;
+    }
+    if (nb2 == m->nb) return 0;
+    uint64_t* mk2 = (uint64_t*)malloc(nb2 * sizeof(uint64_t));
+    int64_t* hd2 = (int64_t*)malloc(nb2 * sizeof(int64_t));
+    uint64_t o = 0;
+    for (uint64_t b = 0; b < m->nb; b++) {
+        uint64_t L = 0;
+        for (int64_t x = m->head[b]; x != NIL; x = m->next[x]) L++;
+        if ((!flags || flags[b]) && L > T) {
+            int64_t x = m->head[b];
+            while (x != NIL) {
+                int64_t nx = m->next[x];
+                hd2[o] = x;
+                mk2[o] = m->bound[x];
+                m->next[x] = NIL;
+                o++;
+                x = nx;
+            }
+        } else {
+            hd2[o] = m->head[b];
+            mk2[o] = m->mkba[b];
+            o++;
+        }
+    }
+    uint64_t added = nb2 - m->nb;
+    free(m->mkba);
+    free(m->head);
+    m->mkba = mk2;
+    m->head = hd2;
+    m->nb = m->nb_cap = nb2;
+    return added;
+}
+
+uint64_t om_model_split_chains(om_model* m, uint64_t T) { return model_split(m, T, NULL); }
+
+uint64_t om_model_merge_underfull_all(om_model* m)
+{
+    uint64_t freed = 0;
+    for (uint64_t b = 0; b < m->nb; b++) freed += model_merge_underfull(m, b);
+    return freed;
+}
+
+void om_model_set_policy(om_model* m, uint64_t split_over, int merge_underfull)
+{
+    m->split_over = split_over;
+    m->merge_underfull = merge_underfull;
+}
+
 /* Inserts and deletes of one batch: sort the update list, reduce each key's run to its net effect,
- * then every bucket pulls its sublist by binary search (Sec. 3.3, Sec. 4.1).  Returns -1
- * (unchanged) if an insert carries KEY_MAX. */
+ * then every bucket pulls its sublist by binary search (Sec. 3.3, Sec. 4.1).  With the maintenance
+ * policy on, every bucket whose sublist was non-empty then merges its underfull neighbours, and
+ * after all buckets are done those touched buckets with chains longer than split_over are split.
+ * Returns -1 (unchanged) if an insert carries KEY_MAX. */
 int om_model_update(om_model* m, uint64_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux)
 {
     uint64_t u = 0;
@@ -598,11 +693,18 @@ int om_model_update(om_model* m, uint64_t n, const uint8_t* ops, const uint64_t*
         uk[U] = r[j].key; uv[U] = val; ue[U] = eff; U++;
         j = e;
     }
+    uint8_t* touched = (uint8_t*)calloc(m->nb ? m->nb : 1, 1);
     for (uint64_t b = 0; b < m->nb; b++) {
         uint64_t start = b == 0 ? 0 : upper_bound_u64(uk, U, m->mkba[b - 1]);
         uint64_t end = upper_bound_u64(uk, U, m->mkba[b]);
-        if (start < end) model_apply_bucket(m, b, uk + start, ue + start, uv + start, end - start);
+        if (start < end) {
+            model_apply_bucket(m, b, uk + start, ue + start, uv + start, end - start);
+            touched[b] = 1;
+            if (m->merge_underfull) model_merge_underfull(m, b);
+        }
     }
+    if (m->split_over) model_split(m, m->split_over, touched);
+    free(touched);
     free(r); free(uk); free(uv); free(ue);
     return 0;
 }

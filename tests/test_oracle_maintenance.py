@@ -1,0 +1,162 @@
+"""Pins of the oracle's chain maintenance (CPU only): the elastic bucket split of Sec. 3.4 and the
+underfull-node merge that Sec. 5.4.1 names as a possible addition to deletion (readings: a split
+bucket becomes one bucket per node of its chain, with the node's maxKey as maxBucket; a merge folds
+a chain's next node into the current one while both together hold at most NS/2 pairs).
+
+* A worked example with NS = 4, derived by hand from those readings and from the canonical split
+  layout of an overflowing node (pieces of NS/2, the remainder in the last).
+* Random batch sequences with the maintenance policy on: invariants, contents and reads (lookup,
+  successor, predecessor) agree with the ordered map after every batch; with the split on no chain
+  is longer than the threshold; with the merge on no two neighbouring nodes of a chain hold NS/2
+  pairs or fewer together; a split moves no pair.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload as W
+
+KMAX64 = (1 << 64) - 1
+
+
+def _layout(md):
+    d = md.dump()
+    nodes, pos = [], 0
+    for n, b in zip(d["node_size"], d["node_bound"]):
+        nodes.append((list(int(x) for x in d["keys"][pos:pos + n]), int(b)))
+        pos += n
+    return [int(x) for x in d["mkba"]], [int(x) for x in d["chain_len"]], nodes
+
+
+def _ins(md, keys):
+    k = np.array(keys, np.uint64)
+    assert md.update(np.full(k.size, W.OP_INSERT, np.uint8), k, k + np.uint64(1000)) == 0
+
+
+def _del(md, keys):
+    k = np.array(keys, np.uint64)
+    assert md.update(np.full(k.size, W.OP_DELETE, np.uint8), k) == 0
+
+
+def _worked_start(merge):
+    # NS = 4, fill 50%: p = 2.  Build [10 20 | 30 40 | 50 60]; maxBucket 20, 40, KEY_MAX.
+    md = oracle.Model(64, 4, 50)
+    k = np.array([10, 20, 30, 40, 50, 60], np.uint64)
+    assert md.bulk_load(k, k + np.uint64(1000)) == 0
+    md.set_policy(0, merge)
+    # 11..15 go to bucket 0: its node merges to 7 keys, more than NS, so it becomes floor(7/2) = 3
+    # pieces of 2, 2 and 3 keys; the first two take their largest key as maxKey.
+    _ins(md, [11, 12, 13, 14, 15])
+    assert _layout(md) == ([20, 40, KMAX64], [3, 1, 1],
+                           [([10, 11], 11), ([12, 13], 13), ([14, 15, 20], 20), ([30, 40], 40),
+                            ([50, 60], KMAX64)])
+    return md
+
+
+def test_worked_example_merge_on_delete():
+    md = _worked_start(merge=True)           # no neighbours of the 2-2-3 chain fit in NS/2 = 2
+    # deleting 11, 12, 14, 15 leaves 1-1-1: the first two fold into [10 13] (2 <= 2), which then
+    # stays apart from [20] (3 > 2)
+    _del(md, [11, 12, 14, 15])
+    assert _layout(md) == ([20, 40, KMAX64], [2, 1, 1],
+                           [([10, 13], 13), ([20], 20), ([30, 40], 40), ([50, 60], KMAX64)])
+    assert md.check() == 0
+    assert md.stats()["nodes"] == 4
+
+
+def test_worked_example_without_merge():
+    md = _worked_start(merge=False)
+    _del(md, [11, 12, 14, 15])
+    assert _layout(md) == ([20, 40, KMAX64], [3, 1, 1],
+                           [([10], 11), ([13], 13), ([20], 20), ([30, 40], 40), ([50, 60], KMAX64)])
+    assert md.merge_underfull_all() == 1     # the explicit pass reaches the merged layout
+    assert _layout(md)[2][:2] == [([10, 13], 13), ([20], 20)]
+
+
+def test_worked_example_merge_after_last_node_leaves():
+    md = _worked_start(merge=True)
+    # 13 14 15 20 leave: the last node empties and leaves, maxBucket 20 passes to [12]; then
+    # [10 11] + [12] = 3 > 2 keeps them apart
+    _del(md, [13, 14, 15, 20])
+    assert _layout(md) == ([20, 40, KMAX64], [2, 1, 1],
+                           [([10, 11], 11), ([12], 20), ([30, 40], 40), ([50, 60], KMAX64)])
+
+
+def test_worked_example_split():
+    md = _worked_start(merge=False)
+    assert md.split_chains(3) == 0           # no chain longer than 3
+    assert md.split_chains(2) == 2           # bucket 0 becomes three buckets
+    assert _layout(md) == ([11, 13, 20, 40, KMAX64], [1, 1, 1, 1, 1],
+                           [([10, 11], 11), ([12, 13], 13), ([14, 15, 20], 20), ([30, 40], 40),
+                            ([50, 60], KMAX64)])
+    assert md.check() == 0
+    # the next insert into the old range of bucket 0 lands by the new maxBuckets
+    _ins(md, [12 + 0, 16])                   # 12 present: no-op; 16 goes to bucket 2 (<= 20)
+    assert _layout(md)[2][2] == ([14, 15, 16, 20], 20)
+
+
+def _reads_agree(mp, md, kw, rng):
+    kmax = (1 << kw) - 1
+    ex, _ = mp.export()
+    q = np.concatenate([ex, ex + np.uint64(1), rng.integers(0, kmax, 500, dtype=np.uint64)])
+    q = q[q < kmax]
+    for op in (W.OP_LOOKUP, W.OP_SUCC, W.OP_PRED):
+        ops = np.full(q.size, op, np.uint8)
+        a, b = mp.read(ops, q), md.read(ops, q)
+        assert np.array_equal(a["keys"], b["keys"]) and np.array_equal(a["vals"], b["vals"])
+
+
+@pytest.mark.parametrize("kw,NS,split,merge", [(64, 4, 1, False), (64, 8, 2, True), (32, 8, 0, True),
+                                               (32, 16, 3, True), (64, 4, 0, True)])
+def test_random_sequences_with_maintenance(kw, NS, split, merge):
+    rng = np.random.default_rng(100 + NS + split)
+    dom = 3000
+    load = np.unique(rng.integers(0, dom, 300)).astype(np.uint64)
+    mp, md = oracle.Map(kw), oracle.Model(kw, NS, 50)
+    assert mp.bulk_load(load, load * np.uint64(7)) == 0 and md.bulk_load(load, load * np.uint64(7)) == 0
+    md.set_policy(split, merge)
+    for step in range(40):
+        n = int(rng.integers(1, 200))
+        hot = rng.random() < 0.5                             # half the batches hit a narrow range
+        lo = int(rng.integers(0, dom - 100))
+        keys = (rng.integers(lo, lo + 100, n) if hot else rng.integers(0, dom, n)).astype(np.uint64)
+        ops = np.where(rng.random(n) < (0.7 if step < 20 else 0.3), W.OP_INSERT, W.OP_DELETE).astype(np.uint8)
+        aux = rng.integers(0, 1 << 30, n).astype(np.uint64)
+        assert mp.update(ops, keys, aux) == 0
+        assert md.update(ops, keys, aux) == 0
+        assert md.check() == 0
+        d = md.dump()
+        ek, ev = mp.export()
+        assert np.array_equal(d["keys"], ek) and np.array_equal(d["vals"], ev)
+        if split:
+            assert md.stats()["max_chain"] <= split
+        if merge:
+            pos = 0
+            for c in d["chain_len"]:
+                sz = d["node_size"][pos:pos + c]
+                assert np.all(sz[:-1] + sz[1:] > NS // 2) if c > 1 else True
+                pos += c
+        if step % 10 == 9:
+            _reads_agree(mp, md, kw, rng)
+
+
+def test_split_moves_no_pair():
+    rng = np.random.default_rng(5)
+    load = np.unique(rng.integers(0, 1 << 20, 2000)).astype(np.uint64)
+    mp, md = oracle.Map(64), oracle.Model(64, 8, 50)
+    mp.bulk_load(load, load)
+    md.bulk_load(load, load)
+    k = np.unique(rng.integers(1000, 60000, 3000)).astype(np.uint64)   # a hot range: long chains
+    mp.update(np.full(k.size, W.OP_INSERT, np.uint8), k, k)
+    md.update(np.full(k.size, W.OP_INSERT, np.uint8), k, k)
+    before = md.dump()
+    long_chains = before["chain_len"][before["chain_len"] > 3]
+    assert long_chains.size > 0
+    added = md.split_chains(3)
+    after = md.dump()
+    assert added == int((long_chains - 1).sum())
+    assert after["mkba"].size == before["mkba"].size + added
+    for f in ("node_size", "node_bound", "keys", "vals"):
+        assert np.array_equal(before[f], after[f])
+    assert md.check() == 0 and md.stats()["max_chain"] <= 3
+    _reads_agree(mp, md, 64, rng)

@@ -31,6 +31,7 @@ __all__ = [
     "key_max", "mix64", "mix32", "uniform01", "universe", "values_for", "zipf",
     "scramble30", "scramble_bits", "universe_at", "log_uniform_sizes", "permutation",
     "config1", "read_scale", "update_heavy", "mixed_stream", "serving_requests",
+    "bijection_below", "xy_rounds",
 ]
 
 
@@ -394,3 +395,65 @@ def serving_requests(seed: int = 5000, kw: int = 64, universe_bits: int = 29, pr
     off[1:] = np.cumsum(sizes)
     return dict(kw=kw, universe_bits=universe_bits, n_preload=1 << preload_bits, arrival_s=arrival,
                 req_off=off, ops=ops, keys=keys, aux=aux, mean_ops=mean_ops)
+
+
+def bijection_below(c: np.ndarray, size: int, seed: int) -> np.ndarray:
+    """A seeded bijection of [0, size) applied to counters c < size: `scramble_bits` over the
+    smallest power of two >= size, re-applied to any image >= size until it falls below size
+    (cycle walking; it terminates because the scramble is a permutation of the power-of-two range)."""
+    c = np.asarray(c, dtype=np.uint64)
+    if size <= 1:
+        return np.zeros(c.shape, dtype=np.uint64)
+    bits = max(int(size - 1).bit_length(), 1)
+    x = scramble_bits(c, bits, seed)
+    out = np.ascontiguousarray(x)
+    bad = np.nonzero(out >= np.uint64(size))[0]
+    while bad.size:
+        out[bad] = scramble_bits(out[bad], bits, seed)
+        bad = bad[out[bad] >= np.uint64(size)]
+    return out
+
+
+def xy_rounds(X: float, Y: float, build: int, inserts: int, rounds: int, seed: int = 6000,
+              kw: int = 64):
+    """Dense-range (X/Y) update workload: a hot interval covering the fraction X of the key range
+    receives the fraction Y of every insert round; the rest of the round is spread uniformly over
+    the remaining key range.  X = Y = 0.9 is the uniform case.
+
+    Keys are distinct by construction: with V = 2^(kw-1) - 1 values v, build keys are 2v and
+    inserted keys 2v + 1 (never KEY_MAX).  Build values v are `bijection_below` of the counters
+    0..build-1 over [0, V).  The hot interval is [h0, h0 + H) in v, H = floor(X V), h0 seeded;
+    hot inserts take counters 0, 1, ... of a bijection of [0, H) shifted by h0, cold inserts counters
+    of a bijection of [0, V - H) with the hot interval skipped.  Each round holds
+    round(Y m) hot and m - round(Y m) cold keys (m = inserts / rounds, the last round takes the
+    remainder), hot ones first: the keys are distinct and every batch is sorted, so their order
+    changes no result.  The delete rounds remove the keys of the insert rounds, round by round
+    (the structure returns to its build keys).
+
+    Returns dict(build_keys, build_vals, insert=[(keys, vals)], delete=[keys], hot=(lo_key, hi_key)).
+    """
+    assert 0.0 < X <= 1.0 and 0.0 <= Y <= 1.0 and kw in (32, 64)
+    dt = _kdt(kw)
+    V = (1 << (kw - 1)) - 1
+    H = max(1, min(V - 1, int(X * V)))
+    h0 = int(_stream_words(seed, 1, 1)[0] % np.uint64(V - H + 1))
+    bk = (bijection_below(np.arange(build, dtype=np.uint64), V, seed ^ 0x11) << np.uint64(1)).astype(dt)
+    per = [inserts // rounds] * rounds
+    per[-1] += inserts - sum(per)
+    n_hot = [int(round(Y * m)) for m in per]
+    assert sum(n_hot) <= H and sum(per) - sum(n_hot) <= V - H, "more keys than the interval holds"
+    ins, dels = [], []
+    ch = cc = 0
+    for r, m in enumerate(per):
+        kh, kc = n_hot[r], m - n_hot[r]
+        vh = bijection_below(np.arange(ch, ch + kh, dtype=np.uint64), H, seed ^ 0x22) + np.uint64(h0)
+        ic = bijection_below(np.arange(cc, cc + kc, dtype=np.uint64), V - H, seed ^ 0x33)
+        vc = np.where(ic < np.uint64(h0), ic, ic + np.uint64(H))
+        ch += kh
+        cc += kc
+        v = np.concatenate([vh, vc])
+        k = ((v << np.uint64(1)) | np.uint64(1)).astype(dt)
+        ins.append((k, values_for(kw, k, salt=r + 1)))
+        dels.append(k.copy())
+    return dict(kw=kw, build_keys=bk, build_vals=values_for(kw, bk), insert=ins, delete=dels,
+                hot=(2 * h0, 2 * (h0 + H)))
