@@ -160,11 +160,14 @@ def measured_peaks():
 
 
 def traffic_record(kernel):
-    """ncu DRAM bytes per item for `kernel`, valid only while its source is unchanged."""
+    """ncu DRAM bytes per item for `kernel`, valid only while the source it was compiled from (the
+    recorded file, or the part of it before the recorded marker) is unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)[kernel]
         src = open(os.path.join(ROOT, "paper_2604_16725_gb300", "csrc", d["source"]), "rb").read()
+        if d.get("until"):                 # the record covers the source up to this marker
+            src = src[:src.index(d["until"].encode())]
         if hashlib.sha256(src).hexdigest() != d["sha256"]:
             return None
         return d
@@ -738,9 +741,11 @@ def bench_xy(args):
     rounds_out = {}
     tot_ops, tot_ms = 0, 0.0
     build = 1 << 24
-    for X in (0.9, 0.5, 0.25, 0.12, 0.03, 0.02):
-        w = W.xy_rounds(X, 0.9, build, 3 * build, 8, seed=6000, kw=64)
-        idx = fx.Index(key_bits=64, node_size=32)
+    variants = (("plain", 0, False), ("elastic", 4, True))
+    for X, (vname, split, merge) in [(X, v) for X in (0.9, 0.5, 0.25, 0.12, 0.03, 0.02) for v in variants]:
+        if vname == "plain":
+            w = W.xy_rounds(X, 0.9, build, 3 * build, 8, seed=6000, kw=64)
+        idx = fx.Index(key_bits=64, node_size=32, split_chains_over=split, merge_underfull=merge)
         idx.bulk_load(td(w["build_keys"]), td(w["build_vals"]), stream=st)
         present = [w["build_keys"]]
         ins_ms, q_ms, del_ms, chains = [], [], [], []
@@ -759,15 +764,19 @@ def bench_xy(args):
             del_ms.append(timed(lambda: idx.delete(kd, stream=st)))
         n_ins = sum(k.size for k, _ in w["insert"])
         n_del = sum(k.size for k in w["delete"])
-        tot_ops += n_ins + n_del
-        tot_ms += sum(ins_ms) + sum(del_ms)
-        rounds_out["X%dY90" % round(100 * X)] = {
+        if vname == "plain":
+            tot_ops += n_ins + n_del
+            tot_ms += sum(ins_ms) + sum(del_ms)
+        s_end = idx.stats(stream=st)
+        name = "X%dY90%s" % (round(100 * X), "" if vname == "plain" else "_split4_merge")
+        rounds_out[name] = {
             "insert_mops_per_round": [round(k.size / (t * 1e-3) / 1e6, 1) for (k, _), t in zip(w["insert"], ins_ms)],
             "lookup_2e25_ms_per_round": [round(t, 3) for t in q_ms],
             "delete_mops_per_round": [round(k.size / (t * 1e-3) / 1e6, 1) for k, t in zip(w["delete"], del_ms)],
             "max_chain_per_round": chains,
-            "insert_mops": n_ins / (sum(ins_ms) * 1e-3) / 1e6, "delete_mops": n_del / (sum(del_ms) * 1e-3) / 1e6}
-        log("X=%g: %s" % (X, rounds_out["X%dY90" % round(100 * X)]))
+            "insert_mops": n_ins / (sum(ins_ms) * 1e-3) / 1e6, "delete_mops": n_del / (sum(del_ms) * 1e-3) / 1e6,
+            "buckets_end": s_end["buckets"], "nodes_end": s_end["nodes_used"]}
+        log("%s: %s" % (name, rounds_out[name]))
         idx.close()
         torch.cuda.empty_cache()
 
@@ -809,7 +818,9 @@ def bench_xy(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "dense-range updates: uint64, node size 32, build 2^24 uniform, 8 insert rounds "
                                    "of 3*2^21 keys with 90% in a hot interval of X of the key range, 8 delete "
-                                   "rounds of the same keys; value = all insert and delete ops / their time"},
+                                   "rounds of the same keys; value = all insert and delete ops / their time "
+                                   "(default structure; the _split4_merge rounds split chains past 4 nodes and "
+                                   "merge underfull neighbours after every batch)"},
             "rounds": rounds_out, "restructure_accounting": table}
     print(json.dumps(line))
     return 0

@@ -76,7 +76,14 @@ typedef struct {
                                  into its place in a second key/value node array, kept for later
                                  restructures (doubles the pool's key and value memory, halves
                                  the restructure's traffic); zero: gather to scratch, then cut */
-    uint32_t reserved[5];
+    uint32_t split_chains_over; /* nonzero T: after every synchronous update batch, each bucket the
+                                 batch touched whose chain is longer than T nodes is split into
+                                 one bucket per node (flix_split_chains; asynchronous batches never
+                                 change the bucket count).  0 (default): off */
+    uint32_t merge_underfull; /* nonzero: after every update batch (synchronous or not), each bucket
+                                 the batch touched merges underfull neighbours (flix_merge_underfull).
+                                 0 (default): off */
+    uint32_t reserved[3];
 } flix_config;
 
 /* Batch-sort variants (same stable order, different speed): one-sweep passes with decoupled
@@ -142,6 +149,23 @@ int flix_lookup_noalloc(flix_t h, const void* d_keys, uint64_t n, void* d_vals_o
  * (KEY_MAX, VAL_NONE) when none exists.  Asynchronous. */
 int flix_successor(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, void* d_vals_out,
                    void* stream);
+
+/* Elastic bucket split (Sec. 3.4 names splitting buckets with long chains of nodes, which narrows
+ * the key range each bucket covers).  Every bucket whose chain holds more than max_chain nodes
+ * (max_chain >= 1) becomes one bucket per node, in chain order; each new bucket's maxBucket is its
+ * node's maxKey, and the chain's last node keeps the old maxBucket.  No pair moves and no node is
+ * allocated: only the MKBA and the bucket heads change (written to a second pair of bucket arrays,
+ * allocated at the first split and sized like the pool, then swapped in).  *h_added (may be NULL)
+ * receives the number of buckets added.  Synchronises.  FLIX_EINVAL if max_chain is 0. */
+int flix_split_chains(flix_t h, uint32_t max_chain, uint64_t* h_added, void* stream);
+
+/* Underfull-neighbour merge (Sec. 5.4.1 names merging underfull nodes during deletion as a possible
+ * addition; Sec. 6.6 merges them into half-full nodes by restructuring).  In every bucket, walk the
+ * chain: while the current node and the next hold at most NS/2 pairs together, the next node's
+ * pairs are appended to the current node, which takes over its maxKey and node-link, and the next
+ * node goes on the free list; otherwise the walk moves on.  *h_freed (may be NULL) receives the
+ * number of nodes freed.  Synchronises. */
+int flix_merge_underfull(flix_t h, uint64_t* h_freed, void* stream);
 
 /* Predecessor queries (largest stored key <= key; the paper names predecessor in Sec. 2.1 without
  * defining it, and this is the mirror of Sec. 6.5's successor): d_keys_out[i], d_vals_out[i], or

@@ -137,5 +137,15 @@ class BatchedRunner:
             return True
         return False
 
+    def split_chains(self, max_chain: int) -> int:
+        """Elastic split of every chain longer than max_chain between graph replays (the captured
+        graphs hold the bucket count and arrays, so they are re-captured when buckets were added)."""
+        self.check()
+        added = self.idx.split_chains(max_chain, stream=self.stream)
+        if added:
+            self.idx.reserve(self.sizes[-1], 0, stream=self.stream)
+            self.invalidate()
+        return added
+
     def synchronize(self):
         self.check()

@@ -327,6 +327,87 @@ __global__ void k_stats(DevIdx<K> ix, unsigned long long* __restrict__ out)
     atomicAdd(&out[2], c);
 }
 
+// Elastic split, pass 1: per bucket, how many buckets it becomes.
+template <class K>
+__global__ void k_split_count(DevIdx<K> ix, uint32_t max_chain, const uint32_t* __restrict__ uoff,
+                              uint64_t* __restrict__ cnt)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ix.nb) return;
+    if (uoff && uoff[b] == uoff[b + 1]) { cnt[b] = 1; return; }
+    uint64_t L = 0;
+    for (uint32_t x = ix.head[b]; x != NIL; x = ix.next[x]) {
+        if (++L > ix.cap) { atomicOr(ix.err, ERR_CHAIN); break; }
+    }
+    cnt[b] = L > max_chain ? L : 1;
+}
+
+// Elastic split, pass 2: the new MKBA and heads.  A split chain's nodes are unlinked and each
+// becomes a bucket whose maxBucket is the node's maxKey (the last node's maxKey is the old
+// maxBucket); other buckets are copied.
+template <class K>
+__global__ void k_split_write(DevIdx<K> ix, const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ boff,
+                              K* __restrict__ mkba2, uint32_t* __restrict__ head2)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ix.nb) return;
+    const uint64_t o = boff[b], L = cnt[b];
+    if (L == 1) {
+        mkba2[o] = ix.mkba[b];
+        head2[o] = ix.head[b];
+        return;
+    }
+    uint32_t x = ix.head[b];
+    for (uint64_t i = 0; i < L && x != NIL; i++) {
+        const uint32_t nx = ix.next[x];
+        head2[o + i] = x;
+        mkba2[o + i] = ix.bound[x];
+        ix.next[x] = NIL;
+        x = nx;
+    }
+}
+
+// Underfull-neighbour merge: walk the chain; while the current node and the next hold at most NS/2
+// pairs together, the next node's pairs are appended to the current one (they are all larger),
+// the current node takes its maxKey and node-link, and the next node goes on the free stack.
+template <class K>
+__global__ void k_merge_underfull(DevIdx<K> ix, const uint32_t* __restrict__ uoff, int gated, DevState* __restrict__ ds,
+                                  uint32_t* __restrict__ free_ids, unsigned long long* __restrict__ freed)
+{
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ix.nb) return;
+    if (gated && !ds->applied) return;   // after a batch: only if the batch was applied
+    if (uoff && uoff[b] == uoff[b + 1]) return;
+    uint32_t a = ix.head[b];
+    if (ix.next[a] == NIL) return;
+    const uint32_t half = ix.NS / 2;
+    uint32_t sa = ix.size[a];
+    uint64_t steps = 0;
+    for (uint32_t x = ix.next[a]; x != NIL; x = ix.next[a]) {
+        if (++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return; }
+        const uint32_t sx = ix.size[x];
+        if (sa + sx <= half) {
+            K* ak = ix.keys + (uint64_t)a * ix.NS + sa;
+            K* av = ix.vals + (uint64_t)a * ix.NS + sa;
+            const K* xk = ix.keys + (uint64_t)x * ix.NS;
+            const K* xv = ix.vals + (uint64_t)x * ix.NS;
+            for (uint32_t i = 0; i < sx; i++) {
+                ak[i] = xk[i];
+                av[i] = xv[i];
+            }
+            sa += sx;
+            ix.size[a] = sa;
+            ix.bound[a] = ix.bound[x];
+            ix.next[a] = ix.next[x];
+            free_ids[atomicAdd(&ds->free_top, 1ull)] = x;
+            if (freed) atomicAdd(freed, 1ull);
+        } else {
+            a = x;
+            sa = sx;
+        }
+    }
+}
+
 }  // namespace
 
 // Forces the module loader to load every kernel of this file now (see preload_kernels).
@@ -349,7 +430,10 @@ void preload_build_kernels()
     FLIX_TOUCH(k_cut_meta<K>);               \
     FLIX_TOUCH(k_dedupe_flags<K>);           \
     FLIX_TOUCH(k_dedupe_write<K>);           \
-    FLIX_TOUCH(k_stats<K>)
+    FLIX_TOUCH(k_stats<K>);                  \
+    FLIX_TOUCH(k_split_count<K>);            \
+    FLIX_TOUCH(k_split_write<K>);            \
+    FLIX_TOUCH(k_merge_underfull<K>)
     FLIX_TOUCH_K(uint32_t);
     FLIX_TOUCH_K(uint64_t);
 #undef FLIX_TOUCH_K
@@ -496,6 +580,27 @@ cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K*
 }
 
 template <class K>
+cudaError_t split_count(Ctx& c, uint32_t max_chain, const uint32_t* uoff, uint64_t* cnt)
+{
+    return launch(c, K_SPLIT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_split_count<K>, dev_view<K>(c.h), max_chain,
+                  uoff, cnt);
+}
+
+template <class K>
+cudaError_t split_write(Ctx& c, const uint64_t* cnt, const uint64_t* boff, K* mkba2, uint32_t* head2)
+{
+    return launch(c, K_SPLIT, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_split_write<K>, dev_view<K>(c.h), cnt, boff,
+                  mkba2, head2);
+}
+
+template <class K>
+cudaError_t merge_underfull(Ctx& c, const uint32_t* uoff, int gated, unsigned long long* freed)
+{
+    return launch(c, K_MERGE, dim3(div_up(c.h->nb, BT)), dim3(BT), 0, k_merge_underfull<K>, dev_view<K>(c.h), uoff,
+                  gated, c.h->dstate, c.h->free_ids, freed);
+}
+
+template <class K>
 cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
 {
     cudaError_t e = fill_bytes(c, out3, 0, 4 * sizeof(uint64_t));
@@ -516,7 +621,10 @@ cudaError_t stats_kernel(Ctx& c, uint64_t* out3)
     template cudaError_t cut_buckets<K>(Ctx&, const K*, const K*, uint64_t, uint64_t);                     \
     template cudaError_t dedupe_sorted<K>(Ctx&, const K*, const uint32_t*, const K*, uint64_t, K*, K*,     \
                                           uint32_t*);                                                      \
-    template cudaError_t stats_kernel<K>(Ctx&, uint64_t*);
+    template cudaError_t stats_kernel<K>(Ctx&, uint64_t*);                                                 \
+    template cudaError_t split_count<K>(Ctx&, uint32_t, const uint32_t*, uint64_t*);                       \
+    template cudaError_t split_write<K>(Ctx&, const uint64_t*, const uint64_t*, K*, uint32_t*);            \
+    template cudaError_t merge_underfull<K>(Ctx&, const uint32_t*, int, unsigned long long*);
 
 FLIX_BUILD_INST(uint32_t)
 FLIX_BUILD_INST(uint64_t)

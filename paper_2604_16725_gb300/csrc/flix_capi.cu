@@ -18,7 +18,7 @@ const char* kKernelNames[K_NUM] = {
     "partition", "read_point", "read_unsort", "range_count", "range_fill",
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
     "update_count", "alloc_copy", "update_apply", "admit",
-    "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill",
+    "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill", "split_chains", "merge_underfull",
 };
 
 cudaError_t Arena::ensure(size_t bytes)
@@ -150,6 +150,11 @@ void pool_free_second(flix_index* h)
     if (h->vals2) cudaFree(h->vals2);
     h->keys2 = h->vals2 = nullptr;
     h->cap2 = 0;
+    if (h->mkba2) cudaFree(h->mkba2);
+    if (h->head2) cudaFree(h->head2);
+    h->mkba2 = nullptr;
+    h->head2 = nullptr;
+    h->capb2 = 0;
 }
 
 void pool_free(flix_index* h)
@@ -348,6 +353,10 @@ size_t batch_scratch_bytes(uint64_t n, uint64_t nb)
            heavy_scratch_bytes(n) + (1 << 16);
 }
 
+size_t split_scratch_bytes(uint64_t nb);
+template <class K>
+int split_chains_impl(flix_index* h, uint32_t max_chain, const uint32_t* uoff, uint64_t* added, cudaStream_t st);
+
 // Reads of a mixed batch (snapshot), then its updates.  hom_op != 0: homogeneous insert/delete.
 // sync: read back the node demand and range total, decide admission (and pool growth) on the host
 // and report errors as return codes.  !sync: no host round trip; the admit kernel decides on the
@@ -367,7 +376,8 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     Ctx c{h, st};
     const uint64_t nb = h->nb;
     const bool mixed = hom_op == 0;
-    const size_t need_bytes = batch_scratch_bytes<K>(n, nb);
+    const bool split_after = sync && h->cfg.split_chains_over;
+    const size_t need_bytes = batch_scratch_bytes<K>(n, nb) + (split_after ? split_scratch_bytes(nb) : 0);
     if (sync) {
         CK(h->arena.ensure(need_bytes));
     } else if (h->arena.cap < need_bytes) {
@@ -445,6 +455,18 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     if (heavy_nodes) CK(update_heavy<K>(c, ukey, uop, uval, nf_off, alloc_ids, hl));
     CK(commit(c));
     if (sync) h->free_top = h->free_top - need + freed;
+    // chain maintenance in the buckets the batch touched: merge underfull neighbours (only if the
+    // batch was admitted), then split chains that grew too long (synchronous batches only)
+    if (h->cfg.merge_underfull) CK(merge_underfull<K>(c, uoff, 1, nullptr));
+    if (split_after) {
+        int r = split_chains_impl<K>(h, h->cfg.split_chains_over, uoff, nullptr, st);
+        if (r) return r;
+    }
+    if (sync && h->cfg.merge_underfull) {
+        int r = readback(h, st, {{&h->dstate->free_top, 8}});
+        if (r) return r;
+        h->free_top = h->hpin[0];
+    }
     return FLIX_OK;
 }
 
@@ -475,6 +497,75 @@ int ensure_second(flix_index* h)
     CK(cudaMalloc(&h->vals2, h->cap * h->NS * h->ks));
     h->cap2 = h->cap;
     return FLIX_OK;
+}
+
+// Makes the second MKBA and bucket-head arrays of the elastic split as large as the pool (a split
+// never makes more buckets than there are nodes in chains).
+int ensure_second_buckets(flix_index* h)
+{
+    if (h->capb2 == h->cap) return FLIX_OK;
+    if (h->mkba2) cudaFree(h->mkba2);
+    if (h->head2) cudaFree(h->head2);
+    h->mkba2 = nullptr;
+    h->head2 = nullptr;
+    h->capb2 = 0;
+    CK(cudaMalloc(&h->mkba2, h->cap * h->ks));
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->head2), h->cap * 4));
+    h->capb2 = h->cap;
+    return FLIX_OK;
+}
+
+size_t split_scratch_bytes(uint64_t nb) { return al((nb + 1) * 8) * 2 + scan_scratch_bytes<uint64_t>(nb + 1); }
+
+// Elastic split of the buckets selected by uoff (all when null) whose chains exceed max_chain.  Takes
+// its scratch from the arena as it stands (a batch calls it with its own scratch still in use).
+template <class K>
+int split_chains_impl(flix_index* h, uint32_t max_chain, const uint32_t* uoff, uint64_t* added, cudaStream_t st)
+{
+    Ctx c{h, st};
+    const uint64_t nb = h->nb;
+    uint64_t* cnt = h->arena.take<uint64_t>(nb + 1);
+    uint64_t* boff = h->arena.take<uint64_t>(nb + 1);
+    if (!cnt || !boff) return FLIX_ENOMEM;
+    CK(split_count<K>(c, max_chain, uoff, cnt));
+    CK(scan_exclusive<uint64_t, uint64_t>(c, cnt, boff, nb));
+    int r = readback(h, st, {{boff + nb, 8}});
+    if (r) return r;
+    const uint64_t nb_new = h->hpin[0];
+    if (added) *added = nb_new - nb;
+    if (nb_new == nb) return check_err(h, st);
+    if (nb_new > h->cap) return FLIX_EINTERNAL;
+    r = ensure_second_buckets(h);
+    if (r) return r;
+    CK(split_write<K>(c, cnt, boff, static_cast<K*>(h->mkba2), h->head2));
+    std::swap(h->mkba, h->mkba2);
+    std::swap(h->head, h->head2);
+    h->nb = nb_new;
+    return check_err(h, st);
+}
+
+template <class K>
+int do_split_chains(flix_index* h, uint32_t max_chain, uint64_t* added, cudaStream_t st)
+{
+    CK(h->arena.ensure(split_scratch_bytes(h->nb) + (1 << 16)));
+    h->arena.reset();
+    return split_chains_impl<K>(h, max_chain, nullptr, added, st);
+}
+
+template <class K>
+int do_merge_underfull(flix_index* h, uint64_t* freed, cudaStream_t st)
+{
+    Ctx c{h, st};
+    CK(h->arena.ensure(1 << 16));
+    h->arena.reset();
+    unsigned long long* cnt = h->arena.take<unsigned long long>(1);
+    CK(fill_bytes(c, cnt, 0, 8));
+    CK(merge_underfull<K>(c, nullptr, 0, cnt));
+    int r = readback(h, st, {{cnt, 8}, {&h->dstate->free_top, 8}});
+    if (r) return r;
+    if (freed) *freed = h->hpin[0];
+    h->free_top = h->hpin[1];
+    return check_err(h, st);
 }
 
 // Restructure with the nodes put in chain order by their maxKeys (some chain is long).
@@ -930,6 +1021,20 @@ int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* st
     if (!h || too_big(batch_max)) return FLIX_EINVAL;
     return DISPATCH(do_reserve<uint32_t>(h, batch_max, free_nodes_min, S(stream)),
                     do_reserve<uint64_t>(h, batch_max, free_nodes_min, S(stream)));
+}
+
+int flix_split_chains(flix_t h, uint32_t max_chain, uint64_t* h_added, void* stream)
+{
+    if (!h || max_chain == 0) return FLIX_EINVAL;
+    return DISPATCH(do_split_chains<uint32_t>(h, max_chain, h_added, S(stream)),
+                    do_split_chains<uint64_t>(h, max_chain, h_added, S(stream)));
+}
+
+int flix_merge_underfull(flix_t h, uint64_t* h_freed, void* stream)
+{
+    if (!h) return FLIX_EINVAL;
+    return DISPATCH(do_merge_underfull<uint32_t>(h, h_freed, S(stream)),
+                    do_merge_underfull<uint64_t>(h, h_freed, S(stream)));
 }
 
 int flix_restructure(flix_t h, void* stream)

@@ -51,7 +51,7 @@ enum KernelId {
     K_PARTITION, K_READ_POINT, K_UNSORT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
     K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY, K_ADMIT,
-    K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL,
+    K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL, K_SPLIT, K_MERGE,
     K_NUM
 };
 
@@ -103,6 +103,7 @@ struct DevState {
     unsigned long long next_top;   // free_top after the batch (from + freed)
     unsigned long long need;       // nodes the batch allocates
     unsigned long long freed;      // nodes the batch frees
+    unsigned long long applied;    // 1 if the last committed batch was admitted
 };
 
 // Status bits an asynchronous batch reports (flix_apply_async).
@@ -134,6 +135,9 @@ struct flix_index {
     void* keys2 = nullptr;         // second key/value node arrays of the one-pass restructure
     void* vals2 = nullptr;
     uint64_t cap2 = 0;             // their capacity in nodes (0: not allocated)
+    void* mkba2 = nullptr;         // second MKBA and bucket heads of the elastic split
+    uint32_t* head2 = nullptr;
+    uint64_t capb2 = 0;            // their capacity in buckets (0: not allocated)
     uint32_t* err = nullptr;       // device error word
     flix::DevState* dstate = nullptr;
 
@@ -376,5 +380,19 @@ cudaError_t dedupe_sorted(Ctx& c, const K* skeys, const uint32_t* sidx, const K*
 
 template <class K>
 cudaError_t stats_kernel(Ctx& c, uint64_t* out3);
+
+// Elastic bucket split (Sec. 3.4).  split_count: cnt[b] = the new buckets bucket b becomes (its
+// chain length when that exceeds max_chain and the bucket is selected, else 1); buckets are
+// selected by a non-empty update range uoff[b] < uoff[b+1], or all when uoff is null.
+// split_write: with boff the exclusive scan of cnt, writes the new MKBA and bucket heads (a split
+// chain's nodes become single-node buckets with their maxKey as maxBucket).
+template <class K>
+cudaError_t split_count(Ctx& c, uint32_t max_chain, const uint32_t* uoff, uint64_t* cnt);
+template <class K>
+cudaError_t split_write(Ctx& c, const uint64_t* cnt, const uint64_t* boff, K* mkba2, uint32_t* head2);
+// Underfull-neighbour merge in the selected buckets (uoff as above); freed nodes go on the free
+// stack; *freed (may be null) counts them.  gated: only if the batch just run was admitted.
+template <class K>
+cudaError_t merge_underfull(Ctx& c, const uint32_t* uoff, int gated, unsigned long long* freed);
 
 }  // namespace flix

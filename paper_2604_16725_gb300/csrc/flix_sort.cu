@@ -344,8 +344,10 @@ size_t sweep_smem()
 // nothing.  Of the others, the plan sorts by all of them (LSD order), unless a prefix of the
 // highest h of them already splits the batch into groups of about 4n / 2^(8h) <= 1/4 item on
 // average; then it sorts by that prefix only and leaves the groups of equal prefix to the finish
-// kernels.  A digit whose fullest bin holds more than 4x its uniform share (n/64 + 256 items) hints
-// at heavy keys, whose groups would be long: the plan then sorts by every digit.  In place, hist
+// kernels.  A digit whose fullest bin holds more than 4x its uniform share (n/64 + 256 items) is
+// heavy; when every prefix digit is heavy, groups may be long (heavy keys) and the plan sorts by
+// every digit.  A skew confined to some prefix digits (a dense key range) keeps the prefix plan,
+// because the largest group is bounded by the lightest prefix digit's fullest bin.  In place, hist
 // rows become the digit bases (items with a smaller digit) of every digit position.
 template <class K>
 __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist, uint64_t n, uint32_t h,
@@ -390,8 +392,11 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
     } else {
         int use = m;
         if ((int)h < m) {
-            bool heavy = false;
-            for (int q = 0; q < (int)h; q++) heavy |= (uint64_t)s_max[nc[q]] > n / 64 + 256;
+            // a group of g keys with one prefix puts g keys into one bin of every prefix digit, so
+            // the largest group is at most the smallest largest-bin over the prefix digits: one
+            // prefix digit without a heavy bin bounds every group the finish meets
+            bool heavy = true;
+            for (int q = 0; q < (int)h; q++) heavy &= (uint64_t)s_max[nc[q]] > n / 64 + 256;
             if (!heavy) {
                 use = (int)h;
                 pl.finish = 1;

@@ -859,6 +859,7 @@ __global__ void k_admit(DevState* __restrict__ ds, const uint64_t* __restrict__ 
 __global__ void k_commit(DevState* __restrict__ ds)
 {
     if (ds->admitted) ds->free_top = ds->next_top;
+    ds->applied = ds->admitted;
     ds->admitted = 0;
 }
 

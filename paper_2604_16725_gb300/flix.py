@@ -32,7 +32,8 @@ class Config(ctypes.Structure):
     _fields_ = [("key_type", ctypes.c_int), ("node_size", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32),
                 ("grow", ctypes.c_uint32), ("pool_nodes", ctypes.c_uint64), ("sort_digit_bits", ctypes.c_uint32),
                 ("sort_variant", ctypes.c_uint32), ("restructure_in_one_pass", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("split_chains_over", ctypes.c_uint32), ("merge_underfull", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -60,6 +61,8 @@ SIGNATURES = {
     "flix_apply_async": (_INT, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_reserve": (_INT, [_VP, _U64, _U64, _VP]),
     "flix_restructure": (_INT, [_VP, _VP]),
+    "flix_split_chains": (_INT, [_VP, ctypes.c_uint32, _VP, _VP]),
+    "flix_merge_underfull": (_INT, [_VP, _VP, _VP]),
     "flix_stats": (_INT, [_VP, _VP, _VP]),
     "flix_export": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_dump_layout": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -116,7 +119,8 @@ class Index:
 
     def __init__(self, key_bits: int = 64, node_size: int | None = None, fill_pct: int = 50,
                  pool_nodes: int = 0, grow: bool = True, device=None, sort_variant: int = 0,
-                 restructure_in_one_pass: bool = True):
+                 restructure_in_one_pass: bool = True, split_chains_over: int = 0,
+                 merge_underfull: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("FliX needs a CUDA device; none is available")
         L = load()
@@ -133,6 +137,8 @@ class Index:
         cfg.grow = 1 if grow else 0
         cfg.sort_variant = sort_variant
         cfg.restructure_in_one_pass = 1 if restructure_in_one_pass else 0
+        cfg.split_chains_over = split_chains_over
+        cfg.merge_underfull = 1 if merge_underfull else 0
         self.node_size = cfg.node_size
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -273,6 +279,20 @@ class Index:
 
     def reserve(self, batch_max: int, free_nodes_min: int = 0, stream=None):
         _check(load().flix_reserve(self._h, batch_max, free_nodes_min, _stream(stream)), "flix_reserve", self._h)
+
+    def split_chains(self, max_chain: int, stream=None) -> int:
+        """Elastic split of every bucket whose chain is longer than max_chain; returns buckets added."""
+        added = ctypes.c_uint64(0)
+        _check(load().flix_split_chains(self._h, max_chain, ctypes.byref(added), _stream(stream)),
+               "flix_split_chains", self._h)
+        return int(added.value)
+
+    def merge_underfull(self, stream=None) -> int:
+        """Underfull-neighbour merge in every bucket; returns nodes freed."""
+        freed = ctypes.c_uint64(0)
+        _check(load().flix_merge_underfull(self._h, ctypes.byref(freed), _stream(stream)),
+               "flix_merge_underfull", self._h)
+        return int(freed.value)
 
     def restructure(self, stream=None):
         _check(load().flix_restructure(self._h, _stream(stream)), "flix_restructure", self._h)

@@ -47,6 +47,46 @@ def test_batched_stream_matches_oracle(kw, NS):
     same(np_of(v, kw), ev, "final vals")
 
 
+def test_batched_stream_with_merge_and_split():
+    """The merge runs inside the captured graphs after every admitted batch; the elastic split runs
+    between replays (graphs re-captured).  Results and layout against the map and the model."""
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.batched import BatchedRunner
+    from tests.gpu_util import compare_layout
+    kw, NS = 64, 8
+    s = W.mixed_stream(seed=4300, kw=kw, n_preload=1 << 13, n_batches=40, lo_exp=4, hi_exp=12, max_len=50,
+                       mix=(0.3, 0.1, 0.05, 0.3, 0.25))
+    idx = fx.Index(key_bits=kw, node_size=NS, merge_underfull=True)
+    idx.bulk_load(s["preload_keys"], s["preload_vals"])
+    mp = oracle.Map(kw)
+    mp.bulk_load(s["preload_keys"], s["preload_vals"])
+    md = oracle.Model(kw, NS, 50)
+    md.bulk_load(s["preload_keys"], s["preload_vals"])
+    md.set_policy(0, True)
+    run = BatchedRunner(idx, max_batch=1 << 12, min_log=4, range_per_op=64, free_nodes_min=1 << 14)
+    added = 0
+    for b, (ops, keys, aux) in enumerate(s["batches"]()):
+        r = run.run(idx._dev(ops, torch.uint8), idx._dev(keys), idx._dev(aux))
+        with torch.cuda.stream(run.stream):
+            got = {k: v.clone() for k, v in r.items()}
+        run.check()
+        e, st = mp.apply(ops, keys, aux)
+        assert st == 0 and md.update(ops, keys, aux) == 0
+        same(np_of(got["keys"], kw), e["keys"], "batch %d keys" % b)
+        same(np_of(got["vals"], kw), e["vals"], "batch %d vals" % b)
+        if b % 8 == 7:
+            a = run.split_chains(2)
+            assert a == md.split_chains(2)
+            added += a
+            compare_layout(idx, md)
+    assert added > 0
+    compare_layout(idx, md)
+    k, v = idx.export()
+    ek, ev = mp.export()
+    same(np_of(k, kw), ek, "final keys")
+    same(np_of(v, kw), ev, "final vals")
+
+
 def test_async_admission_rejects_without_changes():
     """A batch the node pool cannot hold is rejected on the device and leaves the index unchanged."""
     import paper_2604_16725_gb300 as fx

@@ -87,7 +87,7 @@ def test_prefix_groups_of_every_length(fx, sort_variant):
 
 
 def test_heavy_key_sorts_every_digit(fx):
-    """A tenth of the batch is one key: the top digit has a heavy bin and the plan sorts every digit."""
+    """A tenth of the batch is one key: every digit has a heavy bin and the plan sorts every digit."""
     rng = np.random.default_rng(2)
     kw, n = 64, 1 << 20
     load = np.unique(_uniform(rng, kw, 1 << 15))
@@ -126,5 +126,21 @@ def test_prefix_groups_32bit_keys(fx):
     kw, n = 32, 1 << 16
     load = np.unique(_uniform(rng, kw, 1 << 14))
     groups = [_group(rng, kw, 24, 600, 150)] + [_group(rng, kw, 24, int(rng.integers(2, 9)), 3) for _ in range(100)]
+    base = _uniform(rng, kw, n - sum(g.size for g in groups))
+    _run(fx, kw, 32, load, [_batch(rng, kw, base, groups, load) for _ in range(2)])
+
+
+def test_dense_range_keeps_prefix_plan(fx):
+    """A quarter of 2^21 ops in 2% of the key range (the top digit alone is heavy: the plan keeps
+    the prefix passes and the finish), with repeated keys and groups of equal prefix inside it."""
+    rng = np.random.default_rng(6)
+    kw, n = 64, 1 << 21
+    lo = int(0.4 * 2 ** 64)
+    width = int(0.02 * 2 ** 64)
+    load = np.unique(np.concatenate([_uniform(rng, kw, 1 << 15),
+                                     rng.integers(lo, lo + width, 1 << 14, dtype=np.uint64)]))
+    hot = rng.integers(lo, lo + width, n // 4, dtype=np.uint64)
+    hot[: 3000] = hot[3000:6000] & ~np.uint64((1 << 24) - 1)        # groups sharing a 40-bit prefix
+    groups = [hot, np.full(500, hot[10], dtype=np.uint64)]
     base = _uniform(rng, kw, n - sum(g.size for g in groups))
     _run(fx, kw, 32, load, [_batch(rng, kw, base, groups, load) for _ in range(2)])
