@@ -161,13 +161,13 @@ def measured_peaks():
 
 def traffic_record(kernel):
     """ncu DRAM bytes per item for `kernel`, valid only while the source it was compiled from (the
-    recorded file, or the part of it before the recorded marker) is unchanged."""
+    recorded file, or the part of it between the recorded markers) is unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)[kernel]
         src = open(os.path.join(ROOT, "paper_2604_16725_gb300", "csrc", d["source"]), "rb").read()
-        if d.get("until"):                 # the record covers the source up to this marker
-            src = src[:src.index(d["until"].encode())]
+        if d.get("until"):                 # the record covers the source between two markers
+            src = src[src.index(d["from"].encode()) if d.get("from") else 0:src.index(d["until"].encode())]
         if hashlib.sha256(src).hexdigest() != d["sha256"]:
             return None
         return d

@@ -4,9 +4,9 @@
 // The sort is a stable least-significant-digit radix sort of (key, position) pairs with 8-bit
 // digits.  One read of the keys builds the digit histograms of every digit position, and a plan
 // kernel picks the passes from them on the device: digits that are the same in every key are
-// skipped, and when the highest few varying digits already split the batch into groups of about a
-// quarter item, only those are sorted and a finish kernel sorts each group of equal prefix in
-// place (for 2^24 uniform 64-bit keys: 4 passes instead of 8).  Each pass is one scatter kernel
+// skipped, and when the highest few varying digits already split the batch into groups of at most
+// one item on average, only those are sorted and a finish kernel sorts each group of equal prefix
+// in place (for 2^24 uniform 64-bit keys: 3 passes instead of 8).  Each pass is one scatter kernel
 // over 4096-item tiles (512 threads x 8 items, two blocks per SM): a tile ranks its items in
 // shared memory (peers of a digit from 8 warp ballots, one per digit bit; stable: warp-striped
 // items ranked in warp, item, lane order), learns where each digit's run of this tile starts in
@@ -342,9 +342,11 @@ size_t sweep_smem()
 //
 // A digit whose histogram has one bin holding every item is the same in every key and orders
 // nothing.  Of the others, the plan sorts by all of them (LSD order), unless a prefix of the
-// highest h of them already splits the batch into groups of about 4n / 2^(8h) <= 1/4 item on
-// average; then it sorts by that prefix only and leaves the groups of equal prefix to the finish
-// kernels.  A digit whose fullest bin holds more than 4x its uniform share (n/64 + 256 items) is
+// highest h of them already splits the batch into groups of n / 2^(8h) <= 1 item on average;
+// then it sorts by that prefix only and leaves the groups of equal prefix to the finish kernels
+// (one pass costs more than finishing the groups a digit fewer leaves: at 2^24 uniform keys, 3
+// passes and a finish that moves the 63% of items sharing their prefix beat 4 passes and a finish
+// that moves 0.4%).  A digit whose fullest bin holds more than 4x its uniform share (n/64 + 256 items) is
 // heavy; when every prefix digit is heavy, groups may be long (heavy keys) and the plan sorts by
 // every digit.  A skew confined to some prefix digits (a dense key range) keeps the prefix plan,
 // because the largest group is bounded by the lightest prefix digit's fullest bin.  In place, hist
@@ -414,8 +416,8 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
 // After the prefix passes the batch is ordered by prefix, and inside a group of equal prefix by
 // position (the passes are stable).  The payload is the item's position in the input, so the
 // order the sort must produce is (key, payload) ascending, a strict total order; each group is
-// sorted by it in place.  Groups of up to SMALL_SEG items are sorted by the thread at their head;
-// longer ones are listed and sorted by a block each (bitonic in shared memory up to OS_TILE items,
+// sorted by it in place.  Groups of up to SMALL_SEG items are sorted in shared memory, each item
+// moving to its rank in its group; longer ones are listed and sorted by a block each (bitonic in shared memory up to OS_TILE items,
 // beyond that a chunked stable radix sort of the digits under the prefix, through the scratch pair).
 
 constexpr int SMALL_SEG = 8;
@@ -426,96 +428,136 @@ __device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
     return ka < kb || (ka == kb && va < vb);
 }
 
-// Sorts one group of 2..SMALL_SEG items by (key, payload), in place: insertion sort in registers
-// (every index is a constant after unrolling).  Kept out of line so that the rare call does not
-// raise the register count of the scan around it.
-template <class K>
-__device__ __noinline__ void sort_small_group(K* keys, uint32_t* vals, const K* staged, uint32_t L)
-{
-    K sk[SMALL_SEG];
-    uint32_t sv[SMALL_SEG];
-#pragma unroll
-    for (int a = 0; a < SMALL_SEG; a++) {
-        if (a < (int)L) {
-            sk[a] = staged[a];
-            sv[a] = vals[a];
-        }
-    }
-#pragma unroll
-    for (int a = 1; a < SMALL_SEG; a++) {
-        if (a < (int)L) {
-#pragma unroll
-            for (int b = a; b > 0; b--) {
-                if (kv_less(sk[b], sv[b], sk[b - 1], sv[b - 1])) {
-                    const K tk = sk[b]; sk[b] = sk[b - 1]; sk[b - 1] = tk;
-                    const uint32_t tv = sv[b]; sv[b] = sv[b - 1]; sv[b - 1] = tv;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < SMALL_SEG; a++) {
-        if (a < (int)L) {
-            keys[a] = sk[a];
-            vals[a] = sv[a];
-        }
-    }
-}
-
 constexpr int FIN_THREADS = 256;
-constexpr int FIN_ITEMS = 8;
+constexpr int FIN_ITEMS = 7;
 constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 
-// One tile of FIN_TILE positions per block: the tile's keys, the key before it and SMALL_SEG + 1
-// keys after it are staged in shared memory (independent coalesced loads), then each thread looks
-// at FIN_ITEMS positions (FIN_THREADS apart) for group heads; a head's group is sorted by that
-// thread or, if longer than SMALL_SEG, listed.
+// One tile of FIN_TILE positions per block.  The tile's keys and payloads, the key before it and
+// HALO positions after it are staged in shared memory (coalesced loads, all issued before the first
+// store).  Every position then finds the bounds of its group of equal prefix (at most SMALL_SEG
+// steps each way) and, in a group of 2..SMALL_SEG items, its rank by (key, payload) among the
+// group's items, and moves to the group's head + rank in a second staging buffer; a group's head
+// lists the group when it is longer than SMALL_SEG.  The work per item follows its group's size
+// (mostly 1 to 3 items), with no thread sorting for a warp.  The moved items go back in coalesced
+// stores when at least an eighth of the tile moved, else one by one.  A group belongs to the tile
+// that holds its head, also where it runs into the next tile (into the halo): a tile never stores
+// the leading positions that continue a group from the tile before.  Sorting permutes a group
+// only, so every position keeps its prefix and the group bounds another block sees stay the same.
 template <class K>
-__global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(FIN_THREADS, 4) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
                                                              uint64_t n, SortPlan* __restrict__ plan,
                                                              uint64_t* __restrict__ list, uint64_t list_cap,
                                                              uint32_t* __restrict__ err)
 {
     if (!plan->finish) return;
     constexpr int HALO = SMALL_SEG + 1;
-    __shared__ K tile[1 + FIN_TILE + HALO];
+    constexpr uint32_t SPAN = FIN_TILE + HALO;
+    __shared__ K tk[1 + SPAN];            // tk[1 + j] = key at base + j; tk[0] = key at base - 1
+    __shared__ uint32_t tv[SPAN];
+    __shared__ K ok[SPAN];
+    __shared__ uint32_t ov[SPAN];
+    __shared__ uint32_t s_moved, s_lead, s_ext;
     const uint64_t pm = plan->pmask;
     const uint64_t base = (uint64_t)blockIdx.x * FIN_TILE;
-    const uint64_t lim = n - base < (uint64_t)(FIN_TILE + HALO) ? n - base : (uint64_t)(FIN_TILE + HALO);
+    const uint32_t lim = n - base < (uint64_t)SPAN ? (uint32_t)(n - base) : SPAN;
+    {
+        K rk[FIN_ITEMS + 1];
+        uint32_t rv[FIN_ITEMS + 1];
 #pragma unroll
-    for (int r = 0; r < FIN_ITEMS; r++) {
-        const uint32_t j = r * FIN_THREADS + threadIdx.x;
-        if (j < lim) tile[1 + j] = keys[base + j];
-    }
-    if (threadIdx.x < HALO && FIN_TILE + threadIdx.x < lim) tile[1 + FIN_TILE + threadIdx.x] = keys[base + FIN_TILE + threadIdx.x];
-    if (threadIdx.x == 0 && base > 0) tile[0] = keys[base - 1];
-    __syncthreads();
-#pragma unroll 1
-    for (int r = 0; r < FIN_ITEMS; r++) {
-        const uint32_t j = r * FIN_THREADS + threadIdx.x;        // tile position
-        if (j >= lim || j >= (uint32_t)FIN_TILE) break;
-        const K k0 = tile[1 + j];
-        if (base + j > 0 && (static_cast<uint64_t>(tile[j] ^ k0) & pm) == 0) continue;   // not a group head
-        uint32_t L = 1;
-        while (L <= SMALL_SEG && j + L < lim && (static_cast<uint64_t>(tile[1 + j + L] ^ k0) & pm) == 0) L++;
-        if (L == 1) continue;
-        const uint64_t i = base + j;
-        if (L <= SMALL_SEG) {
-            // keys already non-decreasing: equal keys are in position order (the passes are
-            // stable), so the group is sorted and stays as it is (repeated keys, mostly)
-            bool sorted = true;
-#pragma unroll
-            for (int a = 1; a < SMALL_SEG; a++)
-                if (a < (int)L) sorted &= !(tile[1 + j + a] < tile[j + a]);
-            if (sorted) continue;
+        for (int r = 0; r <= FIN_ITEMS; r++) {
+            const uint32_t j = r * FIN_THREADS + threadIdx.x;   // r == FIN_ITEMS: the halo
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
+                rk[r] = keys[base + j];
+                rv[r] = vals[base + j];
+            }
         }
-        if (L > SMALL_SEG) {
-            const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
-            if (slot < list_cap) list[slot] = i;
-            else atomicOr(err, ERR_SORT);
+#pragma unroll
+        for (int r = 0; r <= FIN_ITEMS; r++) {
+            const uint32_t j = r * FIN_THREADS + threadIdx.x;
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
+                tk[1 + j] = rk[r];
+                tv[j] = rv[r];
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (base > 0) tk[0] = keys[base - 1];
+        s_moved = 0;
+        s_ext = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // positions that continue a group whose head lies in the tile before
+        uint32_t lead = 0;
+        if (base > 0)
+            while (lead < (uint32_t)HALO && lead < lim && (static_cast<uint64_t>(tk[1 + lead] ^ tk[0]) & pm) == 0)
+                lead++;
+        s_lead = lead;
+    }
+    uint32_t moved = 0;
+    const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
+    // the tile's positions, then (threads 0..HALO-1) the halo positions of a group headed inside
+    for (uint32_t j = threadIdx.x; j < tile_end + HALO; j += FIN_THREADS) {
+        const bool halo = j >= tile_end;
+        if (j >= lim) break;
+        const K kj = tk[1 + j];
+        const uint32_t vj = tv[j];
+        // group start: walk back while the prefix is equal (inside the tile; base - 1 is tk[0])
+        uint32_t h = j, back = 0;
+        bool before = false;      // the group starts in the tile before
+        while (back <= (uint32_t)SMALL_SEG) {
+            if (h == 0) {
+                before = base > 0 && (static_cast<uint64_t>(tk[0] ^ kj) & pm) == 0;
+                break;
+            }
+            if ((static_cast<uint64_t>(tk[h] ^ kj) & pm) != 0) break;   // tk[h] = key at h - 1
+            h--;
+            back++;
+        }
+        if (halo && (back > (uint32_t)SMALL_SEG || h >= tile_end || h + SMALL_SEG <= j)) {
+            ok[j] = kj;   // not part of a group this tile sorts (unused)
+            ov[j] = vj;
             continue;
         }
-        sort_small_group<K>(keys + i, vals + i, tile + 1 + j, L);
+        uint32_t e = j + 1;
+        while (e < lim && e - h <= (uint32_t)SMALL_SEG && (static_cast<uint64_t>(tk[1 + e] ^ kj) & pm) == 0) e++;
+        const uint32_t L = e - h;
+        if (before || back > (uint32_t)SMALL_SEG || L > (uint32_t)SMALL_SEG || L == 1) {
+            if (!halo && !before && h == j && L > (uint32_t)SMALL_SEG) {
+                const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
+                if (slot < list_cap) list[slot] = base + j;
+                else atomicOr(err, ERR_SORT);
+            }
+            ok[j] = kj;   // stays
+            ov[j] = vj;
+            continue;
+        }
+        uint32_t rank = 0;
+        for (uint32_t i = h; i < e; i++) rank += kv_less(tk[1 + i], tv[i], kj, vj);
+        const uint32_t to = h + rank;
+        ok[to] = kj;
+        ov[to] = vj;
+        moved += to != j;
+        if (!halo && e > tile_end && j == h) s_ext = e - tile_end;     // one group at most runs past
+    }
+    if (moved) atomicAdd(&s_moved, moved);
+    __syncthreads();
+    if (s_moved == 0) return;
+    const uint32_t lead = s_lead, end = tile_end + s_ext;
+    if (s_moved * 8 >= (uint32_t)FIN_TILE) {
+        for (uint32_t j = threadIdx.x; j < end; j += FIN_THREADS) {
+            if (j < lead) continue;
+            keys[base + j] = ok[j];
+            vals[base + j] = ov[j];
+        }
+        return;
+    }
+    for (uint32_t j = threadIdx.x; j < end; j += FIN_THREADS) {
+        if (j < lead) continue;
+        if (ok[j] != tk[1 + j] || ov[j] != tv[j]) {
+            keys[base + j] = ok[j];
+            vals[base + j] = ov[j];
+        }
     }
 }
 
@@ -792,12 +834,12 @@ size_t sort_scratch_bytes(uint64_t n)
     return pingpong + al(P * RADIX * 4) + (rts > one ? rts : one) + fin + 1024;
 }
 
-// Prefix digits the plan may stop at: the fewest h with 2^(8h) >= 4n.
+// Prefix digits the plan may stop at: the fewest h with 2^(8h) >= n.
 template <class K>
 static uint32_t prefix_digits(uint64_t n)
 {
     uint32_t h = 1;
-    while (h < sizeof(K) && (8 * h >= 64 || (1ull << (8 * h)) < 4 * n)) h++;
+    while (h < sizeof(K) && (8 * h >= 64 || (1ull << (8 * h)) < n)) h++;
     return h;
 }
 

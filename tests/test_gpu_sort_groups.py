@@ -1,9 +1,9 @@
 """GPU parity of batches built to reach every path of the batch sort.
 
 The sort skips digits that are the same in every key; it may stop after the highest few varying
-digits and then sorts each group of keys with an equal prefix in place (one thread for up to 8
-items, one block with a bitonic network for up to 4096, a chunked radix sort of the remaining
-digits beyond that); and it sorts by every varying digit when a digit histogram has a heavy bin.
+digits and then sorts each group of keys with an equal prefix in place (in shared memory for up to
+8 items, one block with a bitonic network for up to 4096, a chunked radix sort of the remaining
+digits beyond that); and it sorts by every varying digit when every prefix digit has a heavy bin.
 Each case runs mixed batches through the CUDA path and through the oracle and compares every result
 and the final layout bit-exactly.  A mis-sorted batch routes operations to the wrong buckets or
 folds one key's operations in the wrong order (the groups below hold repeated keys with inserts,
@@ -120,7 +120,7 @@ def test_all_keys_equal(fx):
 
 
 def test_prefix_groups_32bit_keys(fx):
-    """2^16 ops of 32-bit keys: the plan sorts the top 3 digits; a group of about 600 ops (bitonic)
+    """2^16 ops of 32-bit keys: the plan sorts the top 2 digits; a group of about 600 ops (bitonic)
     and 100 groups of 2..8."""
     rng = np.random.default_rng(5)
     kw, n = 32, 1 << 16
