@@ -19,6 +19,7 @@ const char* kKernelNames[K_NUM] = {
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
     "update_count", "alloc_copy", "update_apply", "admit",
     "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill", "split_chains", "merge_underfull",
+    "update_heavy",
 };
 
 cudaError_t Arena::ensure(size_t bytes)
@@ -422,7 +423,7 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff, nullptr));
     const HeavyList hl = heavy_list(c, n);
     if (!hl.list || !hl.n) return FLIX_ENOMEM;
-    CK(update_count<K>(c, ukey, uop, uoff, nf, allgone, hl));
+    CK(update_count<K>(c, ukey, uop, uval, uoff, nf, allgone, hl));
     CK(scan_exclusive<uint64_t, uint64_t>(c, nf, nf_off, nb));
     const uint64_t* nf_total = nf_off + nb;
     const uint64_t* rtot_dev = (mixed && roff) ? roff + n : nullptr;
@@ -885,6 +886,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     h->NS = cfg->node_size;
     h->p = std::max<uint32_t>(1, (uint32_t)(((uint64_t)h->NS * cfg->fill_pct) / 100));
     cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
     cudaError_t e;
     if ((e = cudaMalloc(&h->err, 64)) || (e = cudaMemset(h->err, 0, 64)) ||
         (e = cudaMalloc(&h->dstate, sizeof(DevState))) || (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||

@@ -51,7 +51,7 @@ enum KernelId {
     K_PARTITION, K_READ_POINT, K_UNSORT, K_RANGE_COUNT, K_RANGE_FILL,
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
     K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY, K_ADMIT,
-    K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL, K_SPLIT, K_MERGE,
+    K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL, K_SPLIT, K_MERGE, K_HEAVY,
     K_NUM
 };
 
@@ -121,6 +121,7 @@ struct flix_index {
     uint64_t nb = 0;    // buckets
     uint64_t free_top = 0;  // number of ids on the free stack (host mirror of the device state)
     int device = 0;
+    int nsm = 148;      // SMs of the device
 
     // node pool and buckets (device)
     void* keys = nullptr;
@@ -302,11 +303,18 @@ struct HeavyList {
     void* list = nullptr;
     uint32_t* n = nullptr;   // device count
     uint32_t cap = 0;
+    void* snap_k = nullptr;  // snapshots of the heavy nodes' keys and values (cap x NS each)
+    void* snap_v = nullptr;
+    uint32_t* nchunks = nullptr;     // device count of their chunks; nchunks[1], nchunks[2]: block
+                                     // counters of the find and count kernels (zero between batches)
+    uint32_t* chunk_add = nullptr;   // absent keys each chunk inserts
+    uint32_t* chunk_pre = nullptr;   // their exclusive prefix
+    uint32_t chunk_cap = 0;
+    uint64_t batch = 0;              // updates of the batch (none is heavy unless > HEAVY_U)
 };
 template <class K>
-cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff,
-                         uint64_t* nf, uint8_t* allgone,
-                         const HeavyList& hl);
+cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint32_t* uoff,
+                         uint64_t* nf, uint8_t* allgone, const HeavyList& hl);
 
 template <class K>
 cudaError_t update_apply(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval,

@@ -357,22 +357,30 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
 {
     constexpr int P = sizeof(K);
     __shared__ uint32_t sw[RADIX / 32];
+    __shared__ float sq[RADIX / 32];
     __shared__ uint32_t s_const[P], s_max[P];
+    __shared__ float s_p2[P];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int p = 0; p < P; p++) {
         uint32_t* hp = hist + (size_t)p * RADIX;
         const uint32_t c = hp[threadIdx.x];
         const int all_one_bin = __syncthreads_or((uint64_t)c == n);
         uint32_t m = c;
+        float q = (float)c * (float)c;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
-        if (lane == 0) sw[warp] = m;
+        for (int o = 16; o > 0; o >>= 1) {
+            m = max(m, __shfl_xor_sync(FULL, m, o));
+            q += __shfl_xor_sync(FULL, q, o);
+        }
+        if (lane == 0) { sw[warp] = m; sq[warp] = q; }
         __syncthreads();
         if (threadIdx.x == 0) {
             uint32_t mm = 0;
-            for (int w = 0; w < RADIX / 32; w++) mm = max(mm, sw[w]);
+            float qq = 0.0f;
+            for (int w = 0; w < RADIX / 32; w++) { mm = max(mm, sw[w]); qq += sq[w]; }
             s_max[p] = mm;
             s_const[p] = all_one_bin;
+            s_p2[p] = qq / ((float)n * (float)n);   // chance that two items share this digit
         }
         __syncthreads();
         uint32_t tot;
@@ -393,14 +401,25 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
         pl.npass = 1;
     } else {
         int use = m;
-        if ((int)h < m) {
+        // prefix digits: at least h, and enough that the other items expected in a random item's
+        // group, n times the chance that two items share every prefix digit (digits taken as
+        // independent), stay at most 2 (uniform keys at h give about 1); dense or skewed keys
+        // need more digits than uniform ones
+        int hh = 0;
+        float e = (float)n;
+        while (hh < m) {
+            e *= s_p2[nc[hh]];
+            hh++;
+            if (hh >= (int)h && e <= 2.0f) break;
+        }
+        if (hh < m) {
             // a group of g keys with one prefix puts g keys into one bin of every prefix digit, so
             // the largest group is at most the smallest largest-bin over the prefix digits: one
             // prefix digit without a heavy bin bounds every group the finish meets
             bool heavy = true;
-            for (int q = 0; q < (int)h; q++) heavy &= (uint64_t)s_max[nc[q]] > n / 64 + 256;
+            for (int q = 0; q < hh; q++) heavy &= (uint64_t)s_max[nc[q]] > n / 64 + 256;
             if (!heavy) {
-                use = (int)h;
+                use = hh;
                 pl.finish = 1;
                 pl.pmask = ~0ull << (8 * nc[use - 1]);
             }

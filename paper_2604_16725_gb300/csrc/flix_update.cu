@@ -378,7 +378,23 @@ struct HeavyNode {
     uint32_t node, j, k, t, sz;
     uint32_t need_before;   // nodes the bucket's earlier chain nodes allocate in this batch
     uint64_t b;             // its bucket
+    uint32_t chunk0;        // its first chunk of HV_CHUNK updates in the chunk arrays
+    uint32_t add, del;      // absent keys it inserts, present keys it deletes
+    uint32_t delm[4];       // node slots the batch deletes (NS <= 128)
 };
+constexpr uint32_t HEAVY_FLAG = 0x80000000u;   // tnode[node] = slot | HEAVY_FLAG between find and count
+constexpr int FIND_GROUPS = 8;                 // groups of 32 buckets per warp of k_heavy_find
+
+// Heavy nodes are handled in chunks of HV_CHUNK updates, spread over all blocks:
+//   k_heavy_find   lists the nodes with more than HEAVY_U updates (only buckets with that many
+//                  updates are walked) and snapshots each one's keys and values; its last block
+//                  to finish numbers the chunks (first chunk of each node);
+//   k_heavy_count  per chunk: present keys it deletes (marked) or upserts (snapshot value replaced)
+//                  and absent keys it inserts (counted per chunk and per node); its last block
+//                  takes the prefix of the chunk counts, so each chunk knows the inserts before it;
+//   k_update_count takes a heavy node's merged size from these counts;
+//   k_update_heavy per chunk: places its inserted keys and the node keys in its key range.
+// Every kernel reads the snapshot, because placing writes into the node itself.
 
 template <class K>
 __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
@@ -428,6 +444,28 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
             const uint32_t k = routed_end(ukey, j, ue, bd);
             if (k == j) {
                 all_dropped = false;
+            } else if (k - j > HEAVY_U) {
+                // listed by k_heavy_find and counted by k_heavy_count
+                const uint32_t slot = tnode[node];
+                uint32_t t = 0;
+                if (slot & HEAVY_FLAG) {
+                    HeavyNode& hn = heavy[slot & ~HEAVY_FLAG];
+                    t = sz + hn.add - hn.del;
+                    __syncwarp();
+                    if (lane == 0) {
+                        tnode[node] = t;
+                        hn.t = t;
+                        hn.need_before = (uint32_t)need;
+                    }
+                } else if (lane == 0) {
+                    atomicOr(ix.err, ERR_STEPS);   // the list overflowed
+                }
+                const uint32_t q = pieces_of(t, NS);
+                if (q > 1) need += q - 1;
+                if (t == 0) dropped++;
+                else all_dropped = false;
+                j = k;
+                __syncwarp();
             } else {
                 stage_regs<K>(sk, nullptr, sz, lane, rk, rv);
                 __syncwarp();
@@ -454,14 +492,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
                 add = warp_sum<K>(add);
                 del = warp_sum<K>(del);
                 const uint32_t t = sz + add - del;
-                if (lane == 0) {
-                    tnode[node] = t;
-                    if (k - j > HEAVY_U) {   // merged later by a block of its own (k_update_heavy)
-                        const uint32_t slot = atomicAdd(heavy_n, 1u);
-                        if (slot < heavy_cap) heavy[slot] = HeavyNode{node, j, k, t, sz, (uint32_t)need, b0 + i};
-                        else atomicOr(ix.err, ERR_STEPS);
-                    }
-                }
+                if (lane == 0) tnode[node] = t;
                 const uint32_t q = pieces_of(t, NS);
                 if (q > 1) need += q - 1;
                 if (t == 0) dropped++;
@@ -688,12 +719,254 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
     }
 }
 
-// A heavy node merged by one block: its keys and values are staged in shared memory; its updates
-// stream through in chunks of HV_CHUNK (present deletions marked, upserts of present keys noted,
-// inserted updates placed at (surviving node keys below) + (inserted updates before), the latter
-// from a block scan and a running carry); each node key counts the inserted updates below it as
-// the chunks pass; at the end the surviving node keys are placed.  Same positions and pieces as
-// the warp path.
+// Chunks of the heavy nodes: chunk g belongs to the node h with chunk0[h] <= g < chunk0[h + 1].
+__device__ __forceinline__ uint32_t heavy_of_chunk(const HeavyNode* __restrict__ heavy, uint32_t nh, uint32_t g)
+{
+    uint32_t lo = 0, len = nh;
+    while (len > 0) {            // last h with chunk0[h] <= g
+        const uint32_t half = len >> 1;
+        if (heavy[lo + half].chunk0 <= g) { lo += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return lo - 1;
+}
+
+// Numbers the heavy nodes' chunks (one block of any multiple of 32 threads up to 256): chunk0 of
+// each node, the total in *nchunks.  The records come from other blocks: read past L1.
+__device__ void heavy_chunks(HeavyNode* __restrict__ heavy, const uint32_t* __restrict__ heavy_n, uint32_t heavy_cap,
+                             uint32_t* __restrict__ nchunks, uint32_t chunk_cap, uint32_t* __restrict__ err)
+{
+    __shared__ uint32_t sw[8];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nh = min(__ldcg(heavy_n), heavy_cap);
+    uint32_t carry = 0;
+    for (uint32_t h0 = 0; h0 < nh; h0 += blockDim.x) {
+        const uint32_t h = h0 + threadIdx.x;
+        const uint32_t c = h < nh ? (__ldcg(&heavy[h].k) - __ldcg(&heavy[h].j) + HV_CHUNK - 1) / HV_CHUNK : 0;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) sw[w] = x;
+        __syncthreads();
+        uint32_t wbase = 0, total = 0;
+        for (uint32_t q = 0; q < nw; q++) {
+            if (q < w) wbase += sw[q];
+            total += sw[q];
+        }
+        if (h < nh) heavy[h].chunk0 = carry + wbase + x - c;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry > chunk_cap) {
+            atomicOr(err, ERR_STEPS);
+            carry = chunk_cap;
+        }
+        nchunks[0] = carry;
+    }
+}
+
+// Lists the heavy nodes: a warp walks the chains of its buckets that hold more than HEAVY_U
+// updates (the same walk as the count pass: routed_end per node), records each node with more than
+// HEAVY_U of them, marks it in tnode and snapshots its keys and values.  Other warps only read
+// their buckets' update ranges.
+template <class K>
+__global__ void __launch_bounds__(UP_THREADS) k_heavy_find(DevIdx<K> ix, const K* __restrict__ ukey,
+                                                           const uint32_t* __restrict__ uoff,
+                                                           uint32_t* __restrict__ tnode, HeavyNode* __restrict__ heavy,
+                                                           uint32_t* __restrict__ heavy_n, uint32_t heavy_cap,
+                                                           K* __restrict__ snap_k, K* __restrict__ snap_v,
+                                                           uint32_t* __restrict__ nchunks, uint32_t chunk_cap)
+{
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t NS = ix.NS;
+    bool failed = false;
+    // a warp takes FIND_GROUPS groups of 32 buckets, their update ranges loaded at once
+    const uint64_t g0 = ((uint64_t)blockIdx.x * UP_WARPS + w) * FIND_GROUPS;
+    uint32_t usv[FIND_GROUPS], uev[FIND_GROUPS];
+#pragma unroll
+    for (int q = 0; q < FIND_GROUPS; q++) {
+        const uint64_t bl = (g0 + q) * 32 + lane;
+        usv[q] = bl < ix.nb ? uoff[bl] : 0u;
+        uev[q] = bl < ix.nb ? uoff[bl + 1] : 0u;
+    }
+#pragma unroll 1
+    for (int q = 0; q < FIND_GROUPS && !failed; q++) {
+    const uint64_t b0 = (g0 + q) * 32;
+    const uint32_t us = usv[q], ue0 = uev[q];
+    uint32_t mask = __ballot_sync(FULL, ue0 - us > HEAVY_U);
+    while (mask && !failed) {
+        const uint32_t i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t ue = __shfl_sync(FULL, ue0, i);
+        uint32_t j = __shfl_sync(FULL, us, i);
+        uint32_t node = ix.head[b0 + i];
+        uint32_t sz = ix.size[node], nx = ix.next[node];
+        K bd = ix.bound[node];
+        uint32_t steps = 0;
+        for (;;) {
+            const uint32_t k = routed_end(ukey, j, ue, bd);
+            if (k - j > HEAVY_U) {
+                uint32_t slot = 0;
+                if (lane == 0) slot = atomicAdd(heavy_n, 1u);
+                slot = __shfl_sync(FULL, slot, 0);
+                if (slot < heavy_cap) {
+                    if (lane == 0) {
+                        HeavyNode hn;
+                        hn.node = node; hn.j = j; hn.k = k; hn.t = 0; hn.sz = sz; hn.need_before = 0;
+                        hn.b = b0 + i; hn.chunk0 = 0; hn.add = 0; hn.del = 0;
+                        hn.delm[0] = hn.delm[1] = hn.delm[2] = hn.delm[3] = 0;
+                        heavy[slot] = hn;
+                        tnode[node] = slot | HEAVY_FLAG;
+                    }
+                    for (uint32_t s2 = lane; s2 < sz; s2 += 32) {
+                        snap_k[(uint64_t)slot * NS + s2] = ix.keys[(uint64_t)node * NS + s2];
+                        snap_v[(uint64_t)slot * NS + s2] = ix.vals[(uint64_t)node * NS + s2];
+                    }
+                } else if (lane == 0) {
+                    atomicOr(ix.err, ERR_STEPS);
+                }
+            }
+            j = k;
+            if (j >= ue) break;
+            node = nx;
+            if (node == NIL || ++steps > ix.cap) {
+                if (lane == 0) atomicOr(ix.err, ERR_CHAIN);
+                failed = true;
+                break;
+            }
+            sz = ix.size[node];
+            bd = ix.bound[node];
+            nx = ix.next[node];
+        }
+    }
+    }
+    // the last block to finish numbers the chunks
+    __shared__ uint32_t s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&nchunks[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        heavy_chunks(heavy, heavy_n, heavy_cap, nchunks, chunk_cap, ix.err);
+        if (threadIdx.x == 0) nchunks[1] = 0;
+    }
+}
+
+// Exclusive prefix of the chunk counts over all chunks (one block of HV_THREADS threads); a chunk's
+// inserts before it in its node are chunk_pre[g] - chunk_pre[chunk0].  The counts come from other
+// blocks: read past L1.
+__device__ void heavy_scan(const uint32_t* __restrict__ chunk_add, uint32_t ng, uint32_t* __restrict__ chunk_pre)
+{
+    __shared__ uint32_t sw[HV_THREADS / 32];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (uint32_t g0 = 0; g0 < ng; g0 += HV_THREADS) {
+        const uint32_t g = g0 + threadIdx.x;
+        const uint32_t c = g < ng ? __ldcg(chunk_add + g) : 0;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) sw[w] = x;
+        __syncthreads();
+        uint32_t wbase = 0, total = 0;
+        for (int q = 0; q < HV_THREADS / 32; q++) {
+            if (q < (int)w) wbase += sw[q];
+            total += sw[q];
+        }
+        if (g < ng) chunk_pre[g] = carry + wbase + x - c;
+        carry += total;
+        __syncthreads();
+    }
+}
+
+// Per chunk of a heavy node: present keys it deletes are marked, present keys it upserts take
+// their new value in the snapshot, absent keys it inserts are counted (chunk_add[g] and the node's
+// add; deletions in the node's del).
+template <class K>
+__global__ void __launch_bounds__(HV_THREADS) k_heavy_count(uint32_t NS, const K* __restrict__ ukey,
+                                                           const uint32_t* __restrict__ uop, const K* __restrict__ uval,
+                                                           HeavyNode* __restrict__ heavy,
+                                                           const uint32_t* __restrict__ heavy_n, uint32_t heavy_cap,
+                                                           const K* __restrict__ snap_k, K* __restrict__ snap_v,
+                                                           uint32_t* __restrict__ nchunks,
+                                                           uint32_t* __restrict__ chunk_add,
+                                                           uint32_t* __restrict__ chunk_pre)
+{
+    __shared__ K nk[128];
+    __shared__ uint32_t sa[HV_THREADS / 32], sd[HV_THREADS / 32];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nh = min(*heavy_n, heavy_cap), ng = *nchunks;
+    for (uint32_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        const uint32_t h = heavy_of_chunk(heavy, nh, g);
+        const uint32_t sz = heavy[h].sz;
+        const uint32_t c0 = heavy[h].j + (g - heavy[h].chunk0) * HV_CHUNK;
+        const uint32_t cn = min((uint32_t)HV_CHUNK, heavy[h].k - c0);
+        for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) nk[s2] = snap_k[(uint64_t)h * NS + s2];
+        __syncthreads();
+        uint32_t add = 0, del = 0;
+#pragma unroll
+        for (int r = 0; r < HV_ITEMS; r++) {
+            const uint32_t i = r * HV_THREADS + threadIdx.x;
+            if (i < cn) {
+                const K key = ukey[c0 + i];
+                const uint32_t op = uop[c0 + i];
+                const uint32_t pos = smem_lower_bound(nk, sz, key);
+                const bool present = pos < sz && nk[pos] == key;
+                if (present && op == EFF_DEL) {
+                    atomicOr(&heavy[h].delm[pos >> 5], 1u << (pos & 31));
+                    del++;
+                }
+                if (present && op == EFF_UPS) snap_v[(uint64_t)h * NS + pos] = uval[c0 + i];
+                add += !present && (op == EFF_INS || op == EFF_UPS);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            add += __shfl_xor_sync(FULL, add, o);
+            del += __shfl_xor_sync(FULL, del, o);
+        }
+        if (lane == 0) { sa[w] = add; sd[w] = del; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t ta = 0, td = 0;
+            for (int q = 0; q < HV_THREADS / 32; q++) { ta += sa[q]; td += sd[q]; }
+            chunk_add[g] = ta;
+            if (ta) atomicAdd(&heavy[h].add, ta);
+            if (td) atomicAdd(&heavy[h].del, td);
+        }
+        __syncthreads();   // nk, sa and sd are rewritten for the next chunk
+    }
+    // the last block to finish takes the prefix of the chunk counts
+    __shared__ uint32_t s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&nchunks[2], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        heavy_scan(chunk_add, ng, chunk_pre);
+        if (threadIdx.x == 0) nchunks[2] = 0;
+    }
+}
+
+// Places a heavy node's pairs, one chunk of its updates per block step.  The snapshot of the node
+// (with upserted values) and its deletion marks are staged in shared memory.  An inserted key goes
+// to (surviving node keys below it) + (inserted keys before it: the chunk's carry from the scan
+// plus a block scan inside the chunk); a surviving node key goes to (surviving node keys below it)
+// + (inserted keys below it), placed by the chunk whose key range holds it (the first chunk also
+// takes the keys below every update, the last the keys above).  Same positions and pieces as the
+// warp path; piece metadata comes from k_update_apply.
 template <class K>
 __global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const K* __restrict__ ukey,
                                                              const uint32_t* __restrict__ uop,
@@ -702,31 +975,36 @@ __global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const
                                                              const uint64_t* __restrict__ nf_off,
                                                              const HeavyNode* __restrict__ heavy,
                                                              const uint32_t* __restrict__ heavy_n, uint32_t heavy_cap,
+                                                             const K* __restrict__ snap_k, const K* __restrict__ snap_v,
+                                                             const uint32_t* __restrict__ nchunks,
+                                                             const uint32_t* __restrict__ chunk_pre,
                                                              const DevState* __restrict__ ds)
 {
     if (!ds->admitted) return;
-    __shared__ K nk[128], nv[128], newv[128];
-    __shared__ uint32_t ins_below[128];
-    __shared__ uint8_t ups[128];
+    __shared__ K nk[128], nv[128];
     __shared__ uint32_t delm[4];
     __shared__ K ck[HV_CHUNK];
     __shared__ uint32_t cex[HV_CHUNK + 1];
     __shared__ uint32_t sw[HV_THREADS / 32];
     const uint32_t NS = ix.NS, S2 = NS >> 1;
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t nh = min(*heavy_n, heavy_cap);
-    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint32_t nh = min(*heavy_n, heavy_cap), ng = *nchunks;
+    for (uint32_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        const uint32_t h = heavy_of_chunk(heavy, nh, g);
         const HeavyNode hn = heavy[h];
         const uint32_t sz = hn.sz;
         const uint32_t hq = pieces_of(hn.t, NS);
         const uint64_t abase = (nf_off[hn.b] & 0xFFFFFFFFull) + hn.need_before;   // alloc_ids of its pieces 1..
+        const uint32_t c = g - hn.chunk0;
+        const uint32_t c0 = hn.j + c * HV_CHUNK;
+        const uint32_t cn = min((uint32_t)HV_CHUNK, hn.k - c0);
+        const bool last = c0 + cn == hn.k;
+        const uint32_t carry = chunk_pre[g] - chunk_pre[hn.chunk0];
         for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
-            nk[s2] = ix.keys[(uint64_t)hn.node * NS + s2];
-            nv[s2] = ix.vals[(uint64_t)hn.node * NS + s2];
-            ins_below[s2] = 0;
-            ups[s2] = 0;
+            nk[s2] = snap_k[(uint64_t)h * NS + s2];
+            nv[s2] = snap_v[(uint64_t)h * NS + s2];
         }
-        if (threadIdx.x < 4) delm[threadIdx.x] = 0;
+        if (threadIdx.x < 4) delm[threadIdx.x] = hn.delm[threadIdx.x];
         __syncthreads();
         auto place = [&](uint32_t p, K key, K val) {
             uint32_t r = 0;
@@ -743,82 +1021,65 @@ __global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const
             if (pos & 31) d += __popc(delm[pos >> 5] & ((1u << (pos & 31)) - 1));
             return d;
         };
-        uint32_t carry = 0;
-        for (uint32_t c0 = hn.j; c0 < hn.k; c0 += HV_CHUNK) {
-            const uint32_t cn = min((uint32_t)HV_CHUNK, hn.k - c0);
-            // items i = threadIdx.x * HV_ITEMS + r: consecutive per thread, for the scan
-            uint32_t pos[HV_ITEMS];
-            bool add[HV_ITEMS];
-            uint32_t cnt = 0;
+        // items i = threadIdx.x * HV_ITEMS + r: consecutive per thread, for the scan
+        uint32_t pos[HV_ITEMS];
+        bool add[HV_ITEMS];
+        uint32_t cnt = 0;
 #pragma unroll
-            for (int r = 0; r < HV_ITEMS; r++) {
-                const uint32_t i = threadIdx.x * HV_ITEMS + r;
-                add[r] = false;
-                pos[r] = 0;
-                if (i < cn) {
-                    const K key = ukey[c0 + i];
-                    const uint32_t op = uop[c0 + i];
-                    uint32_t lo = 0, len = sz;
-                    while (len > 0) {
-                        const uint32_t half = len >> 1;
-                        if (nk[lo + half] < key) { lo += half + 1; len -= half + 1; }
-                        else len = half;
-                    }
-                    pos[r] = lo;
-                    const bool present = lo < sz && nk[lo] == key;
-                    if (present && op == EFF_DEL) atomicOr(&delm[lo >> 5], 1u << (lo & 31));
-                    if (present && op == EFF_UPS) { newv[lo] = uval[c0 + i]; ups[lo] = 1; }
-                    add[r] = !present && (op == EFF_INS || op == EFF_UPS);
-                    ck[i] = key;
-                    cnt += add[r];
-                }
+        for (int r = 0; r < HV_ITEMS; r++) {
+            const uint32_t i = threadIdx.x * HV_ITEMS + r;
+            add[r] = false;
+            pos[r] = 0;
+            if (i < cn) {
+                const K key = ukey[c0 + i];
+                const uint32_t op = uop[c0 + i];
+                const uint32_t lo = smem_lower_bound(nk, sz, key);
+                pos[r] = lo;
+                const bool present = lo < sz && nk[lo] == key;
+                add[r] = !present && (op == EFF_INS || op == EFF_UPS);
+                ck[i] = key;
+                cnt += add[r];
             }
-            // block exclusive scan of the per-thread counts
-            uint32_t x = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            if (lane == 31) sw[w] = x;
-            __syncthreads();
-            uint32_t wbase = 0, total = 0;
-            for (int q2 = 0; q2 < HV_THREADS / 32; q2++) {
-                if (q2 < (int)w) wbase += sw[q2];
-                total += sw[q2];
-            }
-            uint32_t ex = wbase + x - cnt;
-#pragma unroll
-            for (int r = 0; r < HV_ITEMS; r++) {
-                const uint32_t i = threadIdx.x * HV_ITEMS + r;
-                if (i < cn) cex[i] = ex;
-                ex += add[r];
-            }
-            if (threadIdx.x == 0) cex[cn] = total;
-            __syncthreads();   // deletion marks and cex complete
-#pragma unroll
-            for (int r = 0; r < HV_ITEMS; r++) {
-                const uint32_t i = threadIdx.x * HV_ITEMS + r;
-                if (add[r]) place(pos[r] - dels_below(pos[r]) + carry + cex[i], ck[i], uval[c0 + i]);
-            }
-            // each node key counts the inserted updates of this chunk below it
-            for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
-                uint32_t lo = 0, len = cn;
-                while (len > 0) {
-                    const uint32_t half = len >> 1;
-                    if (ck[lo + half] < nk[s2]) { lo += half + 1; len -= half + 1; }
-                    else len = half;
-                }
-                ins_below[s2] += cex[lo];
-            }
-            carry += total;
-            __syncthreads();   // ck, cex and sw are rewritten by the next chunk
         }
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) sw[w] = x;
+        __syncthreads();
+        uint32_t wbase = 0, total = 0;
+        for (int q2 = 0; q2 < HV_THREADS / 32; q2++) {
+            if (q2 < (int)w) wbase += sw[q2];
+            total += sw[q2];
+        }
+        uint32_t ex = wbase + x - cnt;
+#pragma unroll
+        for (int r = 0; r < HV_ITEMS; r++) {
+            const uint32_t i = threadIdx.x * HV_ITEMS + r;
+            if (i < cn) cex[i] = ex;
+            ex += add[r];
+        }
+        if (threadIdx.x == 0) cex[cn] = total;
+        __syncthreads();   // ck and cex complete
+#pragma unroll
+        for (int r = 0; r < HV_ITEMS; r++) {
+            const uint32_t i = threadIdx.x * HV_ITEMS + r;
+            if (add[r]) place(pos[r] - dels_below(pos[r]) + carry + cex[i], ck[i], uval[c0 + i]);
+        }
+        // the node keys in this chunk's key range: (key before the chunk, last key of the chunk]
+        const K lo_key = c > 0 ? ukey[c0 - 1] : K(0);
+        const K hi_key = ck[cn - 1];
         for (uint32_t s2 = threadIdx.x; s2 < sz; s2 += HV_THREADS) {
+            const K key = nk[s2];
+            if (c > 0 && !(lo_key < key)) continue;
+            if (!last && hi_key < key) continue;
             if ((delm[s2 >> 5] >> (s2 & 31)) & 1u) continue;
-            place(s2 - dels_below(s2) + ins_below[s2], nk[s2], ups[s2] ? newv[s2] : nv[s2]);
+            const uint32_t lo = smem_lower_bound(ck, cn, key);
+            place(s2 - dels_below(s2) + carry + cex[lo], key, nv[s2]);
         }
-        __syncthreads();   // shared state is reset for the next heavy node
+        __syncthreads();   // shared state is rewritten for the next chunk
     }
 }
 
@@ -901,7 +1162,9 @@ void preload_update_kernels()
     FLIX_TOUCH(k_fold_write_hom<K>);         \
     FLIX_TOUCH(k_update_count<K>);           \
     FLIX_TOUCH(k_update_apply<K>);           \
-    FLIX_TOUCH(k_update_heavy<K>)
+    FLIX_TOUCH(k_update_heavy<K>);           \
+    FLIX_TOUCH(k_heavy_find<K>);             \
+    FLIX_TOUCH(k_heavy_count<K>)
     FLIX_TOUCH_K(uint32_t);
     FLIX_TOUCH_K(uint64_t);
 #undef FLIX_TOUCH_K
@@ -959,31 +1222,59 @@ cudaError_t fold_updates(Ctx& c, const K* skeys, const uint32_t* sidx, uint64_t 
 }
 
 template <class K>
-cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const uint32_t* uoff, uint64_t* nf,
-                         uint8_t* allgone, const HeavyList& hl)
+cudaError_t update_count(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint32_t* uoff,
+                         uint64_t* nf, uint8_t* allgone, const HeavyList& hl)
 {
     const uint32_t grid = div_up(div_up(c.h->nb, 32), UP_WARPS);
-    cudaError_t e = fill_bytes(c, hl.n, 0, 4);
+    cudaError_t e = fill_bytes(c, hl.n, 0, 16);   // heavy count, chunk count, block counters
     if (e) return e;
+    K* snap_k = static_cast<K*>(hl.snap_k);
+    K* snap_v = static_cast<K*>(hl.snap_v);
+    HeavyNode* heavy = static_cast<HeavyNode*>(hl.list);
+    if (hl.batch > HEAVY_U) {   // no node can take more than HEAVY_U updates of a smaller batch
+        const uint32_t fgrid = div_up(div_up(c.h->nb, 32), (uint64_t)UP_WARPS * FIND_GROUPS);
+        if ((e = launch(c, K_HEAVY, dim3(fgrid), dim3(UP_THREADS), 0, k_heavy_find<K>, dev_view<K>(c.h), ukey, uoff,
+                        c.h->tnode, heavy, hl.n, hl.cap, snap_k, snap_v, hl.nchunks, hl.chunk_cap)))
+            return e;
+        if ((e = launch(c, K_HEAVY, dim3(4 * c.h->nsm), dim3(HV_THREADS), 0, k_heavy_count<K>, c.h->NS, ukey, uop,
+                        uval, heavy, (const uint32_t*)hl.n, hl.cap, (const K*)snap_k, snap_v, hl.nchunks, hl.chunk_add,
+                        hl.chunk_pre)))
+            return e;
+    }
     return launch(c, K_UPD_COUNT, dim3(grid), dim3(UP_THREADS), count_smem<K>(c.h->NS), k_update_count<K>,
                   dev_view<K>(c.h), ukey, uop, uoff, c.h->tnode, nf, allgone, static_cast<HeavyNode*>(hl.list),
                   hl.n, hl.cap);
 }
 
 uint32_t heavy_cap_of(uint64_t n) { return (uint32_t)(n / HEAVY_U + 2); }   // disjoint runs of > HEAVY_U updates
+// a run of u updates has ceil(u / HV_CHUNK) chunks
+uint32_t chunk_cap_of(uint64_t n) { return (uint32_t)(n / HV_CHUNK + heavy_cap_of(n) + 1); }
 
 HeavyList heavy_list(Ctx& c, uint64_t n)
 {
     HeavyList hl;
     hl.cap = heavy_cap_of(n);
+    hl.chunk_cap = chunk_cap_of(n);
+    hl.batch = n;
     hl.list = c.h->arena.take<HeavyNode>(hl.cap);
-    hl.n = c.h->arena.take<uint32_t>(1);
+    hl.n = c.h->arena.take<uint32_t>(4);
+    hl.nchunks = hl.n ? hl.n + 1 : nullptr;
+    const size_t snap = (size_t)hl.cap * c.h->NS * c.h->ks;
+    hl.snap_k = c.h->arena.take<unsigned char>(snap);
+    hl.snap_v = c.h->arena.take<unsigned char>(snap);
+    hl.chunk_add = c.h->arena.take<uint32_t>(hl.chunk_cap);
+    hl.chunk_pre = c.h->arena.take<uint32_t>(hl.chunk_cap);
+    if (!hl.snap_k || !hl.snap_v || !hl.nchunks || !hl.chunk_add || !hl.chunk_pre) hl.list = nullptr;
     return hl;
 }
 
+// (with the largest node, 128 slots of 8 bytes)
 size_t heavy_scratch_bytes(uint64_t n)
 {
-    return ((size_t)heavy_cap_of(n) * sizeof(HeavyNode) + 255) / 256 * 256 + 256;
+    const size_t al256 = 256;
+    auto a = [&](size_t b) { return (b + al256 - 1) / al256 * al256; };
+    return a((size_t)heavy_cap_of(n) * sizeof(HeavyNode)) + a(4) + 2 * a((size_t)heavy_cap_of(n) * 128 * 8) + a(4) +
+           2 * a((size_t)chunk_cap_of(n) * 4) + 256;
 }
 
 template <class K>
@@ -1000,11 +1291,11 @@ template <class K>
 cudaError_t update_heavy(Ctx& c, const K* ukey, const uint32_t* uop, const K* uval, const uint64_t* nf_off,
                          const uint32_t* alloc_ids, const HeavyList& hl)
 {
-    int nsm = 148;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.h->device);
-    return launch(c, K_UPD_APPLY, dim3(nsm), dim3(HV_THREADS), 0, k_update_heavy<K>, dev_view<K>(c.h), ukey, uop, uval,
-                  alloc_ids, nf_off, (const HeavyNode*)hl.list, (const uint32_t*)hl.n, hl.cap,
-                  (const DevState*)c.h->dstate);
+    if (hl.batch <= HEAVY_U) return cudaSuccess;
+    return launch(c, K_HEAVY, dim3(4 * c.h->nsm), dim3(HV_THREADS), 0, k_update_heavy<K>, dev_view<K>(c.h), ukey, uop,
+                  uval, alloc_ids, nf_off, (const HeavyNode*)hl.list, (const uint32_t*)hl.n, hl.cap,
+                  (const K*)hl.snap_k, (const K*)hl.snap_v, (const uint32_t*)hl.nchunks,
+                  (const uint32_t*)hl.chunk_pre, (const DevState*)c.h->dstate);
 }
 
 cudaError_t alloc_copy(Ctx& c, const uint32_t* free_ids, uint32_t* out, uint64_t cap_out)
@@ -1032,7 +1323,8 @@ cudaError_t set_free_top(Ctx& c, uint64_t value)
     template cudaError_t validate_inserts<K>(Ctx&, const uint8_t*, const K*, uint64_t, uint32_t*);             \
     template cudaError_t fold_updates<K>(Ctx&, const K*, const uint32_t*, uint64_t, const uint8_t*, int,       \
                                          const K*, K*, uint32_t*, K*, uint32_t*);                              \
-    template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const uint32_t*, uint64_t*, uint8_t*, const HeavyList&); \
+    template cudaError_t update_count<K>(Ctx&, const K*, const uint32_t*, const K*, const uint32_t*, uint64_t*,  \
+                                         uint8_t*, const HeavyList&);                                          \
     template cudaError_t update_apply<K>(Ctx&, const K*, const uint32_t*, const K*, const uint32_t*,           \
                                          const uint64_t*, const uint8_t*, const uint32_t*);                    \
     template cudaError_t update_heavy<K>(Ctx&, const K*, const uint32_t*, const K*, const uint64_t*,           \

@@ -402,3 +402,68 @@ def test_predecessor_edges(fx, kw, NS):
     same(np_of(pv, kw), e["vals"], "pred.vals")
     em = md.read(np.full(q.size, W.OP_PRED, np.uint8), q)
     same(em["keys"], e["keys"], "model.pred.keys")
+
+
+@pytest.mark.parametrize("kw", [32, 64])
+def test_heavy_nodes_across_chunks(fx, kw):
+    """Heavy nodes are merged in chunks of 2048 updates spread over blocks.  A node of 20 keys gets
+    9000 updates: node keys sit exactly on the first chunk boundary (one deleted, one upserted),
+    between two chunks, below and above every update, and one is inserted again while present.
+    Then two heavy nodes in one chain, then a heavy node that only deletes (it empties and leaves
+    the chain)."""
+    rng = np.random.default_rng(40 + kw)
+    dt = np.uint32 if kw == 32 else np.uint64
+    NS = 64
+    top = (1 << 31) if kw == 32 else (1 << 40)
+    u = np.unique(rng.integers(1 << 20, top, 12000, dtype=np.uint64))[:9000]
+    while u[4096] - u[4095] < 2:
+        u[4096:] += np.uint64(2)
+    extra = np.setdiff1d(np.unique(rng.integers(1 << 20, top, 40, dtype=np.uint64)), u)[:15]
+    load = np.unique(np.concatenate([[5, u[2047], u[2048], u[4095] + 1, u[6000], u[-1] + 100], extra])).astype(np.uint64)
+    vals = (load * np.uint64(7)).astype(dt).astype(np.uint64)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    idx.bulk_load(load.astype(dt), vals.astype(dt))
+    mp, md = oracle_pair(kw, NS, 50, load, vals)
+    assert idx.stats()["buckets"] == 1
+    ops = np.full(u.size, W.OP_INSERT, np.uint8)
+    ops[2047] = W.OP_DELETE
+    keys = u.copy()
+    aux = rng.integers(1, 1 << 30, u.size).astype(np.uint64)
+    # upsert of u[2048] (present): delete then insert; deletes of absent keys above every update key,
+    # so that u[i] stays the i-th update of the node and u[2047] / u[2048] end / start a chunk
+    absent = u[-1] + np.uint64(200) + np.arange(0, 900, 3, dtype=np.uint64)
+    keys = np.concatenate([keys, u[2048:2049], absent])
+    ops = np.concatenate([ops, np.array([W.OP_INSERT], np.uint8), np.full(absent.size, W.OP_DELETE, np.uint8)])
+    ops[2048] = W.OP_DELETE
+    aux = np.concatenate([aux, np.array([12345], np.uint64), np.zeros(absent.size, np.uint64)])
+    p = rng.permutation(keys.size)
+    apply_both(idx, mp, md, ops[p], keys[p].astype(dt), aux[p].astype(dt), kw)
+    compare_layout(idx, md)
+    d = md.dump()
+    # two heavy nodes in one chain: 3000 keys inside the range of the chain's 100th node, 3000 above all
+    lo_b, hi_b = int(d["node_bound"][99]), int(d["node_bound"][100])
+    inside = np.unique(rng.integers(lo_b + 1, hi_b, 6000, dtype=np.uint64))
+    inside = np.setdiff1d(inside, mp.export()[0])[:3000]
+    above = np.arange(int(u[-1]) + 1000, int(u[-1]) + 1000 + 3000 * 3, 3, dtype=np.uint64)
+    node100 = d["keys"][int(d["node_size"][:100].sum()):int(d["node_size"][:101].sum())]
+    k2 = np.concatenate([inside, above, node100[::2]])
+    o2 = np.concatenate([np.full(inside.size + above.size, W.OP_INSERT, np.uint8),
+                         np.full(node100[::2].size, W.OP_DELETE, np.uint8)])
+    a2 = rng.integers(1, 1 << 30, k2.size).astype(np.uint64)
+    p = rng.permutation(k2.size)
+    apply_both(idx, mp, md, o2[p], k2[p].astype(dt), a2[p].astype(dt), kw)
+    compare_layout(idx, md)
+    # a heavy node that only deletes: all keys of the chain's 50th node and 3000 absent keys in its range
+    d = md.dump()
+    lo_b, hi_b = int(d["node_bound"][49]), int(d["node_bound"][50])
+    node50 = d["keys"][int(d["node_size"][:50].sum()):int(d["node_size"][:51].sum())]
+    stored = mp.export()[0]
+    gone = np.setdiff1d(np.unique(rng.integers(lo_b + 1, hi_b + 1, 8000, dtype=np.uint64)), stored)[:3000]
+    k3 = np.concatenate([node50, gone])
+    assert gone.size > 2048
+    idx.delete(k3.astype(dt))
+    mp.update(np.full(k3.size, W.OP_DELETE, np.uint8), k3)
+    md.update(np.full(k3.size, W.OP_DELETE, np.uint8), k3)
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+    idx.close()
