@@ -617,6 +617,12 @@ __global__ void __launch_bounds__(OS_THREADS, 1) k_sort_finish_big(K* __restrict
             if (__syncthreads_or(stop)) break;
         }
         const uint64_t L = s_end - start;
+        // a group already in (key, payload) order stays as it is: a key repeated across the batch,
+        // mostly (the passes are stable, so its copies are in position order)
+        bool descent = false;
+        for (uint64_t j = start + 1 + threadIdx.x; j < start + L; j += OS_THREADS)
+            descent |= kv_less(keys[j], vals[j], keys[j - 1], vals[j - 1]);
+        if (!__syncthreads_or(descent)) continue;
         if (L <= (uint64_t)OS_TILE) {
             uint32_t P2 = 2;
             while (P2 < L) P2 <<= 1;
