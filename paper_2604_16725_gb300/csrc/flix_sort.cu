@@ -448,22 +448,22 @@ __device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
 }
 
 constexpr int FIN_THREADS = 256;
-constexpr int FIN_ITEMS = 7;
+constexpr int FIN_ITEMS = 8;
 constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 
-// One tile of FIN_TILE positions per block.  The tile's keys and payloads, the key before it and
-// HALO positions after it are staged in shared memory (coalesced loads, all issued before the first
-// store).  Every position then finds the bounds of its group of equal prefix (at most SMALL_SEG
-// steps each way) and, in a group of 2..SMALL_SEG items, its rank by (key, payload) among the
-// group's items, and moves to the group's head + rank in a second staging buffer; a group's head
-// lists the group when it is longer than SMALL_SEG.  The work per item follows its group's size
-// (mostly 1 to 3 items), with no thread sorting for a warp.  The moved items go back in coalesced
-// stores when at least an eighth of the tile moved, else one by one.  A group belongs to the tile
-// that holds its head, also where it runs into the next tile (into the halo): a tile never stores
-// the leading positions that continue a group from the tile before.  Sorting permutes a group
-// only, so every position keeps its prefix and the group bounds another block sees stay the same.
+// One tile of FIN_TILE positions per block.  The tile's keys, the key before it and HALO keys after
+// it are staged in shared memory (coalesced loads, all issued before the first store).  Every
+// position then finds the bounds of its group of equal prefix (at most SMALL_SEG steps each way);
+// an item of a group of 2..SMALL_SEG items whose head lies in this tile loads its payload into
+// shared memory, and after a barrier takes its rank by (key, payload) among the group's items and
+// stores itself at the group's head + rank when that differs from where it is.  A group's head
+// lists the group when it is longer than SMALL_SEG.  Singletons and groups already in order cost a
+// key load each and store nothing.  A group belongs to the tile that holds its head, also where it
+// runs into the next tile (into the halo, taken by the first HALO threads), so two blocks never
+// store the same position; and since sorting permutes a group only, every position keeps its
+// prefix and the group bounds another block reads stay the same.
 template <class K>
-__global__ void __launch_bounds__(FIN_THREADS, 4) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
                                                              uint64_t n, SortPlan* __restrict__ plan,
                                                              uint64_t* __restrict__ list, uint64_t list_cap,
                                                              uint32_t* __restrict__ err)
@@ -472,55 +472,35 @@ __global__ void __launch_bounds__(FIN_THREADS, 4) k_sort_finish(K* __restrict__ 
     constexpr int HALO = SMALL_SEG + 1;
     constexpr uint32_t SPAN = FIN_TILE + HALO;
     __shared__ K tk[1 + SPAN];            // tk[1 + j] = key at base + j; tk[0] = key at base - 1
-    __shared__ uint32_t tv[SPAN];
-    __shared__ K ok[SPAN];
-    __shared__ uint32_t ov[SPAN];
-    __shared__ uint32_t s_moved, s_lead, s_ext;
+    __shared__ uint32_t tv[SPAN];         // payloads of the items in groups this tile sorts
     const uint64_t pm = plan->pmask;
     const uint64_t base = (uint64_t)blockIdx.x * FIN_TILE;
     const uint32_t lim = n - base < (uint64_t)SPAN ? (uint32_t)(n - base) : SPAN;
+    const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
     {
         K rk[FIN_ITEMS + 1];
-        uint32_t rv[FIN_ITEMS + 1];
 #pragma unroll
         for (int r = 0; r <= FIN_ITEMS; r++) {
             const uint32_t j = r * FIN_THREADS + threadIdx.x;   // r == FIN_ITEMS: the halo
-            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
-                rk[r] = keys[base + j];
-                rv[r] = vals[base + j];
-            }
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) rk[r] = keys[base + j];
         }
 #pragma unroll
         for (int r = 0; r <= FIN_ITEMS; r++) {
             const uint32_t j = r * FIN_THREADS + threadIdx.x;
-            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
-                tk[1 + j] = rk[r];
-                tv[j] = rv[r];
-            }
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) tk[1 + j] = rk[r];
         }
     }
-    if (threadIdx.x == 0) {
-        if (base > 0) tk[0] = keys[base - 1];
-        s_moved = 0;
-        s_ext = 0;
-    }
+    if (threadIdx.x == 0 && base > 0) tk[0] = keys[base - 1];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // positions that continue a group whose head lies in the tile before
-        uint32_t lead = 0;
-        if (base > 0)
-            while (lead < (uint32_t)HALO && lead < lim && (static_cast<uint64_t>(tk[1 + lead] ^ tk[0]) & pm) == 0)
-                lead++;
-        s_lead = lead;
-    }
-    uint32_t moved = 0;
-    const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
-    // the tile's positions, then (threads 0..HALO-1) the halo positions of a group headed inside
-    for (uint32_t j = threadIdx.x; j < tile_end + HALO; j += FIN_THREADS) {
+    // pass 1: group bounds; the items of groups sorted here bring their payloads
+    uint32_t info[FIN_ITEMS + 1];   // 0, or head | L << 16 of the item's group
+#pragma unroll
+    for (int r = 0; r <= FIN_ITEMS; r++) {
+        info[r] = 0;
+        const uint32_t j = r * FIN_THREADS + threadIdx.x;
+        if (j >= lim || (r == FIN_ITEMS && threadIdx.x >= (uint32_t)HALO)) continue;
         const bool halo = j >= tile_end;
-        if (j >= lim) break;
         const K kj = tk[1 + j];
-        const uint32_t vj = tv[j];
         // group start: walk back while the prefix is equal (inside the tile; base - 1 is tk[0])
         uint32_t h = j, back = 0;
         bool before = false;      // the group starts in the tile before
@@ -533,49 +513,37 @@ __global__ void __launch_bounds__(FIN_THREADS, 4) k_sort_finish(K* __restrict__ 
             h--;
             back++;
         }
-        if (halo && (back > (uint32_t)SMALL_SEG || h >= tile_end || h + SMALL_SEG <= j)) {
-            ok[j] = kj;   // not part of a group this tile sorts (unused)
-            ov[j] = vj;
-            continue;
-        }
+        if (before || back > (uint32_t)SMALL_SEG || (halo && h >= tile_end)) continue;
         uint32_t e = j + 1;
         while (e < lim && e - h <= (uint32_t)SMALL_SEG && (static_cast<uint64_t>(tk[1 + e] ^ kj) & pm) == 0) e++;
         const uint32_t L = e - h;
-        if (before || back > (uint32_t)SMALL_SEG || L > (uint32_t)SMALL_SEG || L == 1) {
-            if (!halo && !before && h == j && L > (uint32_t)SMALL_SEG) {
+        if (L > (uint32_t)SMALL_SEG) {
+            if (!halo && h == j) {
                 const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
                 if (slot < list_cap) list[slot] = base + j;
                 else atomicOr(err, ERR_SORT);
             }
-            ok[j] = kj;   // stays
-            ov[j] = vj;
             continue;
         }
-        uint32_t rank = 0;
-        for (uint32_t i = h; i < e; i++) rank += kv_less(tk[1 + i], tv[i], kj, vj);
-        const uint32_t to = h + rank;
-        ok[to] = kj;
-        ov[to] = vj;
-        moved += to != j;
-        if (!halo && e > tile_end && j == h) s_ext = e - tile_end;     // one group at most runs past
+        if (L == 1) continue;
+        tv[j] = vals[base + j];
+        info[r] = h | L << 16;
     }
-    if (moved) atomicAdd(&s_moved, moved);
     __syncthreads();
-    if (s_moved == 0) return;
-    const uint32_t lead = s_lead, end = tile_end + s_ext;
-    if (s_moved * 8 >= (uint32_t)FIN_TILE) {
-        for (uint32_t j = threadIdx.x; j < end; j += FIN_THREADS) {
-            if (j < lead) continue;
-            keys[base + j] = ok[j];
-            vals[base + j] = ov[j];
-        }
-        return;
-    }
-    for (uint32_t j = threadIdx.x; j < end; j += FIN_THREADS) {
-        if (j < lead) continue;
-        if (ok[j] != tk[1 + j] || ov[j] != tv[j]) {
-            keys[base + j] = ok[j];
-            vals[base + j] = ov[j];
+    // pass 2: each item of a sorted group goes to head + its rank
+#pragma unroll
+    for (int r = 0; r <= FIN_ITEMS; r++) {
+        if (!info[r]) continue;
+        const uint32_t j = r * FIN_THREADS + threadIdx.x;
+        const uint32_t h = info[r] & 0xFFFFu, L = info[r] >> 16;
+        const K kj = tk[1 + j];
+        const uint32_t vj = tv[j];
+        uint32_t rank = 0;
+        for (uint32_t i = h; i < h + L; i++) rank += kv_less(tk[1 + i], tv[i], kj, vj);
+        const uint32_t to = h + rank;
+        if (to != j) {
+            keys[base + to] = kj;
+            vals[base + to] = vj;
         }
     }
 }
