@@ -463,7 +463,7 @@ constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 // store the same position; and since sorting permutes a group only, every position keeps its
 // prefix and the group bounds another block reads stay the same.
 template <class K>
-__global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(FIN_THREADS, 6) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
                                                              uint64_t n, SortPlan* __restrict__ plan,
                                                              uint64_t* __restrict__ list, uint64_t list_cap,
                                                              uint32_t* __restrict__ err)
@@ -479,15 +479,22 @@ __global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ 
     const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
     {
         K rk[FIN_ITEMS + 1];
+        uint32_t rv[FIN_ITEMS + 1];
 #pragma unroll
         for (int r = 0; r <= FIN_ITEMS; r++) {
             const uint32_t j = r * FIN_THREADS + threadIdx.x;   // r == FIN_ITEMS: the halo
-            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) rk[r] = keys[base + j];
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
+                rk[r] = keys[base + j];
+                rv[r] = vals[base + j];
+            }
         }
 #pragma unroll
         for (int r = 0; r <= FIN_ITEMS; r++) {
             const uint32_t j = r * FIN_THREADS + threadIdx.x;
-            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) tk[1 + j] = rk[r];
+            if (j < lim && (r < FIN_ITEMS || threadIdx.x < (uint32_t)HALO)) {
+                tk[1 + j] = rk[r];
+                tv[j] = rv[r];
+            }
         }
     }
     if (threadIdx.x == 0 && base > 0) tk[0] = keys[base - 1];
@@ -526,7 +533,6 @@ __global__ void __launch_bounds__(FIN_THREADS, 8) k_sort_finish(K* __restrict__ 
             continue;
         }
         if (L == 1) continue;
-        tv[j] = vals[base + j];
         info[r] = h | L << 16;
     }
     __syncthreads();
