@@ -451,12 +451,12 @@ constexpr int FIN_THREADS = 256;
 constexpr int FIN_ITEMS = 8;
 constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 
-// One tile of FIN_TILE positions per block.  The tile's keys, the key before it and HALO keys after
-// it are staged in shared memory (coalesced loads, all issued before the first store).  Every
-// position then finds the bounds of its group of equal prefix (at most SMALL_SEG steps each way);
-// an item of a group of 2..SMALL_SEG items whose head lies in this tile loads its payload into
-// shared memory, and after a barrier takes its rank by (key, payload) among the group's items and
-// stores itself at the group's head + rank when that differs from where it is.  A group's head
+// One tile of FIN_TILE positions per block.  The tile's keys and payloads, the key before it and
+// HALO positions after it are staged in shared memory (coalesced loads, all issued before the first
+// store).  Every position then finds the bounds of its group of equal prefix (at most SMALL_SEG
+// steps each way); an item of a group of 2..SMALL_SEG items whose head lies in this tile takes its
+// rank by (key, payload) among the group's items and stores itself at the group's head + rank when
+// that differs from where it is.  A group's head
 // lists the group when it is longer than SMALL_SEG.  Singletons and groups already in order cost a
 // key load each and store nothing.  A group belongs to the tile that holds its head, also where it
 // runs into the next tile (into the halo, taken by the first HALO threads), so two blocks never
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 6) k_sort_finish(K* __restrict__ 
     constexpr int HALO = SMALL_SEG + 1;
     constexpr uint32_t SPAN = FIN_TILE + HALO;
     __shared__ K tk[1 + SPAN];            // tk[1 + j] = key at base + j; tk[0] = key at base - 1
-    __shared__ uint32_t tv[SPAN];         // payloads of the items in groups this tile sorts
+    __shared__ uint32_t tv[SPAN];
     const uint64_t pm = plan->pmask;
     const uint64_t base = (uint64_t)blockIdx.x * FIN_TILE;
     const uint32_t lim = n - base < (uint64_t)SPAN ? (uint32_t)(n - base) : SPAN;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 6) k_sort_finish(K* __restrict__ 
     }
     if (threadIdx.x == 0 && base > 0) tk[0] = keys[base - 1];
     __syncthreads();
-    // pass 1: group bounds; the items of groups sorted here bring their payloads
+    // pass 1: group bounds
     uint32_t info[FIN_ITEMS + 1];   // 0, or head | L << 16 of the item's group
 #pragma unroll
     for (int r = 0; r <= FIN_ITEMS; r++) {
