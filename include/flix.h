@@ -84,6 +84,15 @@ typedef struct {
                                  the batch touched merges underfull neighbours (flix_merge_underfull).
                                  0 (default): off */
     uint32_t reserved[3];
+    /* Optional device allocator for every device buffer the handle owns (node pool, bucket arrays,
+     * scratch, state words), e.g. a framework's caching allocator: dev_alloc(bytes, alloc_ctx)
+     * returns memory of the current device aligned to at least 256 bytes, or NULL when it cannot;
+     * dev_free(ptr, alloc_ctx) takes back a pointer dev_alloc returned.  The library synchronises
+     * the device before every dev_free, so no kernel still uses the memory.  Both NULL (default):
+     * cudaMalloc and cudaFree. */
+    void* (*dev_alloc)(size_t bytes, void* alloc_ctx);
+    void (*dev_free)(void* ptr, void* alloc_ctx);
+    void* alloc_ctx;
 } flix_config;
 
 /* Batch-sort variants (same stable order, different speed): one-sweep passes with decoupled
@@ -108,7 +117,8 @@ typedef struct {
 void flix_config_default(flix_config* cfg, flix_keytype kt);
 
 /* Create an empty index (one bucket with one empty node) on the current CUDA device.
- * Returns FLIX_ETYPE for an unsupported key type or node size, FLIX_ECUDA if allocation fails. */
+ * Returns FLIX_ETYPE for an unsupported key type or node size, FLIX_EINVAL if only one of
+ * dev_alloc and dev_free is given, FLIX_ECUDA if allocation fails. */
 int flix_create(const flix_config* cfg, flix_t* out);
 
 /* Free every device and host resource of h (synchronises the device). */

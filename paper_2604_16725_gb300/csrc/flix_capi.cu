@@ -22,18 +22,35 @@ const char* kKernelNames[K_NUM] = {
     "update_heavy",
 };
 
+cudaError_t dev_malloc(const DevAlloc& da, void** p, size_t bytes)
+{
+    if (!da.alloc) return cudaMalloc(p, bytes);
+    *p = da.alloc(bytes, da.ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void dev_free(const DevAlloc& da, void* p)
+{
+    if (!p) return;
+    if (!da.free) {
+        cudaFree(p);   // synchronises the device
+        return;
+    }
+    cudaDeviceSynchronize();
+    da.free(p, da.ctx);
+}
+
 cudaError_t Arena::ensure(size_t bytes)
 {
     if (bytes <= cap) return cudaSuccess;
     size_t want = std::max(bytes, cap + cap / 2);
     want = (want + (1 << 20) - 1) & ~size_t((1 << 20) - 1);
     if (base) {
-        cudaError_t e = cudaFree(base);  // synchronises the device: no call still uses the arena
+        dev_free(da, base);  // synchronises the device: no call still uses the arena
         base = nullptr;
         cap = 0;
-        if (e) return e;
     }
-    cudaError_t e = cudaMalloc(&base, want);
+    cudaError_t e = dev_malloc(da, reinterpret_cast<void**>(&base), want);
     if (e) { base = nullptr; return e; }
     cap = want;
     used = 0;
@@ -42,7 +59,7 @@ cudaError_t Arena::ensure(size_t bytes)
 
 void Arena::release()
 {
-    if (base) cudaFree(base);
+    dev_free(da, base);
     base = nullptr;
     cap = used = 0;
 }
@@ -147,12 +164,12 @@ int check_err(flix_index* h, cudaStream_t st)
 // The second key/value node array of the one-pass restructure (sized like the pool).
 void pool_free_second(flix_index* h)
 {
-    if (h->keys2) cudaFree(h->keys2);
-    if (h->vals2) cudaFree(h->vals2);
+    dev_free(h->da, h->keys2);
+    dev_free(h->da, h->vals2);
     h->keys2 = h->vals2 = nullptr;
     h->cap2 = 0;
-    if (h->mkba2) cudaFree(h->mkba2);
-    if (h->head2) cudaFree(h->head2);
+    dev_free(h->da, h->mkba2);
+    dev_free(h->da, h->head2);
     h->mkba2 = nullptr;
     h->head2 = nullptr;
     h->capb2 = 0;
@@ -161,8 +178,7 @@ void pool_free_second(flix_index* h)
 void pool_free(flix_index* h)
 {
     void* ptrs[] = {h->keys, h->vals, h->size, h->bound, h->next, h->tnode, h->mkba, h->head, h->free_ids};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dev_free(h->da, p);
     h->keys = h->vals = h->bound = h->mkba = nullptr;
     h->size = h->next = h->tnode = h->head = h->free_ids = nullptr;
     h->cap = 0;
@@ -178,24 +194,24 @@ cudaError_t pool_alloc_arrays(flix_index* h, uint64_t cap, PoolArrays& a)
 {
     memset(&a, 0, sizeof(a));
     const size_t ks = h->ks;
+    const DevAlloc& da = h->da;
     cudaError_t e;
-    if ((e = cudaMalloc(&a.keys, cap * h->NS * ks))) return e;
-    if ((e = cudaMalloc(&a.vals, cap * h->NS * ks))) return e;
-    if ((e = cudaMalloc(&a.bound, cap * ks))) return e;
-    if ((e = cudaMalloc(&a.mkba, cap * ks))) return e;
-    if ((e = cudaMalloc(&a.size, cap * 4))) return e;
-    if ((e = cudaMalloc(&a.next, cap * 4))) return e;
-    if ((e = cudaMalloc(&a.tnode, cap * 4))) return e;
-    if ((e = cudaMalloc(&a.head, cap * 4))) return e;
-    if ((e = cudaMalloc(&a.free_ids, cap * 4))) return e;
+    if ((e = dev_malloc(da, &a.keys, cap * h->NS * ks))) return e;
+    if ((e = dev_malloc(da, &a.vals, cap * h->NS * ks))) return e;
+    if ((e = dev_malloc(da, &a.bound, cap * ks))) return e;
+    if ((e = dev_malloc(da, &a.mkba, cap * ks))) return e;
+    if ((e = dev_malloc(da, reinterpret_cast<void**>(&a.size), cap * 4))) return e;
+    if ((e = dev_malloc(da, reinterpret_cast<void**>(&a.next), cap * 4))) return e;
+    if ((e = dev_malloc(da, reinterpret_cast<void**>(&a.tnode), cap * 4))) return e;
+    if ((e = dev_malloc(da, reinterpret_cast<void**>(&a.head), cap * 4))) return e;
+    if ((e = dev_malloc(da, reinterpret_cast<void**>(&a.free_ids), cap * 4))) return e;
     return cudaSuccess;
 }
 
-void pool_free_arrays(PoolArrays& a)
+void pool_free_arrays(flix_index* h, PoolArrays& a)
 {
     void* ptrs[] = {a.keys, a.vals, a.bound, a.mkba, a.size, a.next, a.tnode, a.head, a.free_ids};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dev_free(h->da, p);
 }
 
 void pool_adopt(flix_index* h, const PoolArrays& a, uint64_t cap)
@@ -212,7 +228,7 @@ int pool_reset(flix_index* h, uint64_t cap)
     pool_free(h);
     PoolArrays a;
     cudaError_t e = pool_alloc_arrays(h, cap, a);
-    if (e) { pool_free_arrays(a); return fail(h, e); }
+    if (e) { pool_free_arrays(h, a); return fail(h, e); }
     pool_adopt(h, a, cap);
     return FLIX_OK;
 }
@@ -224,7 +240,7 @@ int pool_grow(flix_index* h, cudaStream_t st, uint64_t new_cap)
     if (new_cap > 0xFFFFFFF0ull) return FLIX_ENOMEM;
     PoolArrays a;
     cudaError_t e = pool_alloc_arrays(h, new_cap, a);
-    if (e) { pool_free_arrays(a); cudaGetLastError(); return FLIX_ENOMEM; }
+    if (e) { pool_free_arrays(h, a); cudaGetLastError(); return FLIX_ENOMEM; }
     const uint64_t c = h->cap;
     const size_t ks = h->ks;
     CK(cudaMemcpyAsync(a.keys, h->keys, c * h->NS * ks, cudaMemcpyDeviceToDevice, st));
@@ -494,8 +510,8 @@ int ensure_second(flix_index* h)
 {
     if (h->cap2 == h->cap) return FLIX_OK;
     pool_free_second(h);
-    CK(cudaMalloc(&h->keys2, h->cap * h->NS * h->ks));
-    CK(cudaMalloc(&h->vals2, h->cap * h->NS * h->ks));
+    CK(dev_malloc(h->da, &h->keys2, h->cap * h->NS * h->ks));
+    CK(dev_malloc(h->da, &h->vals2, h->cap * h->NS * h->ks));
     h->cap2 = h->cap;
     return FLIX_OK;
 }
@@ -505,13 +521,13 @@ int ensure_second(flix_index* h)
 int ensure_second_buckets(flix_index* h)
 {
     if (h->capb2 == h->cap) return FLIX_OK;
-    if (h->mkba2) cudaFree(h->mkba2);
-    if (h->head2) cudaFree(h->head2);
+    dev_free(h->da, h->mkba2);
+    dev_free(h->da, h->head2);
     h->mkba2 = nullptr;
     h->head2 = nullptr;
     h->capb2 = 0;
-    CK(cudaMalloc(&h->mkba2, h->cap * h->ks));
-    CK(cudaMalloc(reinterpret_cast<void**>(&h->head2), h->cap * 4));
+    CK(dev_malloc(h->da, &h->mkba2, h->cap * h->ks));
+    CK(dev_malloc(h->da, reinterpret_cast<void**>(&h->head2), h->cap * 4));
     h->capb2 = h->cap;
     return FLIX_OK;
 }
@@ -878,6 +894,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     if (cfg->fill_pct == 0 || cfg->fill_pct > 100) return FLIX_EINVAL;
     if (cfg->sort_digit_bits != 0 && cfg->sort_digit_bits != 8) return FLIX_ENOTIMPL;
     if (cfg->sort_variant > FLIX_SORT_REDUCE_SCAN) return FLIX_EINVAL;
+    if (!cfg->dev_alloc != !cfg->dev_free) return FLIX_EINVAL;   // both or neither
     preload_kernels();
     flix_index* h = new flix_index();
     h->cfg = *cfg;
@@ -887,9 +904,14 @@ int flix_create(const flix_config* cfg, flix_t* out)
     h->p = std::max<uint32_t>(1, (uint32_t)(((uint64_t)h->NS * cfg->fill_pct) / 100));
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+    h->da.alloc = cfg->dev_alloc;
+    h->da.free = cfg->dev_free;
+    h->da.ctx = cfg->alloc_ctx;
+    h->arena.da = h->da;
     cudaError_t e;
-    if ((e = cudaMalloc(&h->err, 64)) || (e = cudaMemset(h->err, 0, 64)) ||
-        (e = cudaMalloc(&h->dstate, sizeof(DevState))) || (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
+    if ((e = dev_malloc(h->da, reinterpret_cast<void**>(&h->err), 64)) || (e = cudaMemset(h->err, 0, 64)) ||
+        (e = dev_malloc(h->da, reinterpret_cast<void**>(&h->dstate), sizeof(DevState))) ||
+        (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
         (e = cudaHostAlloc(&h->hpin, 64 * sizeof(uint64_t), cudaHostAllocMapped)) ||
         (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->hpin_dev), h->hpin, 0))) {
         int r = fail(h, e);
@@ -913,8 +935,8 @@ int flix_destroy(flix_t h)
     cudaDeviceSynchronize();
     pool_free(h);
     h->arena.release();
-    if (h->err) cudaFree(h->err);
-    if (h->dstate) cudaFree(h->dstate);
+    dev_free(h->da, h->err);
+    dev_free(h->da, h->dstate);
     if (h->hpin) cudaFreeHost(h->hpin);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;

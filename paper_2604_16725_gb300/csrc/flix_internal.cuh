@@ -55,8 +55,18 @@ enum KernelId {
     K_NUM
 };
 
+// Device allocations of a handle: the caller's allocator (flix_config) or cudaMalloc/cudaFree.
+struct DevAlloc {
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*free)(void*, void*) = nullptr;
+    void* ctx = nullptr;
+};
+cudaError_t dev_malloc(const DevAlloc& da, void** p, size_t bytes);
+void dev_free(const DevAlloc& da, void* p);   // synchronises the device first
+
 // Bump allocator over one device buffer, reset at the start of every call.
 struct Arena {
+    DevAlloc da;
     char* base = nullptr;
     size_t cap = 0;
     size_t used = 0;
@@ -122,6 +132,7 @@ struct flix_index {
     uint64_t free_top = 0;  // number of ids on the free stack (host mirror of the device state)
     int device = 0;
     int nsm = 148;      // SMs of the device
+    flix::DevAlloc da;  // device allocator
 
     // node pool and buckets (device)
     void* keys = nullptr;

@@ -33,7 +33,27 @@ class Config(ctypes.Structure):
                 ("grow", ctypes.c_uint32), ("pool_nodes", ctypes.c_uint64), ("sort_digit_bits", ctypes.c_uint32),
                 ("sort_variant", ctypes.c_uint32), ("restructure_in_one_pass", ctypes.c_uint32),
                 ("split_chains_over", ctypes.c_uint32), ("merge_underfull", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("reserved", ctypes.c_uint32 * 3), ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _torch_allocator(device):
+    """Device allocator callbacks backed by PyTorch's caching allocator (the library synchronises
+    the device before it frees)."""
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, device)
+        except RuntimeError:   # out of memory: the library reports FLIX_ECUDA / FLIX_ENOMEM
+            return None
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _ALLOC_FN(alloc), _FREE_FN(free)
 
 
 class Stats(ctypes.Structure):
@@ -120,7 +140,9 @@ class Index:
     def __init__(self, key_bits: int = 64, node_size: int | None = None, fill_pct: int = 50,
                  pool_nodes: int = 0, grow: bool = True, device=None, sort_variant: int = 0,
                  restructure_in_one_pass: bool = True, split_chains_over: int = 0,
-                 merge_underfull: bool = False):
+                 merge_underfull: bool = False, allocator: str | None = None):
+        """allocator: None (cudaMalloc) or "torch" (every device buffer of the index comes from
+        PyTorch's caching allocator and counts in torch.cuda.memory_allocated)."""
         if not torch.cuda.is_available():
             raise RuntimeError("FliX needs a CUDA device; none is available")
         L = load()
@@ -139,6 +161,13 @@ class Index:
         cfg.restructure_in_one_pass = 1 if restructure_in_one_pass else 0
         cfg.split_chains_over = split_chains_over
         cfg.merge_underfull = 1 if merge_underfull else 0
+        self._alloc_cbs = None
+        if allocator == "torch":
+            self._alloc_cbs = _torch_allocator(self.device)   # kept alive as long as the index
+            cfg.dev_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
+            cfg.dev_free = ctypes.cast(self._alloc_cbs[1], ctypes.c_void_p)
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         self.node_size = cfg.node_size
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

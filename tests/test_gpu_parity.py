@@ -467,3 +467,39 @@ def test_heavy_nodes_across_chunks(fx, kw):
     compare_layout(idx, md)
     compare_contents(idx, mp, kw)
     idx.close()
+
+
+def test_torch_caching_allocator(fx):
+    """Every device buffer of the index comes from PyTorch's caching allocator: it shows in
+    torch.cuda.memory_allocated, survives pool growth, the restructure's and the split's second
+    arrays and mixed batches (results against the oracle), and goes back on close."""
+    rng = np.random.default_rng(77)
+    kw, NS = 64, 16
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    load = np.unique(rng.integers(0, 1 << 40, 5000, dtype=np.uint64))
+    vals = load * np.uint64(3)
+    idx = fx.Index(key_bits=kw, node_size=NS, pool_nodes=700, allocator="torch")
+    idx.bulk_load(load, vals)
+    assert torch.cuda.memory_allocated() > before
+    mp, md = oracle_pair(kw, NS, 50, load, vals)
+    for b in range(6):
+        n = 4000
+        keys = np.concatenate([rng.integers(0, 1 << 40, n // 2, dtype=np.uint64),
+                               rng.integers(1 << 30, (1 << 30) + 100000, n // 2, dtype=np.uint64)])
+        ops = rng.choice([W.OP_LOOKUP, W.OP_SUCC, W.OP_PRED, W.OP_INSERT, W.OP_INSERT, W.OP_DELETE], n).astype(np.uint8)
+        aux = rng.integers(1, 1 << 30, n).astype(np.uint64)
+        apply_both(idx, mp, md, ops, keys, aux, kw)
+        compare_layout(idx, md)
+        if b == 2:
+            idx.restructure()
+            md.restructure()
+            compare_layout(idx, md)
+        if b == 4:
+            assert idx.split_chains(2) == md.split_chains(2)
+            compare_layout(idx, md)
+    assert idx.stats()["pool_nodes"] > 700
+    compare_contents(idx, mp, kw)
+    idx.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
