@@ -454,7 +454,12 @@ def main():
             "outside_step": {"predecessor": {"mops": (1 << LOG_Q) / (statistics.median(pred_ms) * 1e-3) / 1e6,
                                              "ms_p50": statistics.median(pred_ms), "queries": 1 << LOG_Q}},
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "roofline": roofline, "apply_roofline": apply_roofline, "gpu_launches": launches,
+            "roofline": roofline, "apply_roofline": apply_roofline,
+            # every kernel's CUDA-event time per step (profiled pass): apply-only times are the
+            # non-sort entries (read_point, read_unsort, range_*, update_*, gather, ...)
+            "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 4)
+                                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+            "gpu_launches": launches,
             "clocks": clocks}
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()  # noqa: E731
