@@ -35,6 +35,13 @@
  *     unlinked unless the whole chain emptied, in which case the chain's first node stays as an empty
  *     node; when the chain's last node leaves, its maxKey (= maxBucket) passes to the new last node.
  *
+ *     Two structural operations the paper proposes without fixing them (off unless asked for):
+ *     the elastic split of a bucket with a long chain (Sec. 3.4), read here as one bucket per node
+ *     of the chain with the node's maxKey as maxBucket, and the merge of underfull nodes during
+ *     deletion (Sec. 5.4.1), read here as folding a chain's next node into the current one while
+ *     both hold at most NS/2 pairs.  A policy runs both after every update batch on the buckets
+ *     the batch touched (merge first, then split).
+ *
  * Keys and values are held as uint64 for both key widths kw in {32, 64}; KEY_MAX = 2^kw - 1 is not a
  * storable key (it is the last bucket's maxBucket and the successor "none" key) and VAL_NONE is
  * the all-ones value of the same width.
