@@ -40,3 +40,39 @@ def test_strerror_without_gpu():
     L = fx.load()
     assert L.flix_strerror(0) == b"ok"
     assert b"KEY_MAX" in L.flix_strerror(-1)
+
+
+def test_config_defaults_and_create_validation_without_gpu():
+    """flix_config_default and every argument check of flix_create run on the host before any CUDA
+    call: bad configurations are rejected with the documented codes and leave *out NULL."""
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.flix import Config
+    L = fx.load()
+    cfg = Config()
+    L.flix_config_default(ctypes.byref(cfg), 1)            # FLIX_KEY_U64
+    assert (cfg.key_type, cfg.node_size, cfg.fill_pct, cfg.grow) == (1, 64, 50, 1)
+    assert cfg.restructure_in_one_pass == 1 and cfg.split_chains_over == 0 and cfg.merge_underfull == 0
+    assert not cfg.dev_alloc and not cfg.dev_free
+    L.flix_config_default(ctypes.byref(cfg), 0)            # FLIX_KEY_U32
+    assert cfg.node_size == 32
+    assert L.flix_create(None, None) == -1                  # FLIX_EINVAL
+
+    def rejected(**fields):
+        c = Config()
+        L.flix_config_default(ctypes.byref(c), 1)
+        for k, v in fields.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p(1234)
+        code = L.flix_create(ctypes.byref(c), ctypes.byref(h))
+        assert h.value is None
+        return code
+
+    assert rejected(key_type=7) == -4                       # FLIX_ETYPE
+    assert rejected(node_size=3) == -4
+    assert rejected(node_size=256) == -4
+    assert rejected(fill_pct=0) == -1
+    assert rejected(fill_pct=101) == -1
+    assert rejected(sort_digit_bits=11) == -7               # FLIX_ENOTIMPL
+    assert rejected(sort_variant=9) == -1
+    assert rejected(dev_alloc=1) == -1                      # an allocator without its free
+    assert rejected(dev_free=1) == -1
