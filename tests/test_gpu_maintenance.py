@@ -158,3 +158,32 @@ def test_split_with_pool_growth(fx):
     assert idx.stats()["pool_nodes"] > 600
     compare_contents(idx, mp, kw)
     idx.close()
+
+
+@pytest.mark.parametrize("kw", [32, 64])
+def test_policy_with_heavy_nodes(fx, kw):
+    """Batches with more than 2048 updates to one node (merged by all blocks) while the merge and
+    the split run after every batch: the maintenance sees the heavy node's final pieces."""
+    rng = np.random.default_rng(90 + kw)
+    dt = np.uint32 if kw == 32 else np.uint64
+    load = np.unique(rng.integers(0, 1 << 24, 2000)).astype(np.uint64)
+    idx, mp, md = _pair(fx, kw, 16, load, split=4, merge=True)
+    hi = np.arange((1 << 25) + 1, (1 << 25) + 1 + 3 * 15000, 3, dtype=np.uint64)    # above every key
+    for b in range(3):
+        # 5000 keys above everything stored: the last bucket's node takes them all (heavy)
+        keys = np.concatenate([hi[b * 5000:(b + 1) * 5000], load[rng.integers(0, load.size, 300)]])
+        ops = np.concatenate([np.full(keys.size - 300, W.OP_INSERT, np.uint8),
+                              np.full(300, W.OP_DELETE, np.uint8)])
+        aux = rng.integers(1, 1 << 30, keys.size).astype(np.uint64)
+        p = rng.permutation(keys.size)
+        apply_both(idx, mp, md, ops[p], keys[p].astype(dt), aux[p].astype(dt), kw)
+        compare_layout(idx, md)
+        assert idx.stats()["max_chain"] <= 4
+    # delete most of the inserted keys in one batch: heavy deletes, then merges
+    gone = hi[rng.random(hi.size) < 0.9]
+    idx.delete(gone.astype(dt))
+    mp.update(np.full(gone.size, W.OP_DELETE, np.uint8), gone)
+    md.update(np.full(gone.size, W.OP_DELETE, np.uint8), gone)
+    compare_layout(idx, md)
+    compare_contents(idx, mp, kw)
+    idx.close()
