@@ -88,8 +88,22 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
     const uint64_t a0 = ca[blockIdx.x], a1 = ca[blockIdx.x + 1];
     const uint64_t b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0);
-    for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS) sA[t] = mkba[a0 + t];
-    for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS) sB[t] = skeys[b0 + t];
+    {
+        // every load of the tile is issued before the first store to shared memory
+        K ra[PT_ITEMS], rb[PT_ITEMS];
+#pragma unroll
+        for (int r = 0; r < PT_ITEMS; r++) {
+            const uint32_t t = r * PT_THREADS + threadIdx.x;
+            if (t < la) ra[r] = mkba[a0 + t];
+            if (t < lb) rb[r] = skeys[b0 + t];
+        }
+#pragma unroll
+        for (int r = 0; r < PT_ITEMS; r++) {
+            const uint32_t t = r * PT_THREADS + threadIdx.x;
+            if (t < la) sA[t] = ra[r];
+            if (t < lb) sB[t] = rb[r];
+        }
+    }
     __syncthreads();
     if (bk)
         for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS)
