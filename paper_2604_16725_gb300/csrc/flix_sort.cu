@@ -85,25 +85,6 @@ __device__ __forceinline__ uint32_t digit_of(K k, int shift) { return static_cas
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *reinterpret_cast<const volatile uint32_t*>(p); }
 __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) { *reinterpret_cast<volatile uint32_t*>(p) = v; }
 
-// Digit histograms of every pass from one read of the keys.
-template <class K>
-__global__ void __launch_bounds__(256) k_hist_all(const K* __restrict__ keys, uint64_t n, uint32_t* __restrict__ hist)
-{
-    constexpr int P = sizeof(K);
-    __shared__ uint32_t sh[P * RADIX];
-    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        K k = keys[i];
-#pragma unroll
-        for (int p = 0; p < P; p++) atomicAdd(&sh[p * RADIX + digit_of(k, 8 * p)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
-}
-
 // Stable rank of each lane's item among the warp's lanes with the same digit: the peer mask is
 // built from NB ballots, one per digit bit (NB = 9 when the digit value RADIX marks a lane
 // without an item).
@@ -428,6 +409,36 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
         for (int q = 0; q < use; q++) pl.shift[q] = 8 * nc[use - 1 - q];
     }
     *plan = pl;
+}
+
+// Digit histograms of every pass from one read of the keys.
+template <class K>
+__global__ void __launch_bounds__(256) k_hist_all(const K* __restrict__ keys, uint64_t n, uint32_t* __restrict__ hist)
+{
+    constexpr int P = sizeof(K);
+    __shared__ uint32_t sh[P * RADIX];
+    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four keys in flight per thread: their loads are issued before any of the counts
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        K k[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) k[u] = keys[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int p = 0; p < P; p++) atomicAdd(&sh[p * RADIX + digit_of(k[u], 8 * p)], 1u);
+    }
+    for (; i < n; i += stride) {
+        const K k = keys[i];
+#pragma unroll
+        for (int p = 0; p < P; p++) atomicAdd(&sh[p * RADIX + digit_of(k, 8 * p)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 // ---- finishing the groups of equal prefix ----------------------------------------------------------
