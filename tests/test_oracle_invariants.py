@@ -116,11 +116,57 @@ def test_successor_predecessor_and_range_vs_linear_scan():
                 assert int(rp["keys"][i]) == km and int(rp["vals"][i]) == km and rp["found"][i] == 0
         # the numpy sampled helpers agree with the map (they serve the full-size sampled checks)
         sk, sv, sf = oracle.sorted_successor(keys, vals, q, kw)
-        assert np.array_equal(sk, r["keys"]) and np.array_equal(sv, r["vals"])
+        assert np.array_equal(sk, r["keys"]) and np.array_equal(sv, r["vals"]) and np.array_equal(sf, r["found"])
         pk, pv, pf = oracle.sorted_predecessor(keys, vals, q, kw)
         assert np.array_equal(pk, rp["keys"]) and np.array_equal(pv, rp["vals"]) and np.array_equal(pf, rp["found"])
         cnt = oracle.sorted_range_counts(keys, q, hi)
         assert np.array_equal(cnt, np.diff(rr["range_off"]))
+
+
+def _scan_lookup(allk, allv, x, km):
+    """Lookup by a linear scan of the stored pairs: the definition, written out."""
+    for k, v in zip(allk, allv):
+        if k == x:
+            return v, 1
+    return km, 0
+
+
+@pytest.mark.parametrize("kw", [32, 64])
+def test_sorted_lookup_vs_map_and_linear_scan(kw):
+    # sorted_lookup checks the full-size sampled and the every-output GPU lookups; here it is
+    # compared with the ordered map and with a linear scan: hits, misses, the keys next to the
+    # reserved KEY_MAX, the smallest key, and an empty key set
+    km = (1 << kw) - 1
+    rng = np.random.default_rng(11 + kw)
+    keys = np.unique(np.concatenate([rng.integers(0, 3000, 300).astype(np.uint64),
+                                     np.array([0, km - 1, km - 2], np.uint64)]))
+    vals = (keys * np.uint64(7) + np.uint64(3)) & np.uint64(km - 1)
+    q = np.concatenate([keys[rng.integers(0, keys.size, 200)], rng.integers(0, 3100, 200).astype(np.uint64),
+                        np.array([0, 1, km - 1, km - 2, km - 3, km], np.uint64)])
+    allk, allv = keys.tolist(), vals.tolist()
+    for sk, sv in ((keys, vals), (np.zeros(0, np.uint64), np.zeros(0, np.uint64))):
+        lv, lf = oracle.sorted_lookup(sk, sv, q, kw)
+        mp = oracle.Map(kw)
+        mp.bulk_load(sk, sv)
+        r = mp.read(np.full(q.size, W.OP_LOOKUP, np.uint8), q)
+        assert np.array_equal(lv, r["vals"]) and np.array_equal(lf, r["found"])
+        for i in range(q.size):
+            v, f = _scan_lookup(sk.tolist(), sv.tolist(), int(q[i]), km)
+            assert int(lv[i]) == v and int(lf[i]) == f
+        if sk.size:
+            assert int(lf.sum()) >= 200                       # every drawn stored key is a hit
+            assert int(lv[-1]) == km and lf[-1] == 0          # KEY_MAX itself is never stored
+            assert int(lv[-4]) == allv[allk.index(km - 1)] and lf[-4] == 1
+        else:
+            assert not lf.any() and (lv == np.uint64(km)).all()
+    # the successor and predecessor helpers on an empty set and next to KEY_MAX
+    for fn in (oracle.sorted_successor, oracle.sorted_predecessor):
+        ek, ev, ef = fn(np.zeros(0, np.uint64), np.zeros(0, np.uint64), q, kw)
+        assert not ef.any() and (ek == np.uint64(km)).all() and (ev == np.uint64(km)).all()
+    sk_, sv_, sf_ = oracle.sorted_successor(keys, vals, np.array([km - 1, km], np.uint64), kw)
+    assert sk_.tolist() == [km - 1, km] and sf_.tolist() == [1, 0]
+    pk_, pv_, pf_ = oracle.sorted_predecessor(keys, vals, np.array([km, 0], np.uint64), kw)
+    assert pk_.tolist() == [km - 1, 0] and pf_.tolist() == [1, 1]
 
 
 def test_generators_are_deterministic_and_distinct():

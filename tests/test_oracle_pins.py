@@ -168,17 +168,40 @@ def test_mixed_batch_snapshot_reads():
 
 
 def test_model_keeps_first_node_when_bucket_empties():
+    # Worked by hand from Sec. 3.2 (build), the split rule and Sec. 4.4 (an emptied node leaves the
+    # chain, unless the bucket would have no node left).  NS 4, p 2: buckets [10 20] [30 40] [50 60],
+    # maxBucket 20, 40, KEY_MAX; nodes 0, 1, 2.
+    km = oracle.key_max(32)
     m = oracle.Model(32, 4, 50)
-    m.bulk_load([1, 2, 3, 4, 5, 6], [1, 2, 3, 4, 5, 6])   # buckets [1,2] [3,4] [5,6]
-    # grow bucket 1 into a chain of two nodes, then delete everything in it
-    m.update([oracle.OP_INSERT] * 0, [], [])
+    m.bulk_load([10, 20, 30, 40, 50, 60], [1, 2, 3, 4, 5, 6])
+    assert m.stats()["nodes"] == 3
+    # bucket 1 takes 31..35: merged run 30 31 32 33 34 35 40 (t = 7 > 4) becomes floor(7/2) = 3
+    # pieces of 2, 2 and 3 keys, maxKeys 31, 33 and the old 40; two nodes come from the pool
+    m.update([oracle.OP_INSERT] * 5, [31, 32, 33, 34, 35], [31, 32, 33, 34, 35])
     d0 = m.dump()
-    assert d0["chain_len"].tolist() == [1, 1, 1]
-    m.update([oracle.OP_DELETE] * 2, [3, 4])
+    assert d0["chain_len"].tolist() == [1, 3, 1]
+    assert d0["node_size"].tolist() == [2, 2, 2, 3, 2]
+    assert d0["node_bound"].tolist() == [20, 31, 33, 40, km]
+    assert m.stats()["nodes"] == 5
+    # every key of bucket 1 leaves: the chain's first node stays, empty, as the bucket's only node,
+    # with maxKey = maxBucket 40; the other two go back to the free stack
+    m.update([oracle.OP_DELETE] * 7, [30, 31, 32, 33, 34, 35, 40])
     d = m.dump()
     assert d["chain_len"].tolist() == [1, 1, 1]
     assert d["node_size"].tolist() == [2, 0, 2]
-    assert d["node_bound"].tolist()[1] == 4           # the empty node keeps maxBucket
+    assert d["node_bound"].tolist() == [20, 40, km]
+    assert d["mkba"].tolist() == [20, 40, km]
+    assert m.stats()["nodes"] == 3 and m.stats()["max_chain"] == 1
+    assert m.check() == 0
+    # the emptied bucket still routes its range: successor of 25 is in bucket 2, an insert lands in
+    # the kept node, and the freed nodes are reused before the pool grows
+    r = m.read([oracle.OP_SUCC, oracle.OP_LOOKUP], [25, 40])
+    assert r["keys"].tolist()[0] == 50 and r["found"].tolist() == [1, 0]
+    m.update([oracle.OP_INSERT] * 3, [36, 37, 38], [36, 37, 38])
+    d1 = m.dump()
+    assert d1["chain_len"].tolist() == [1, 1, 1] and d1["node_size"].tolist() == [2, 3, 2]
+    m.update([oracle.OP_INSERT] * 3, [11, 12, 13], [11, 12, 13])   # 10 11 12 13 20: pieces 2 and 3
+    assert m.dump()["chain_len"].tolist() == [2, 1, 1] and m.stats()["nodes"] == 4
     assert m.check() == 0
     # the last bucket: its chain's last node leaves, maxBucket passes to the new last node
     m2 = oracle.Model(32, 4, 100)
