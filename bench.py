@@ -724,9 +724,11 @@ def bench_xy(args):
     Rounds: build 2^24 uniform keys; 8 insert rounds of 3 * 2^21 keys (300% growth), Y = 90% of each
     round inside a hot interval covering X of the key range, X from 90% (uniform) down to 2%; after
     every insert round a batch of 2^25 lookups of stored keys (the skew experiment of Sec. 6.4); then
-    8 delete rounds removing the inserted keys.  Restructure accounting (Sec. 6.6, Tab. 2): builds
-    of 1M, 33M and 100M keys, 8 insert rounds to 4x the build at X25Y90 and X90Y90, 8 delete rounds,
-    then one restructure: nodes before and after, and the share recovered.  Every call is timed with
+    8 delete rounds removing the inserted keys.  Restructure accounting (Sec. 6.6, Tab. 4): each
+    printed row (builds of 1M, 33M and 100M keys, 8 insert rounds to the printed final size at
+    X25Y90 and X90Y90), 8 delete rounds removing the share of the inserted keys that the row
+    implies, then one restructure: nodes before and after, the share recovered, and the row's own
+    figures beside them.  Every call is timed with
     CUDA events on its stream, inputs resident on the device."""
     import torch
     import paper_2604_16725_gb300 as fx
@@ -786,38 +788,43 @@ def bench_xy(args):
         torch.cuda.empty_cache()
 
     table = []
-    for b in (1 << 20, 1 << 25, 100_000_000):
+    for name, b, final, p_rec, p_pct in W.TAB4:
         if b > args.xy_max_build:
             continue
-        for X in (0.25, 0.9):
-            w = W.xy_rounds(X, 0.9, b, 3 * b, 8, seed=6100, kw=64)
-            idx = fx.Index(key_bits=64, node_size=32)
-            idx.bulk_load(td(w["build_keys"]), td(w["build_vals"]), stream=st)
-            t_ins = t_del = 0.0
-            for k, v in w["insert"]:
-                kd, vd = td(k), td(v)
-                t_ins += timed(lambda: idx.insert(kd, vd, stream=st))
-                del kd, vd
-            s_ins = idx.stats(stream=st)
-            for k in w["delete"]:
-                kd = td(k)
-                t_del += timed(lambda: idx.delete(kd, stream=st))
-                del kd
-            s_del = idx.stats(stream=st)
-            t_res = timed(lambda: idx.restructure(stream=st))
-            s_res = idx.stats(stream=st)
-            row = {"workload": "X%dY90" % round(100 * X), "build": b, "final": s_ins["live_keys"],
-                   "nodes_after_inserts": s_ins["nodes_used"], "max_chain": s_ins["max_chain"],
-                   "nodes_before_restructure": s_del["nodes_used"], "nodes_after_restructure": s_res["nodes_used"],
-                   "nodes_recovered": s_del["nodes_used"] - s_res["nodes_used"],
-                   "recovered_pct": 100.0 * (s_del["nodes_used"] - s_res["nodes_used"]) / max(s_del["nodes_used"], 1),
-                   "restructure_ms": t_res, "insert_mops": 3 * b / (t_ins * 1e-3) / 1e6,
-                   "delete_mops": 3 * b / (t_del * 1e-3) / 1e6}
-            log("restructure accounting: %s" % row)
-            table.append(row)
-            idx.close()
-            del w
-            torch.cuda.empty_cache()
+        imp = W.tab4_implied((name, b, final, p_rec, p_pct))
+        X = 0.25 if name.startswith("X25") else 0.9
+        w = W.xy_rounds(X, 0.9, b, final - b, 8, seed=6100, kw=64, delete_share=imp["delete_share"])
+        idx = fx.Index(key_bits=64, node_size=32)
+        idx.bulk_load(td(w["build_keys"]), td(w["build_vals"]), stream=st)
+        t_ins = t_del = 0.0
+        for k, v in w["insert"]:
+            kd, vd = td(k), td(v)
+            t_ins += timed(lambda: idx.insert(kd, vd, stream=st))
+            del kd, vd
+        s_ins = idx.stats(stream=st)
+        for k in w["delete"]:
+            kd = td(k)
+            t_del += timed(lambda: idx.delete(kd, stream=st))
+            del kd
+        s_del = idx.stats(stream=st)
+        t_res = timed(lambda: idx.restructure(stream=st))
+        s_res = idx.stats(stream=st)
+        n_del = sum(k.size for k in w["delete"])
+        row = {"workload": name, "build": b, "final": s_ins["live_keys"], "delete_share": round(imp["delete_share"], 4),
+               "live_at_restructure": s_del["live_keys"],
+               "nodes_after_inserts": s_ins["nodes_used"], "max_chain": s_ins["max_chain"],
+               "nodes_before_restructure": s_del["nodes_used"], "nodes_after_restructure": s_res["nodes_used"],
+               "nodes_recovered": s_del["nodes_used"] - s_res["nodes_used"],
+               "recovered_pct": 100.0 * (s_del["nodes_used"] - s_res["nodes_used"]) / max(s_del["nodes_used"], 1),
+               "paper": {"nodes_recovered": p_rec, "recovered_pct": p_pct,
+                         "implied_nodes_before": round(imp["before"]), "implied_nodes_after": round(imp["after"])},
+               "restructure_ms": t_res, "insert_mops": (final - b) / (t_ins * 1e-3) / 1e6,
+               "delete_mops": n_del / (t_del * 1e-3) / 1e6}
+        log("restructure accounting: %s" % row)
+        table.append(row)
+        idx.close()
+        del w
+        torch.cuda.empty_cache()
 
     line = {"form": "xy", "metric": METRIC, "value": tot_ops / (tot_ms * 1e-3) / 1e6, "unit": "Mops/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",

@@ -160,3 +160,30 @@ def test_split_moves_no_pair():
         assert np.array_equal(before[f], after[f])
     assert md.check() == 0 and md.stats()["max_chain"] <= 3
     _reads_agree(mp, md, 64, rng)
+
+
+@pytest.mark.parametrize("row", [0, 3])
+def test_restructure_accounting_against_tab4(row):
+    """Tab. 4 (Sec. 6.6) at its 1M build (2^20 keys, node size 32, 8 insert rounds to 4M at X/Y =
+    25/90 or 90/90, 8 delete rounds, one restructure).  Reading "% recovered" as a share of the
+    nodes before the restructure, the table fixes the node count before it (about 188k for both
+    workloads) and, through the half-full cut, the live keys at the restructure; the delete rounds
+    remove the share of the inserted keys that this implies.  The model's node count before the
+    restructure comes from the split rule alone and must land near the table's; so must the nodes
+    and share it recovers."""
+    name, build, final, rec, pct = W.TAB4[row]
+    q = W.tab4_implied(W.TAB4[row])
+    X = 0.25 if name.startswith("X25") else 0.9
+    w = W.xy_rounds(X, 0.9, build, final - build, 8, seed=6100, kw=64, delete_share=q["delete_share"])
+    m = oracle.Model(64, 32, 50)
+    m.bulk_load(w["build_keys"], w["build_vals"])
+    for k, v in w["insert"]:
+        assert m.update(np.full(k.size, oracle.OP_INSERT, np.uint8), k, v) == 0
+    for k in w["delete"]:
+        assert m.update(np.full(k.size, oracle.OP_DELETE, np.uint8), k) == 0
+    before = m.stats()["nodes"]
+    got = m.restructure()
+    assert abs(before / q["before"] - 1) < 0.02
+    assert abs(got / rec - 1) < 0.03
+    assert abs(100.0 * got / before - pct) < 1.0
+    assert m.check(build_shape=True) == 0

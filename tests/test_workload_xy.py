@@ -41,3 +41,25 @@ def test_bijection_below_is_a_permutation():
     for size in (1, 2, 3, 1000, 4097):
         p = W.bijection_below(np.arange(size, dtype=np.uint64), size, 9)
         assert np.array_equal(np.sort(p), np.arange(size, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("share", [0.0, 0.3, 0.653])
+def test_xy_delete_share_is_a_subset_of_the_inserts(share):
+    w = W.xy_rounds(0.25, 0.9, 2000, 6001, 8, seed=5, kw=64, delete_share=share)
+    ins = np.concatenate([k for k, _ in w["insert"]])
+    d = np.concatenate(w["delete"])
+    assert len(w["delete"]) == 8 and d.size == int(round(share * ins.size))
+    assert np.unique(d).size == d.size and np.isin(d, ins).all()
+    sizes = [x.size for x in w["delete"]]
+    assert max(sizes) - min(sizes) <= 1
+
+
+def test_tab4_implied_quantities():
+    # the printed rows, read with "% recovered" = recovered / nodes before the restructure
+    for row in W.TAB4:
+        q = W.tab4_implied(row)
+        assert abs(q["before"] - q["after"] - row[3]) < 1e-6
+        assert 0.0 < q["delete_share"] < 1.0 and row[1] < q["live"] < row[2]
+    # the same build at both workloads leaves about the same node count before the restructure
+    b = {r[0] + str(r[1]): W.tab4_implied(r)["before"] for r in W.TAB4}
+    assert abs(b["X25Y90" + str(1 << 20)] / b["X90Y90" + str(1 << 20)] - 1) < 0.01

@@ -31,7 +31,7 @@ __all__ = [
     "key_max", "mix64", "mix32", "uniform01", "universe", "values_for", "zipf",
     "scramble30", "scramble_bits", "universe_at", "log_uniform_sizes", "permutation",
     "config1", "read_scale", "update_heavy", "mixed_stream", "serving_requests",
-    "bijection_below", "xy_rounds",
+    "bijection_below", "xy_rounds", "TAB4", "tab4_implied",
 ]
 
 
@@ -415,7 +415,7 @@ def bijection_below(c: np.ndarray, size: int, seed: int) -> np.ndarray:
 
 
 def xy_rounds(X: float, Y: float, build: int, inserts: int, rounds: int, seed: int = 6000,
-              kw: int = 64):
+              kw: int = 64, delete_share: float = 1.0):
     """Dense-range (X/Y) update workload: a hot interval covering the fraction X of the key range
     receives the fraction Y of every insert round; the rest of the round is spread uniformly over
     the remaining key range.  X = Y = 0.9 is the uniform case.
@@ -427,12 +427,14 @@ def xy_rounds(X: float, Y: float, build: int, inserts: int, rounds: int, seed: i
     of a bijection of [0, V - H) with the hot interval skipped.  Each round holds
     round(Y m) hot and m - round(Y m) cold keys (m = inserts / rounds, the last round takes the
     remainder), hot ones first: the keys are distinct and every batch is sorted, so their order
-    changes no result.  The delete rounds remove the keys of the insert rounds, round by round
-    (the structure returns to its build keys).
+    changes no result.  With delete_share = 1 the delete rounds remove the keys of the insert
+    rounds, round by round (the structure returns to its build keys); with delete_share < 1 they
+    remove round(delete_share * inserts) of the inserted keys, a seeded choice in seeded order, in
+    `rounds` batches of (nearly) equal size.
 
     Returns dict(build_keys, build_vals, insert=[(keys, vals)], delete=[keys], hot=(lo_key, hi_key)).
     """
-    assert 0.0 < X <= 1.0 and 0.0 <= Y <= 1.0 and kw in (32, 64)
+    assert 0.0 < X <= 1.0 and 0.0 <= Y <= 1.0 and kw in (32, 64) and 0.0 <= delete_share <= 1.0
     dt = _kdt(kw)
     V = (1 << (kw - 1)) - 1
     H = max(1, min(V - 1, int(X * V)))
@@ -455,5 +457,31 @@ def xy_rounds(X: float, Y: float, build: int, inserts: int, rounds: int, seed: i
         k = ((v << np.uint64(1)) | np.uint64(1)).astype(dt)
         ins.append((k, values_for(kw, k, salt=r + 1)))
         dels.append(k.copy())
+    if delete_share < 1.0:
+        allk = np.concatenate(dels) if dels else np.zeros(0, dt)
+        take = permutation(seed ^ 0x44, 5, allk.size)[:int(round(delete_share * allk.size))]
+        dels = [np.ascontiguousarray(d) for d in np.array_split(allk[take], rounds)]
     return dict(kw=kw, build_keys=bk, build_vals=values_for(kw, bk), insert=ins, delete=dels,
                 hot=(2 * h0, 2 * (h0 + H)))
+
+
+# Tab. 4 (Sec. 6.6): nodes recovered by one restructure after 8 insert rounds and 8 delete rounds,
+# node size 32.  (workload, build keys, final keys, nodes recovered, % recovered) as printed; "1M"
+# and "33M" are read as 2^20 and 2^25 (their final sizes, 4M and 134M, are 4x those), "100M" as
+# 10^8 with the printed final size 300M.
+TAB4 = (("X25Y90", 1 << 20, 4 << 20, 54623, 29), ("X25Y90", 1 << 25, 4 << 25, 1745428, 29),
+        ("X25Y90", 100_000_000, 300_000_000, 3928746, 28), ("X90Y90", 1 << 20, 4 << 20, 81307, 43),
+        ("X90Y90", 1 << 25, 4 << 25, 2603137, 43), ("X90Y90", 100_000_000, 300_000_000, 6130104, 46))
+
+
+def tab4_implied(row, half: int = 16):
+    """What one Tab. 4 row implies when "% recovered" is the share of the nodes before the
+    restructure: nodes before = recovered / share, nodes after = before - recovered, live keys at
+    the restructure = after * half (the restructure cuts half-full nodes), and the share of the
+    inserted keys the delete rounds removed = (final - live) / (final - build)."""
+    _, build, final, rec, pct = row
+    before = rec / (pct / 100.0)
+    after = before - rec
+    live = after * half
+    return dict(before=before, after=after, live=live, delete_share=(final - live) / (final - build))
+
