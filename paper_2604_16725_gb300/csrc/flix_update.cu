@@ -37,6 +37,7 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 template <class K>
 __global__ void k_validate(const uint8_t* __restrict__ ops, const K* __restrict__ keys, uint64_t n, uint32_t* flag)
 {
+    grid_dep_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if ((ops == nullptr || ops[i] == FLIX_OP_INSERT) && keys[i] == key_max<K>()) atomicOr(flag, ERR_BADKEY);
@@ -46,6 +47,7 @@ __global__ void k_validate(const uint8_t* __restrict__ ops, const K* __restrict_
 template <class K>
 __global__ void k_fold_flags(const K* __restrict__ skeys, uint64_t m, uint32_t* __restrict__ head)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     head[j] = (j == 0 || skeys[j] != skeys[j - 1]) ? 1u : 0u;
@@ -54,6 +56,7 @@ __global__ void k_fold_flags(const K* __restrict__ skeys, uint64_t m, uint32_t* 
 __global__ void k_fold_init(uint64_t m, uint32_t* __restrict__ lastdel, uint32_t* __restrict__ firstins,
                             uint32_t* __restrict__ emit)
 {
+    grid_dep_enter();
     const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m) return;
     lastdel[r] = 0;
@@ -72,6 +75,7 @@ __global__ void k_fold_del(const uint32_t* __restrict__ sidx, uint64_t m, const 
                            const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
                            uint32_t* __restrict__ lastdel)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     if (ops[sidx[j]] == FLIX_OP_DELETE) atomicMax(&lastdel[run_id(head, hex, j)], (uint32_t)(j + 1));
@@ -82,6 +86,7 @@ __global__ void k_fold_ins(const uint32_t* __restrict__ sidx, uint64_t m, const 
                            const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
                            const uint32_t* __restrict__ lastdel, uint32_t* __restrict__ firstins)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
     if (ops[sidx[j]] != FLIX_OP_INSERT) return;
@@ -94,6 +99,7 @@ __global__ void k_fold_emit(uint64_t m, const uint32_t* __restrict__ head, const
                             const uint32_t* __restrict__ lastdel, const uint32_t* __restrict__ firstins,
                             uint32_t* __restrict__ emit, uint32_t* __restrict__ eff, uint32_t* __restrict__ hpos)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m || !head[j]) return;
     const uint32_t r = hex[j];
@@ -113,6 +119,7 @@ __global__ void k_fold_write_mixed(uint64_t m, const K* __restrict__ skeys, cons
                                    const uint32_t* __restrict__ hpos, const uint32_t* __restrict__ firstins,
                                    K* __restrict__ ukey, uint32_t* __restrict__ uop, K* __restrict__ uval)
 {
+    grid_dep_enter();
     const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m || !emit[r]) return;
     const uint32_t p = epos[r];
@@ -129,6 +136,7 @@ __global__ void k_fold_write_hom(uint64_t m, uint32_t eff, const K* __restrict__
                                  const uint32_t* __restrict__ head, const uint32_t* __restrict__ hex,
                                  K* __restrict__ ukey, uint32_t* __restrict__ uop, K* __restrict__ uval)
 {
+    grid_dep_enter();
     const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m || !head[j]) return;
     const uint32_t p = hex[j];
@@ -405,6 +413,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
                                                              HeavyNode* __restrict__ heavy, uint32_t* __restrict__ heavy_n,
                                                              uint32_t heavy_cap)
 {
+    grid_dep_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t NS = ix.NS;
@@ -534,6 +543,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
                                                              uint32_t* __restrict__ free_ids,
                                                              const DevState* __restrict__ ds)
 {
+    grid_dep_enter();
     if (!ds->admitted) return;
     const uint64_t push_base = ds->from;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -781,6 +791,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_heavy_find(DevIdx<K> ix, const K
                                                            K* __restrict__ snap_k, K* __restrict__ snap_v,
                                                            uint32_t* __restrict__ nchunks, uint32_t chunk_cap)
 {
+    grid_dep_enter();
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t NS = ix.NS;
     bool failed = false;
@@ -902,6 +913,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_heavy_count(uint32_t NS, const K
                                                            uint32_t* __restrict__ chunk_add,
                                                            uint32_t* __restrict__ chunk_pre)
 {
+    grid_dep_enter();
     __shared__ K nk[128];
     __shared__ uint32_t sa[HV_THREADS / 32], sd[HV_THREADS / 32];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -980,6 +992,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const
                                                              const uint32_t* __restrict__ chunk_pre,
                                                              const DevState* __restrict__ ds)
 {
+    grid_dep_enter();
     if (!ds->admitted) return;
     __shared__ K nk[128], nv[128];
     __shared__ uint32_t delm[4];
@@ -1086,6 +1099,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_update_heavy(DevIdx<K> ix, const
 __global__ void k_alloc_copy(const uint32_t* __restrict__ free_ids, const DevState* __restrict__ ds,
                              uint32_t* __restrict__ out, uint64_t cap_out)
 {
+    grid_dep_enter();
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (!ds->admitted || i >= ds->need || i >= cap_out) return;
     out[i] = free_ids[ds->from + i];
@@ -1095,6 +1109,7 @@ __global__ void k_admit(DevState* __restrict__ ds, const uint64_t* __restrict__ 
                         const uint32_t* __restrict__ badkey, const uint64_t* __restrict__ range_total,
                         uint64_t range_cap, uint64_t* __restrict__ status)
 {
+    grid_dep_enter();
     const uint64_t v = *nf_total;
     const uint64_t need = v & 0xFFFFFFFFull, freed = v >> 32;
     const uint64_t top = ds->free_top;
@@ -1119,6 +1134,7 @@ __global__ void k_admit(DevState* __restrict__ ds, const uint64_t* __restrict__ 
 
 __global__ void k_commit(DevState* __restrict__ ds)
 {
+    grid_dep_enter();
     if (ds->admitted) ds->free_top = ds->next_top;
     ds->applied = ds->admitted;
     ds->admitted = 0;
@@ -1126,6 +1142,7 @@ __global__ void k_commit(DevState* __restrict__ ds)
 
 __global__ void k_set_free_top(DevState* __restrict__ ds, uint64_t value)
 {
+    grid_dep_enter();
     ds->free_top = value;
     ds->admitted = 0;
 }

@@ -86,6 +86,7 @@ SIGNATURES = {
     "flix_stats": (_INT, [_VP, _VP, _VP]),
     "flix_export": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_dump_layout": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "flix_sort_pairs": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "flix_profile_enable": (_INT, [_VP, _INT]),
     "flix_profile_reset": (_INT, [_VP]),
     "flix_profile_read": (_INT, [_VP, _U32, _VP, _VP, _VP, _VP, _VP]),
@@ -215,6 +216,15 @@ class Index:
         _check(load().flix_lookup(self._h, _ptr(q), q.numel(), _ptr(vals), _ptr(f), _stream(stream)),
                "flix_lookup", self._h)
         return vals, f
+
+    def sort_pairs(self, keys, stream=None):
+        """Test hook: the batch sort alone.  Returns (keys ascending, input position of each)."""
+        q = self._dev(keys)
+        ko = self._empty(q.numel())
+        po = self._empty(q.numel(), torch.int32)
+        _check(load().flix_sort_pairs(self._h, _ptr(q), q.numel(), _ptr(ko), _ptr(po), _stream(stream)),
+               "flix_sort_pairs", self._h)
+        return ko, po
 
     def successor(self, keys, stream=None, out=None):
         """out: optional (keys_out, vals_out) device tensors of at least len(keys) elements."""
