@@ -24,34 +24,35 @@ constexpr int PT_ITEMS = 8;
 constexpr int PT_TILE = PT_THREADS * PT_ITEMS;
 constexpr int RP_THREADS = 256;
 
-// Smallest a in [max(0, d - nB), min(d, nA)] such that A[a] >= B[d - 1 - a]: the number of A
-// items among the first d items of the merge of A and B when B wins ties.
-template <class K>
-__device__ __forceinline__ uint64_t corank(const K* __restrict__ A, uint64_t nA, const K* __restrict__ B,
-                                           uint64_t nB, uint64_t d)
-{
-    uint64_t lo = d > nB ? d - nB : 0, hi = d < nA ? d : nA;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
-        if (A[mid] >= B[d - 1 - mid]) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
 // Merge-path split points: ca[t] = A items among the first min(t * PT_TILE, nA + m) items of the
-// merge of A = mkba and B = the sorted batch (B wins ties), for t = 0..ntiles.
+// merge of A = mkba and B = the sorted batch (B wins ties), for t = 0..ntiles.  One warp per split
+// point: each round probes 32 points of the bracket at once (the test A[a] >= B[d - 1 - a] turns
+// from false to true once along it), so about five dependent rounds replace a binary search's 25.
 template <class K>
 __global__ void __launch_bounds__(256) k_corank(const K* __restrict__ mkba, uint64_t nA, const K* __restrict__ skeys,
                                                 uint64_t mmax, const uint32_t* __restrict__ m_dev,
                                                 uint64_t* __restrict__ ca, uint32_t ntiles)
 {
     grid_dep_enter();
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t > ntiles) return;
+    const uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    if (t > ntiles) return;                     // whole warps leave together
     const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
     const uint64_t L = nA + m;
     const uint64_t d = (uint64_t)t * PT_TILE < L ? (uint64_t)t * PT_TILE : L;
-    ca[t] = corank(mkba, nA, skeys, m, d);
+    uint64_t lo = d > m ? d - m : 0, hi = d < nA ? d : nA;   // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const uint64_t x = lo + ((hi - lo) * (lane + 1)) / 33;   // lo <= x < hi
+        const uint32_t bal = __ballot_sync(FULL, mkba[x] >= skeys[d - 1 - x]);
+        const uint32_t f = bal ? __ffs(bal) - 1 : 32;
+        const uint64_t xf = __shfl_sync(FULL, x, f & 31);
+        const uint64_t xp = __shfl_sync(FULL, x, (f + 31) & 31);
+        if (f < 32) hi = xf;
+        lo = f == 0 ? lo : xp + 1;
+    }
+    const uint64_t x = lo + lane;
+    const uint32_t bal = __ballot_sync(FULL, x < hi && mkba[x] >= skeys[d - 1 - x]);
+    if (lane == 0) ca[t] = bal ? lo + __ffs(bal) - 1 : hi;
 }
 
 // First index in s[0..len) whose value is >= q (lower) or > q (upper).
@@ -70,8 +71,11 @@ __device__ __forceinline__ uint32_t smem_bound(const K* s, uint32_t len, K q)
 
 // One merge-path tile of PT_TILE merged items per block: off[i + 1] = number of batch keys <=
 // mkba[i] (off may be null); bk[j] = bucket of batch key j = number of mkba entries < key j (bk may
-// be null).  Inside the tile each item finds its rank among the other side's tile items by binary
-// search in shared memory; items are thread-strided, so the writes coalesce.
+// be null).  Inside the tile each thread merges PT_ITEMS consecutive merged items: it finds where
+// its diagonal crosses the two sorted slices (a binary search in shared memory), then walks its
+// items in order, a batch key taking the bucket after the mkba entries passed so far and an mkba
+// entry the count of batch keys passed so far (ties: the batch key first).  Results are staged in
+// shared memory and written out coalesced.
 template <class K>
 __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ mkba, const K* __restrict__ skeys,
                                                           const uint64_t* __restrict__ ca, uint64_t nA, uint64_t mmax,
@@ -81,6 +85,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
     grid_dep_enter();
     __shared__ K sA[PT_TILE];
     __shared__ K sB[PT_TILE];
+    __shared__ uint32_t sout[PT_TILE];   // bk of B item t at t; off of A item t at PT_TILE - 1 - t
     const uint64_t m = m_dev ? (uint64_t)*m_dev : mmax;
     const uint64_t L = nA + m;
     const uint64_t d0 = (uint64_t)blockIdx.x * PT_TILE;
@@ -107,12 +112,32 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
         }
     }
     __syncthreads();
+    const uint32_t n = la + lb;
+    const uint32_t k0 = threadIdx.x * PT_ITEMS;
+    if (k0 < n) {
+        // split of diagonal k0: the smallest i with sA[i] >= sB[k0 - 1 - i] (A items among the first k0)
+        uint32_t lo = k0 > lb ? k0 - lb : 0, hi = k0 < la ? k0 : la;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (sA[mid] >= sB[k0 - 1 - mid]) hi = mid; else lo = mid + 1;
+        }
+        uint32_t i = lo, j = k0 - lo;
+        const uint32_t kend = k0 + PT_ITEMS < n ? k0 + PT_ITEMS : n;
+        for (uint32_t k = k0; k < kend; k++) {
+            if (j < lb && (i >= la || !(sA[i] < sB[j]))) {
+                sout[j] = i;                      // batch key j: i mkba entries of the tile are below it
+                j++;
+            } else {
+                sout[PT_TILE - 1 - i] = j;        // mkba entry i: j batch keys of the tile are <= it
+                i++;
+            }
+        }
+    }
+    __syncthreads();
     if (bk)
-        for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS)
-            bk[b0 + t] = (uint32_t)(a0 + smem_bound<K, false>(sA, la, sB[t]));
+        for (uint32_t t = threadIdx.x; t < lb; t += PT_THREADS) bk[b0 + t] = (uint32_t)(a0 + sout[t]);
     if (off)
-        for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS)
-            off[a0 + t + 1] = (uint32_t)(b0 + smem_bound<K, true>(sB, lb, sA[t]));
+        for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS) off[a0 + t + 1] = (uint32_t)(b0 + sout[PT_TILE - 1 - t]);
 }
 
 // First position in nk[0..sz) whose key is >= q.
@@ -177,8 +202,112 @@ struct ReadWin {
     uint8_t* rf;
 };
 
-// Point reads, one thread per sorted query.  Results go to the query's input position, or, with
-// win, to its window's region for k_win_scatter.
+// Result of one point read once its node is known (Sec. 4.1 walk done): pos is the first of the
+// node's sz keys >= q (LOOKUP, SUCC) or > q (PRED), and kpos the key at pos (LOOKUP, SUCC, when
+// pos < sz) or at pos - 1 (PRED, when pos > 0).  A successor past the node continues with the
+// first key of the next non-empty node in chain order, into the following buckets (Sec. 6.5: the
+// smallest key >= q); a predecessor before the node's first key takes the last key of the node
+// walked past, else of the nearest earlier bucket whose chain holds a key.
+template <class K>
+__device__ __forceinline__ void point_result(const DevIdx<K>& ix, int op, K q, uint32_t b, uint32_t node, uint32_t sz,
+                                             uint32_t nx, uint32_t prev, uint32_t pos, K kpos, K& rk, K& rv,
+                                             uint8_t& f)
+{
+    const uint32_t NS = ix.NS;
+    if (op == FLIX_OP_PRED) {
+        // chain nodes other than a bucket's only node are never empty
+        uint32_t pn = NIL, pp = 0;
+        if (pos > 0) {
+            rk = kpos;
+            rv = ix.vals[(uint64_t)node * NS + pos - 1];
+            f = 1;
+            return;
+        }
+        if (prev != NIL && ix.size[prev] > 0) {
+            pn = prev;
+            pp = ix.size[prev] - 1;
+        } else {
+            uint64_t guard = 0;
+            const uint64_t lim = (uint64_t)ix.cap + ix.nb + 1;
+            for (int64_t bb = (int64_t)b - 1; bb >= 0 && pn == NIL && guard < lim; bb--) {
+                uint32_t x = ix.head[bb];
+                uint32_t last = x;
+                while (x != NIL && guard++ < lim) {
+                    last = x;
+                    x = ix.next[x];
+                }
+                const uint32_t ls = ix.size[last];
+                if (ls > 0) {
+                    pn = last;
+                    pp = ls - 1;
+                }
+            }
+        }
+        if (pn != NIL) {
+            rk = ix.keys[(uint64_t)pn * NS + pp];
+            rv = ix.vals[(uint64_t)pn * NS + pp];
+            f = 1;
+        }
+        return;
+    }
+    if (op == FLIX_OP_LOOKUP) {
+        if (pos < sz && kpos == q) {
+            rk = q;
+            rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
+            f = 1;
+        }
+        return;
+    }
+    if (pos < sz) {
+        rk = kpos;
+        rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
+        f = 1;
+        return;
+    }
+    // the smallest key >= q is the first key of the next non-empty node in chain order,
+    // continuing into the following buckets
+    uint32_t n2 = nx;
+    uint64_t bb = b;
+    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
+        if (n2 == NIL) {
+            if (++bb >= ix.nb) break;
+            n2 = ix.head[bb];
+            continue;
+        }
+        if (ix.size[n2] > 0) {
+            rk = ix.keys[(uint64_t)n2 * NS];
+            rv = ix.vals[(uint64_t)n2 * NS];
+            f = 1;
+            break;
+        }
+        n2 = ix.next[n2];
+    }
+}
+
+// Delivery of one result: to the query's input position, or (win) tagged with it into the next
+// free place of its window's region (offsets per window and block from a count and a scan).
+template <class K>
+__device__ __forceinline__ void deliver(uint32_t idx, K rk, K rv, uint8_t f, K* __restrict__ keys_out,
+                                        K* __restrict__ vals_out, uint8_t* __restrict__ found_out,
+                                        const ReadWin<K>& win, uint32_t nwin, uint32_t* s_wcnt)
+{
+    if (!nwin) {
+        if (keys_out) keys_out[idx] = rk;
+        if (vals_out) vals_out[idx] = rv;
+        if (found_out) found_out[idx] = f;
+        return;
+    }
+    const uint32_t w = idx >> win.shift;
+    const uint32_t r = atomicAdd(&s_wcnt[w], 1u);
+    const uint64_t at = win.off[(uint64_t)w * gridDim.x + blockIdx.x] + r;
+    win.idx[at] = idx;
+    if (keys_out) win.rk[at] = rk;
+    if (vals_out) win.rv[at] = rv;
+    if (found_out) win.rf[at] = f;
+}
+
+// Point reads, one thread per sorted query (bucket bk from the partition).  Results go to the
+// query's input position, or, with win, to its window's region for k_win_scatter.
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mode, const K* __restrict__ skeys,
                                                            const uint32_t* __restrict__ sidx, uint64_t m,
@@ -203,95 +332,23 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
     if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC || op == FLIX_OP_PRED) {
         const K q = skeys[j];
         const uint32_t b = bk[j];
-        const uint32_t NS = ix.NS;
         uint32_t node, sz, nx, prev;
         K bd;
-        if (!find_node(ix, b, q, node, sz, bd, nx, prev)) {
-            // chain error flagged; default results
-        } else if (op == FLIX_OP_PRED) {
-            // the largest stored key <= q: below the node's first key > q, else the last key of
-            // the node walked past (chain nodes other than a bucket's only node are never empty),
-            // else of the nearest earlier bucket whose chain holds a key
-            const K* nk = ix.keys + (uint64_t)node * NS;
-            const uint32_t pu = node_upper_bound(nk, 0, sz, q);
-            uint32_t pn = NIL, pp = 0;
-            if (pu > 0) {
-                pn = node;
-                pp = pu - 1;
-            } else if (prev != NIL && ix.size[prev] > 0) {
-                pn = prev;
-                pp = ix.size[prev] - 1;
+        if (find_node(ix, b, q, node, sz, bd, nx, prev)) {   // else: chain error flagged, default results
+            const K* nk = ix.keys + (uint64_t)node * ix.NS;
+            uint32_t pos;
+            K kpos = K(0);
+            if (op == FLIX_OP_PRED) {
+                pos = node_upper_bound(nk, 0, sz, q);
+                if (pos > 0) kpos = __ldg(nk + pos - 1);
             } else {
-                uint64_t guard = 0;
-                const uint64_t lim = (uint64_t)ix.cap + ix.nb + 1;
-                for (int64_t bb = (int64_t)b - 1; bb >= 0 && pn == NIL && guard < lim; bb--) {
-                    uint32_t x = ix.head[bb];
-                    uint32_t last = x;
-                    while (x != NIL && guard++ < lim) {
-                        last = x;
-                        x = ix.next[x];
-                    }
-                    const uint32_t ls = ix.size[last];
-                    if (ls > 0) {
-                        pn = last;
-                        pp = ls - 1;
-                    }
-                }
+                pos = node_lower_bound(nk, sz, q);
+                if (pos < sz) kpos = __ldg(nk + pos);
             }
-            if (pn != NIL) {
-                rk = ix.keys[(uint64_t)pn * NS + pp];
-                rv = ix.vals[(uint64_t)pn * NS + pp];
-                f = 1;
-            }
-        } else {
-            const K* nk = ix.keys + (uint64_t)node * NS;
-            const uint32_t pos = node_lower_bound(nk, sz, q);
-            if (op == FLIX_OP_LOOKUP) {
-                if (pos < sz && __ldg(nk + pos) == q) {
-                    rk = q;
-                    rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
-                    f = 1;
-                }
-            } else if (pos < sz) {
-                rk = __ldg(nk + pos);
-                rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
-                f = 1;
-            } else {
-                // the smallest key >= q is the first key of the next non-empty node in chain order,
-                // continuing into the following buckets
-                uint32_t n2 = nx;
-                uint64_t bb = b;
-                for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
-                    if (n2 == NIL) {
-                        if (++bb >= ix.nb) break;
-                        n2 = ix.head[bb];
-                        continue;
-                    }
-                    if (ix.size[n2] > 0) {
-                        rk = ix.keys[(uint64_t)n2 * NS];
-                        rv = ix.vals[(uint64_t)n2 * NS];
-                        f = 1;
-                        break;
-                    }
-                    n2 = ix.next[n2];
-                }
-            }
+            point_result(ix, op, q, b, node, sz, nx, prev, pos, kpos, rk, rv, f);
         }
     }
-    if (!nwin) {
-        if (keys_out) keys_out[idx] = rk;
-        if (vals_out) vals_out[idx] = rv;
-        if (found_out) found_out[idx] = f;
-        return;
-    }
-    // windowed: the result goes, tagged with idx, to the next free place of its window's region
-    const uint32_t w = idx >> win.shift;
-    const uint32_t r = atomicAdd(&s_wcnt[w], 1u);
-    const uint64_t at = win.off[(uint64_t)w * gridDim.x + blockIdx.x] + r;
-    win.idx[at] = idx;
-    if (keys_out) win.rk[at] = rk;
-    if (vals_out) win.rv[at] = rv;
-    if (found_out) win.rf[at] = f;
+    deliver(idx, rk, rv, f, keys_out, vals_out, found_out, win, nwin, s_wcnt);
 }
 
 // Windowed result delivery: counts[w * nblocks + b] = results of read block b whose input position
@@ -512,8 +569,8 @@ cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64
     const uint32_t grid = div_up(nb + m, PT_TILE);
     uint64_t* ca = c.h->arena.take<uint64_t>((size_t)grid + 1);
     if (!ca) return cudaErrorMemoryAllocation;
-    cudaError_t e = launch(c, K_PARTITION, dim3(div_up((uint64_t)grid + 1, 256)), dim3(256), 0, k_corank<K>, mkba, nb,
-                           skeys, m, m_dev, ca, grid);
+    cudaError_t e = launch(c, K_PARTITION, dim3(div_up(((uint64_t)grid + 1) * 32, 256)), dim3(256), 0, k_corank<K>,
+                           mkba, nb, skeys, m, m_dev, ca, grid);
     if (e) return e;
     return launch(c, K_PARTITION, dim3(grid), dim3(PT_THREADS), 0, k_partition<K>, mkba, skeys, (const uint64_t*)ca,
                   nb, m, m_dev, off, bk);

@@ -503,3 +503,50 @@ def test_torch_caching_allocator(fx):
     idx.close()
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == before
+
+
+@pytest.mark.parametrize("kw,NS", [(32, 2), (64, 8), (32, 32), (64, 64), (64, 128)])
+def test_point_reads_on_chains_every_density(fx, kw, NS):
+    """Lookup, successor and predecessor batches of 1/2, 4 and 64 queries per node on an index whose
+    buckets are chains (after skewed inserts and some deletes): the fused read stages the nodes of a
+    warp's queries in shared memory in one or two rounds, or searches them in global memory when
+    the queries hit many nodes; every output against the ordered map."""
+    rng = np.random.default_rng(NS + kw)
+    load = W.universe(kw, 21, 0, 6000).astype(np.uint64)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    vals = W.values_for(kw, load)
+    idx.bulk_load(load.astype(np.uint32 if kw == 32 else np.uint64), vals)
+    mp = oracle.Map(kw)
+    mp.bulk_load(load, vals)
+    lo = int(np.sort(load)[1000])
+    ins = np.unique(lo + rng.integers(1, 1 << 24, 8000).astype(np.uint64))          # a dense range: chains
+    ins = ins[~np.isin(ins, load)]
+    ins = np.concatenate([ins, W.universe(kw, 21, 6000, 9000).astype(np.uint64)])
+    iv = W.values_for(kw, ins, salt=3)
+    dt = np.uint32 if kw == 32 else np.uint64
+    idx.insert(ins.astype(dt), iv)
+    mp.update(np.full(ins.size, W.OP_INSERT, np.uint8), ins, iv)
+    dels = ins[rng.integers(0, ins.size, 2000)]
+    idx.delete(dels.astype(dt))
+    mp.update(np.full(dels.size, W.OP_DELETE, np.uint8), dels)
+    assert idx.stats()["max_chain"] > 1
+    sk_, sv_ = mp.export()
+    nodes = idx.stats()["nodes_used"]
+    for per_node in (0.5, 4, 64):
+        m = max(1, int(per_node * nodes))
+        q = np.concatenate([sk_[rng.integers(0, sk_.size, m // 2)],
+                            rng.integers(0, (1 << kw) - 1, m - m // 2, dtype=np.uint64)])
+        q = q[rng.permutation(q.size)].astype(dt)
+        v, f = idx.lookup(q)
+        e = mp.read(np.full(q.size, W.OP_LOOKUP, np.uint8), q)
+        same(np_of(v, kw), e["vals"], "lookup.vals %s" % per_node)
+        same(f.cpu().numpy(), e["found"], "lookup.found %s" % per_node)
+        k2, v2 = idx.successor(q)
+        e = mp.read(np.full(q.size, W.OP_SUCC, np.uint8), q)
+        same(np_of(k2, kw), e["keys"], "succ.keys %s" % per_node)
+        same(np_of(v2, kw), e["vals"], "succ.vals %s" % per_node)
+        k3, v3 = idx.predecessor(q)
+        e = mp.read(np.full(q.size, W.OP_PRED, np.uint8), q)
+        same(np_of(k3, kw), e["keys"], "pred.keys %s" % per_node)
+        same(np_of(v3, kw), e["vals"], "pred.vals %s" % per_node)
+    idx.close()
