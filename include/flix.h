@@ -83,7 +83,12 @@ typedef struct {
     uint32_t merge_underfull; /* nonzero: after every update batch (synchronous or not), each bucket
                                  the batch touched merges underfull neighbours (flix_merge_underfull).
                                  0 (default): off */
-    uint32_t reserved[3];
+    uint32_t bucket_threads;  /* threads that apply one bucket's updates (the paper's single-thread
+                                 and tiled kernels, Sec. 4.2-4.3): 0 (default) one thread for a
+                                 bucket whose chain is one node and that receives at most 8 updates
+                                 which still fit the node, a warp (32 threads) for every other
+                                 bucket; 32: a warp for every bucket.  Same layout either way */
+    uint32_t reserved[2];
     /* Optional device allocator for every device buffer the handle owns (node pool, bucket arrays,
      * scratch, state words), e.g. a framework's caching allocator: dev_alloc(bytes, alloc_ctx)
      * returns memory of the current device aligned to at least 256 bytes, or NULL when it cannot;

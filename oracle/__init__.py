@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -56,6 +56,10 @@ def lib():
         L.om_map_range_fill.argtypes = [vp, sz, vp, vp, vp, vp, vp, vp]
         L.om_map_update.restype = i32
         L.om_map_update.argtypes = [vp, sz, vp, vp, vp]
+        L.om_map_read_mt.argtypes = [vp, sz, vp, vp, vp, vp, vp, vp, vp, i32]
+        L.om_map_range_fill_mt.argtypes = [vp, sz, vp, vp, vp, vp, vp, vp, i32]
+        L.om_map_update_mt.restype = i32
+        L.om_map_update_mt.argtypes = [vp, sz, vp, vp, vp, i32]
         L.om_delete_compact.restype = u32
         L.om_delete_compact.argtypes = [vp, u32, vp, u32, vp, vp]
         L.om_merge_insert.restype = u32
@@ -154,6 +158,29 @@ class Map:
         o, k = _u8(ops), _u64(keys)
         a = _u64(aux) if aux is not None else np.zeros(k.size, np.uint64)
         return lib().om_map_update(self._h, k.size, _p(o), _p(k), _p(a))
+
+    def read_mt(self, ops, keys, aux=None, threads: int = 1, ranges: bool = True):
+        """read() on `threads` host threads (the batch-synchronous CPU baseline); same outputs."""
+        o, k = _u8(ops), _u64(keys)
+        a = _u64(aux) if aux is not None else np.zeros(k.size, np.uint64)
+        n = k.size
+        ok = np.empty(n, np.uint64)
+        ov = np.empty(n, np.uint64)
+        of = np.empty(n, np.uint8)
+        off = np.empty(n + 1, np.uint64)
+        lib().om_map_read_mt(self._h, n, _p(o), _p(k), _p(a), _p(ov), _p(of), _p(ok), _p(off), threads)
+        tot = int(off[-1])
+        rk = np.empty(tot, np.uint64)
+        rv = np.empty(tot, np.uint64)
+        if tot and ranges:
+            lib().om_map_range_fill_mt(self._h, n, _p(o), _p(k), _p(a), _p(off), _p(rk), _p(rv), threads)
+        return dict(keys=ok, vals=ov, found=of, range_off=off, range_keys=rk, range_vals=rv)
+
+    def update_mt(self, ops, keys, aux=None, threads: int = 1) -> int:
+        """update() on `threads` host threads; same result."""
+        o, k = _u8(ops), _u64(keys)
+        a = _u64(aux) if aux is not None else np.zeros(k.size, np.uint64)
+        return lib().om_map_update_mt(self._h, k.size, _p(o), _p(k), _p(a), threads)
 
     def apply(self, ops, keys, aux=None):
         """A mixed batch: reads on the snapshot, then updates.  Returns (reads, status)."""

@@ -42,10 +42,17 @@
  *     both hold at most NS/2 pairs.  A policy runs both after every update batch on the buckets
  *     the batch touched (merge first, then split).
  *
+ *  3. The same semantic map on all host cores (om_map_*_mt): the batch's reads split over threads by
+ *     op ranges (each thread answers its ops on the unchanged snapshot), range offsets by one
+ *     sequential scan, then the batch's net updates (the same per-key replay as om_map_update)
+ *     merged into the sorted arrays by threads that each own a key range.  Same results as part 1;
+ *     it is the timed CPU baseline, not a reference for the GPU.
+ *
  * Keys and values are held as uint64 for both key widths kw in {32, 64}; KEY_MAX = 2^kw - 1 is not a
  * storable key (it is the last bucket's maxBucket and the successor "none" key) and VAL_NONE is
  * the all-ones value of the same width.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -899,5 +906,179 @@ int om_model_check(const om_model* m, int build_shape)
         }
     }
     if (in_chains + m->nfree != m->hw) return 5;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * 3. Batch-synchronous map on all host cores
+ * ---------------------------------------------------------------------------------------------- */
+
+typedef struct {
+    const om_map* m;
+    size_t lo, hi;
+    const uint8_t* ops;
+    const uint64_t *keys, *aux;
+    uint64_t *out_val, *out_key, *cnt;
+    uint8_t* out_found;
+    const uint64_t* range_off;
+    uint64_t *rkeys, *rvals;
+} mt_read_job;
+
+static void* mt_read_part(void* arg)
+{
+    mt_read_job* j = (mt_read_job*)arg;
+    const size_t n = j->hi - j->lo;
+    uint64_t* off = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+    om_map_read(j->m, n, j->ops + j->lo, j->keys + j->lo, j->aux + j->lo, j->out_val ? j->out_val + j->lo : NULL,
+                j->out_found ? j->out_found + j->lo : NULL, j->out_key ? j->out_key + j->lo : NULL, off);
+    for (size_t i = 0; i < n; i++) j->cnt[j->lo + i] = off[i + 1] - off[i];
+    free(off);
+    return NULL;
+}
+
+static void* mt_fill_part(void* arg)
+{
+    mt_read_job* j = (mt_read_job*)arg;
+    om_map_range_fill(j->m, j->hi - j->lo, j->ops + j->lo, j->keys + j->lo, j->aux + j->lo, j->range_off + j->lo,
+                      j->rkeys, j->rvals);
+    return NULL;
+}
+
+static int clamp_threads(int t) { return t < 1 ? 1 : (t > 256 ? 256 : t); }
+
+/* om_map_read on nthreads threads (same outputs); range_off is required. */
+void om_map_read_mt(const om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux,
+                    uint64_t* out_val, uint8_t* out_found, uint64_t* out_key, uint64_t* range_off, int nthreads)
+{
+    const int T = clamp_threads(nthreads);
+    pthread_t th[256];
+    mt_read_job jb[256];
+    uint64_t* cnt = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    for (int t = 0; t < T; t++) {
+        mt_read_job j = {m, n * t / T, n * (t + 1) / T, ops, keys, aux, out_val, out_key, cnt, out_found, NULL, NULL, NULL};
+        jb[t] = j;
+        pthread_create(&th[t], NULL, mt_read_part, &jb[t]);
+    }
+    for (int t = 0; t < T; t++) pthread_join(th[t], NULL);
+    range_off[0] = 0;
+    for (size_t i = 0; i < n; i++) range_off[i + 1] = range_off[i] + cnt[i];
+    free(cnt);
+}
+
+/* om_map_range_fill on nthreads threads. */
+void om_map_range_fill_mt(const om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux,
+                          const uint64_t* range_off, uint64_t* rkeys, uint64_t* rvals, int nthreads)
+{
+    const int T = clamp_threads(nthreads);
+    pthread_t th[256];
+    mt_read_job jb[256];
+    for (int t = 0; t < T; t++) {
+        mt_read_job j = {m, n * t / T, n * (t + 1) / T, ops, keys, aux, NULL, NULL, NULL, NULL, range_off, rkeys, rvals};
+        jb[t] = j;
+        pthread_create(&th[t], NULL, mt_fill_part, &jb[t]);
+    }
+    for (int t = 0; t < T; t++) pthread_join(th[t], NULL);
+}
+
+typedef struct {
+    const om_map* m;
+    const orec* r;
+    size_t rlo, rhi;      /* this thread's update records (whole key runs) */
+    size_t mlo, mhi;      /* the map slots with keys in its key range */
+    uint64_t *nk, *nv;    /* output arrays (NULL: count only) */
+    size_t out0, cnt;
+} mt_merge_job;
+
+/* The merge of one key range: map slots [mlo, mhi) and update records [rlo, rhi), each key's run
+ * replayed on that key's prior state (as om_map_update). */
+static void* mt_merge_part(void* arg)
+{
+    mt_merge_job* j = (mt_merge_job*)arg;
+    const om_map* m = j->m;
+    size_t i = j->mlo, k = j->rlo, c = 0;
+    while (i < j->mhi || k < j->rhi) {
+        if (k >= j->rhi || (i < j->mhi && m->k[i] < j->r[k].key)) {
+            if (j->nk) { j->nk[j->out0 + c] = m->k[i]; j->nv[j->out0 + c] = m->v[i]; }
+            c++; i++;
+            continue;
+        }
+        size_t e = k;
+        while (e < j->rhi && j->r[e].key == j->r[k].key) e++;
+        int present = 0;
+        uint64_t val = 0;
+        if (i < j->mhi && m->k[i] == j->r[k].key) { present = 1; val = m->v[i]; i++; }
+        apply_run(j->r + k, e - k, &present, &val);
+        if (present) {
+            if (j->nk) { j->nk[j->out0 + c] = j->r[k].key; j->nv[j->out0 + c] = val; }
+            c++;
+        }
+        k = e;
+    }
+    j->cnt = c;
+    return NULL;
+}
+
+/* om_map_update on nthreads threads (same result). */
+int om_map_update_mt(om_map* m, size_t n, const uint8_t* ops, const uint64_t* keys, const uint64_t* aux,
+                     int nthreads)
+{
+    size_t u = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (ops[i] == OP_INSERT && keys[i] >= m->kmax) return -1;
+        if (ops[i] == OP_INSERT || ops[i] == OP_DELETE) u++;
+    }
+    orec* r = (orec*)malloc((u ? u : 1) * sizeof(orec));
+    u = 0;
+    for (size_t i = 0; i < n; i++) {
+        if (ops[i] != OP_INSERT && ops[i] != OP_DELETE) continue;
+        r[u].key = keys[i];
+        r[u].val = ops[i] == OP_INSERT ? aux[i] : 0;
+        r[u].pos = i;
+        r[u].op = ops[i];
+        u++;
+    }
+    qsort(r, u, sizeof(orec), cmp_key_pos);
+    const int T = clamp_threads(nthreads);
+    pthread_t th[256];
+    mt_merge_job jb[256];
+    /* thread t owns the update records from split t (moved forward to a key boundary) and the map
+     * keys below the next thread's first record key */
+    size_t split[257];
+    for (int t = 0; t <= T; t++) {
+        size_t s = u * (size_t)t / (size_t)T;
+        while (s > 0 && s < u && r[s].key == r[s - 1].key) s++;
+        split[t] = s;
+    }
+    for (int t = 1; t <= T; t++)
+        if (split[t] < split[t - 1]) split[t] = split[t - 1];
+    for (int t = 0; t < T; t++) {
+        mt_merge_job j;
+        memset(&j, 0, sizeof(j));
+        j.m = m;
+        j.r = r;
+        j.rlo = split[t];
+        j.rhi = split[t + 1];
+        j.mlo = t == 0 ? 0 : (split[t] < u ? lower_bound_u64(m->k, m->n, r[split[t]].key) : m->n);
+        j.mhi = t + 1 == T ? m->n : (split[t + 1] < u ? lower_bound_u64(m->k, m->n, r[split[t + 1]].key) : m->n);
+        jb[t] = j;
+        pthread_create(&th[t], NULL, mt_merge_part, &jb[t]);
+    }
+    for (int t = 0; t < T; t++) pthread_join(th[t], NULL);
+    size_t total = 0;
+    for (int t = 0; t < T; t++) { jb[t].out0 = total; total += jb[t].cnt; }
+    uint64_t* nk = (uint64_t*)malloc((total + 1) * sizeof(uint64_t));
+    uint64_t* nv = (uint64_t*)malloc((total + 1) * sizeof(uint64_t));
+    for (int t = 0; t < T; t++) {
+        jb[t].nk = nk;
+        jb[t].nv = nv;
+        pthread_create(&th[t], NULL, mt_merge_part, &jb[t]);
+    }
+    for (int t = 0; t < T; t++) pthread_join(th[t], NULL);
+    free(m->k);
+    free(m->v);
+    m->k = nk;
+    m->v = nv;
+    m->n = total;
+    free(r);
     return 0;
 }

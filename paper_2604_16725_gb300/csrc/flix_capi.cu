@@ -909,6 +909,7 @@ int flix_create(const flix_config* cfg, flix_t* out)
     if (cfg->fill_pct == 0 || cfg->fill_pct > 100) return FLIX_EINVAL;
     if (cfg->sort_digit_bits != 0 && cfg->sort_digit_bits != 8) return FLIX_ENOTIMPL;
     if (cfg->sort_variant > FLIX_SORT_REDUCE_SCAN) return FLIX_EINVAL;
+    if (cfg->bucket_threads != 0 && cfg->bucket_threads != 32) return FLIX_EINVAL;
     if (!cfg->dev_alloc != !cfg->dev_free) return FLIX_EINVAL;   // both or neither
     preload_kernels();
     flix_index* h = new flix_index();

@@ -56,6 +56,7 @@ struct DevIdx {
     uint32_t nb;
     uint32_t cap;   // node-pool capacity: no chain walk takes more steps
     uint32_t* err;
+    uint32_t lane_path;   // nonzero: a light one-node bucket's updates are applied by one thread
 };
 
 enum KernelId {
@@ -246,6 +247,7 @@ DevIdx<K> dev_view(flix_index* h)
     d.nb = static_cast<uint32_t>(h->nb);
     d.cap = static_cast<uint32_t>(h->cap);
     d.err = h->err;
+    d.lane_path = h->cfg.bucket_threads != 32;
     return d;
 }
 

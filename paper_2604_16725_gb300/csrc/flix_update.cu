@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const
         nf[b0 + lane] = 0;
         allgone[b0 + lane] = 0;
     }
-    const bool fast = ((mask >> lane) & 1u) && g.nx == NIL && g.ue - g.us <= FAST_U;
+    const bool fast = ((mask >> lane) & 1u) && ix.lane_path && g.nx == NIL && g.ue - g.us <= FAST_U;
     if (fast) {
         const uint32_t t = lane_count<K>(ix.keys + (uint64_t)g.node * NS, g.sz, ukey, uop, g.us, g.ue);
         tnode[g.node] = t;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update_apply(DevIdx<K> ix, const
         ag_l = allgone[b0 + lane];
         t0_l = tnode[g.node];
     }
-    const bool fast = ((mask >> lane) & 1u) && g.nx == NIL && g.ue - g.us <= FAST_U && t0_l <= NS;
+    const bool fast = ((mask >> lane) & 1u) && ix.lane_path && g.nx == NIL && g.ue - g.us <= FAST_U && t0_l <= NS;
     if (fast) {
         lane_apply<K>(ix.keys + (uint64_t)g.node * NS, ix.vals + (uint64_t)g.node * NS, g.sz, t0_l, ukey, uop, uval,
                       g.us, g.ue);

@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("grow", ctypes.c_uint32), ("pool_nodes", ctypes.c_uint64), ("sort_digit_bits", ctypes.c_uint32),
                 ("sort_variant", ctypes.c_uint32), ("restructure_in_one_pass", ctypes.c_uint32),
                 ("split_chains_over", ctypes.c_uint32), ("merge_underfull", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3), ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p),
+                ("bucket_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2), ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p),
                 ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -141,9 +141,10 @@ class Index:
     def __init__(self, key_bits: int = 64, node_size: int | None = None, fill_pct: int = 50,
                  pool_nodes: int = 0, grow: bool = True, device=None, sort_variant: int = 0,
                  restructure_in_one_pass: bool = True, split_chains_over: int = 0,
-                 merge_underfull: bool = False, allocator: str | None = None):
+                 merge_underfull: bool = False, allocator: str | None = None, bucket_threads: int = 0):
         """allocator: None (cudaMalloc) or "torch" (every device buffer of the index comes from
-        PyTorch's caching allocator and counts in torch.cuda.memory_allocated)."""
+        PyTorch's caching allocator and counts in torch.cuda.memory_allocated).  bucket_threads: 0 (one
+        thread for a light one-node bucket, a warp otherwise) or 32 (a warp for every bucket)."""
         if not torch.cuda.is_available():
             raise RuntimeError("FliX needs a CUDA device; none is available")
         L = load()
@@ -162,6 +163,7 @@ class Index:
         cfg.restructure_in_one_pass = 1 if restructure_in_one_pass else 0
         cfg.split_chains_over = split_chains_over
         cfg.merge_underfull = 1 if merge_underfull else 0
+        cfg.bucket_threads = bucket_threads
         self._alloc_cbs = None
         if allocator == "torch":
             self._alloc_cbs = _torch_allocator(self.device)   # kept alive as long as the index

@@ -138,3 +138,32 @@ def test_random_batch_sequences(seed):
             md.restructure()
             assert md.check(build_shape=True) == 0
             assert md.dump()["keys"].tolist() == before
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_batch_synchronous_map_on_threads_equals_the_map(threads):
+    """The all-core CPU baseline (reads split over threads, updates merged by key range on threads)
+    gives the results and the state of the plain map after every mixed batch."""
+    rng = np.random.default_rng(threads)
+    for kw in (32, 64):
+        load = np.unique(rng.integers(0, 50000, 6000).astype(np.uint64))
+        a, b = oracle.Map(kw), oracle.Map(kw)
+        a.bulk_load(load, load * np.uint64(3))
+        b.bulk_load(load, load * np.uint64(3))
+        for rnd in range(6):
+            n = int(rng.integers(1, 4000))
+            ops = rng.choice([oracle.OP_LOOKUP, oracle.OP_SUCC, oracle.OP_PRED, oracle.OP_RANGE, oracle.OP_INSERT,
+                              oracle.OP_DELETE, oracle.OP_NOP], n).astype(np.uint8)
+            keys = rng.integers(0, 52000, n).astype(np.uint64)
+            hit = rng.random(n) < 0.4                     # stored keys for hits, deletes and upserts
+            keys[hit] = load[rng.integers(0, load.size, int(hit.sum()))]
+            aux = np.where(ops == oracle.OP_RANGE, keys + rng.integers(0, 300, n).astype(np.uint64),
+                           rng.integers(0, 1 << 20, n).astype(np.uint64))
+            ra = a.read(ops, keys, aux)
+            rb = b.read_mt(ops, keys, aux, threads=threads)
+            for f in ("keys", "vals", "found", "range_off", "range_keys", "range_vals"):
+                assert np.array_equal(ra[f], rb[f]), (kw, rnd, f)
+            assert a.update(ops, keys, aux) == b.update_mt(ops, keys, aux, threads=threads) == 0
+            ka, va = a.export()
+            kb, vb = b.export()
+            assert np.array_equal(ka, kb) and np.array_equal(va, vb), (kw, rnd)

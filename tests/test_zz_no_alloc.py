@@ -1,5 +1,6 @@
 """flix_lookup_noalloc, the lookup entry point that allocates no device memory during the call, gives
-exactly the results of flix_lookup, on two calls in a row, through the C ABI.
+exactly the results of flix_lookup, on two calls in a row, through the C ABI, and both equal the
+oracle's lookup over the loaded keys.
 
 It serves callers that cannot allocate device memory when they query (a process whose allocator
 has already reserved the device, a latency-bound path that must not block on cudaMalloc, a custom
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import workload as W
 
 pytestmark = pytest.mark.gpu
@@ -30,6 +32,9 @@ def test_noalloc_lookup_matches_lookup(kw, NS):
     idx = fx.Index(key_bits=kw, node_size=NS)
     idx.bulk_load(c["load_keys"], c["load_vals"])
     stream = torch.cuda.current_stream()
+    order = np.argsort(c["load_keys"].astype(np.uint64), kind="stable")
+    sk = c["load_keys"].astype(np.uint64)[order]
+    sv = c["load_vals"].astype(np.uint64)[order]
     for call, q in enumerate((c["queries"], c["queries"][::-1][:40000].copy())):
         qd = idx._dev(q)
         n = qd.numel()
@@ -41,6 +46,10 @@ def test_noalloc_lookup_matches_lookup(kw, NS):
         torch.cuda.synchronize()
         assert torch.equal(v, v_ref), "values differ on call %d" % call
         assert torch.equal(f, f_ref), "found flags differ on call %d" % call
+        ev, ef = oracle.sorted_lookup(sk, sv, q.astype(np.uint64), kw)
+        got = v.cpu().numpy().view(np.uint32 if kw == 32 else np.uint64).astype(np.uint64)
+        assert np.array_equal(got, ev), "values differ from the oracle on call %d" % call
+        assert np.array_equal(f.cpu().numpy(), ef), "found flags differ from the oracle on call %d" % call
         assert 0.6 < f.float().mean().item() < 0.8
 
 
