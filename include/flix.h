@@ -236,6 +236,44 @@ int flix_apply_async(flix_t h, const uint8_t* d_ops, const void* d_keys, const v
                      void* d_range_keys, void* d_range_vals, uint64_t range_cap, uint64_t* d_status,
                      void* stream);
 
+/* One batch of a persistent queue (flix_apply_queue): the arrays of a flix_apply_async call, all
+ * caller-owned device memory, plus an optional device word `ready`: when it is not NULL the kernel
+ * waits for the word to become nonzero before it reads the batch (a producer can then fill the
+ * batch while the kernel runs the ones before it). */
+typedef struct {
+    const uint8_t* ops;    /* n op codes FLIX_OP_* */
+    const void* keys;      /* n keys */
+    const void* aux;       /* n insert values or range upper bounds */
+    uint64_t n;            /* at most FLIX_QUEUE_BATCH_MAX */
+    void* keys_out;        /* n, as flix_apply (may be NULL when no op writes it) */
+    void* vals_out;        /* n */
+    uint8_t* found;        /* n */
+    uint64_t* range_off;   /* n + 1 */
+    void* range_keys;      /* range_cap */
+    void* range_vals;      /* range_cap */
+    uint64_t range_cap;
+    uint64_t* status;      /* 4 words, as flix_apply_async; flags bit 8: not run (a wait gave up) */
+    const uint32_t* ready; /* NULL, or a word the kernel waits on before it reads the batch */
+} flix_batch;
+
+#define FLIX_QUEUE_BATCH_MAX 2048u
+
+/* A queue of count small mixed batches run in order by ONE persistent kernel (the batched form of
+ * the paper's method: no launch per batch).  A cooperative grid of one wave of blocks takes the
+ * batches one after another; each batch goes through the method's steps as phases separated by
+ * grid barriers: its sort (Sec. 3.3) and same-key fold, the snapshot reads and every op's bucket,
+ * the per-bucket update count and the range offsets, the admission (free nodes, range capacity,
+ * reserved key), the range pairs, and the per-bucket merge, split and compaction (Sec. 4.3.2,
+ * Sec. 4.4), one thread per touched bucket.  Each batch has exactly the semantics and outputs of
+ * flix_apply_async (a rejected batch changes nothing; its reads are still written).  Every wait (a
+ * batch's ready word, a grid barrier) gives up after wait_us microseconds: the queue then stops,
+ * the batches not run get flag 8 in status[0], and the next synchronising call on the handle
+ * returns FLIX_ETIMEDOUT.  h_batches is a HOST array of count descriptors (copied before the
+ * launch).  Asynchronous; not for stream capture.  The chain split and underfull merge policies
+ * are not applied on this path (FLIX_ENOTIMPL when one is configured).  Returns FLIX_EINVAL for a
+ * batch larger than FLIX_QUEUE_BATCH_MAX. */
+int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us, void* stream);
+
 /* Reserve scratch for batches of up to batch_max ops and grow the pool (if needed) so that at least
  * free_nodes_min nodes are free.  Synchronises.  FLIX_ENOMEM if the device cannot hold it. */
 int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* stream);

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libflix.so")
 
-SOURCES = ["flix_sort.cu", "flix_read.cu", "flix_update.cu", "flix_build.cu", "flix_capi.cu", "flix_noalloc.cu"]
+SOURCES = ["flix_sort.cu", "flix_read.cu", "flix_update.cu", "flix_build.cu", "flix_capi.cu", "flix_noalloc.cu",
+           "flix_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]

@@ -19,7 +19,7 @@ const char* kKernelNames[K_NUM] = {
     "validate", "fold_flags", "fold_init", "fold_del", "fold_ins", "fold_emit", "fold_write",
     "update_count", "alloc_copy", "update_apply", "admit",
     "live_count", "gather", "cut_keys", "cut_meta", "dedupe", "stats", "fill", "split_chains", "merge_underfull",
-    "update_heavy",
+    "update_heavy", "queue",
 };
 
 cudaError_t dev_malloc(const DevAlloc& da, void** p, size_t bytes)
@@ -157,6 +157,10 @@ int check_err(flix_index* h, cudaStream_t st)
     const uint32_t v = (uint32_t)h->hpin[63];
     if (v) {
         { Ctx c0{h, st}; CK(fill_bytes(c0, h->err, 0, 4)); }
+        if (v == ERR_TIMEOUT) {
+            h->last_error = "a bounded device-side wait gave up (persistent queue)";
+            return FLIX_ETIMEDOUT;
+        }
         h->last_error = "device consistency check failed (code " + std::to_string(v) + ")";
         return FLIX_EINTERNAL;
     }
@@ -862,6 +866,7 @@ void preload_kernels()
     preload_read_kernels();
     preload_update_kernels();
     preload_build_kernels();
+    preload_persist_kernels();
     done.push_back(dev);
 }
 
@@ -929,7 +934,8 @@ int flix_create(const flix_config* cfg, flix_t* out)
         (e = dev_malloc(h->da, reinterpret_cast<void**>(&h->dstate), sizeof(DevState))) ||
         (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
         (e = cudaHostAlloc(&h->hpin, 64 * sizeof(uint64_t), cudaHostAllocMapped)) ||
-        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->hpin_dev), h->hpin, 0))) {
+        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->hpin_dev), h->hpin, 0)) ||
+        (e = cudaEventCreateWithFlags(&h->qstage_ev, cudaEventDisableTiming))) {
         int r = fail(h, e);
         flix_destroy(h);
         return r;
@@ -954,6 +960,9 @@ int flix_destroy(flix_t h)
     dev_free(h->da, h->err);
     dev_free(h->da, h->dstate);
     if (h->hpin) cudaFreeHost(h->hpin);
+    if (h->qstage_ev) cudaEventSynchronize(h->qstage_ev);
+    if (h->qstage) cudaFreeHost(h->qstage);
+    if (h->qstage_ev) cudaEventDestroy(h->qstage_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return FLIX_OK;
@@ -1061,6 +1070,13 @@ int flix_apply_async(flix_t h, const uint8_t* d_ops, const void* d_keys, const v
         do_batch<uint64_t>(h, d_ops, 0, (const uint64_t*)d_keys, (const uint64_t*)d_aux, n, (uint64_t*)d_keys_out,
                            (uint64_t*)d_vals_out, d_found, d_range_off, (uint64_t*)d_range_keys,
                            (uint64_t*)d_range_vals, range_cap, nullptr, d_status, false, S(stream)));
+}
+
+int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us, void* stream)
+{
+    if (!h || (count && !h_batches)) return FLIX_EINVAL;
+    return DISPATCH(apply_queue<uint32_t>(h, h_batches, count, wait_us, S(stream)),
+                    apply_queue<uint64_t>(h, h_batches, count, wait_us, S(stream)));
 }
 
 int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* stream)

@@ -22,7 +22,7 @@ constexpr uint32_t NIL = 0xFFFFFFFFu;
 enum Eff : uint32_t { EFF_NONE = 0, EFF_INS = 1, EFF_DEL = 2, EFF_UPS = 3 };
 
 // Device error word bits (checked at the next synchronising call).
-enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u, ERR_SPIN = 16u, ERR_SORT = 32u };
+enum : uint32_t { ERR_CHAIN = 1u, ERR_BADKEY = 2u, ERR_RANGE = 4u, ERR_STEPS = 8u, ERR_SPIN = 16u, ERR_SORT = 32u, ERR_TIMEOUT = 64u };
 
 template <class K>
 __host__ __device__ constexpr K key_max() { return static_cast<K>(~K(0)); }
@@ -66,7 +66,7 @@ enum KernelId {
     K_VALIDATE, K_FOLD_FLAGS, K_FOLD_INIT, K_FOLD_DEL, K_FOLD_INS, K_FOLD_EMIT, K_FOLD_WRITE,
     K_UPD_COUNT, K_ALLOC_COPY, K_UPD_APPLY, K_ADMIT,
     K_LIVE_COUNT, K_GATHER, K_CUT_KEYS, K_CUT_META, K_DEDUPE, K_STATS, K_FILL, K_SPLIT, K_MERGE, K_HEAVY,
-    K_NUM
+    K_QUEUE, K_NUM
 };
 
 // Device allocations of a handle: the caller's allocator (flix_config) or cudaMalloc/cudaFree.
@@ -177,6 +177,10 @@ struct flix_index {
     size_t ev_used = 0;
     uint64_t launches = 0;
     std::string last_error;
+
+    void* qstage = nullptr;        // pinned staging of a persistent queue's batch descriptors
+    size_t qstage_bytes = 0;
+    cudaEvent_t qstage_ev = nullptr;   // recorded after the staging copy was issued
 };
 
 namespace flix {
@@ -251,6 +255,149 @@ DevIdx<K> dev_view(flix_index* h)
     return d;
 }
 
+// ---- node search helpers (device) ------------------------------------------------------------
+//
+// NC: node data is read through the non-coherent (read-only) cache; a kernel that itself changes
+// nodes between its reads (the persistent queue kernel) passes false and reads coherently.
+
+template <bool NC, class T>
+__device__ __forceinline__ T ld_node(const T* p)
+{
+    if (NC) return __ldg(p);
+    return *p;
+}
+
+// First position in nk[0..sz) whose key is >= q.
+template <class K, bool NC = true>
+__device__ __forceinline__ uint32_t node_lower_bound(const K* __restrict__ nk, uint32_t sz, K q)
+{
+    uint32_t base = 0, len = sz;
+    while (len > 0) {
+        uint32_t half = len >> 1;
+        if (ld_node<NC>(nk + base + half) < q) { base += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return base;
+}
+
+// First position in nk[from..sz) whose key is > q.
+template <class K, bool NC = true>
+__device__ __forceinline__ uint32_t node_upper_bound(const K* __restrict__ nk, uint32_t from, uint32_t sz, K q)
+{
+    uint32_t base = from, len = sz - from;
+    while (len > 0) {
+        uint32_t half = len >> 1;
+        if (!(q < ld_node<NC>(nk + base + half))) { base += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return base;
+}
+
+// From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1);
+// prev = the node walked past last (NIL when the walk ends at the first node).
+template <class K, bool NC = true>
+__device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, uint32_t& node, uint32_t& sz, K& bd,
+                                          uint32_t& nx, uint32_t& prev)
+{
+    prev = NIL;
+    node = ld_node<NC>(ix.head + b);
+    sz = ld_node<NC>(ix.size + node);
+    bd = ld_node<NC>(ix.bound + node);
+    nx = ld_node<NC>(ix.next + node);
+    uint32_t steps = 0;
+    while (q > bd) {
+        if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return false; }
+        prev = node;
+        node = nx;
+        sz = ld_node<NC>(ix.size + node);
+        bd = ld_node<NC>(ix.bound + node);
+        nx = ld_node<NC>(ix.next + node);
+    }
+    return true;
+}
+
+// Result of one point read once its node is known (Sec. 4.1 walk done): pos is the first of the
+// node's sz keys >= q (LOOKUP, SUCC) or > q (PRED), and kpos the key at pos (LOOKUP, SUCC, when
+// pos < sz) or at pos - 1 (PRED, when pos > 0).  A successor past the node continues with the
+// first key of the next non-empty node in chain order, into the following buckets (Sec. 6.5: the
+// smallest key >= q); a predecessor before the node's first key takes the last key of the node
+// walked past, else of the nearest earlier bucket whose chain holds a key.
+template <class K, bool NC = true>
+__device__ __forceinline__ void point_result(const DevIdx<K>& ix, int op, K q, uint32_t b, uint32_t node, uint32_t sz,
+                                             uint32_t nx, uint32_t prev, uint32_t pos, K kpos, K& rk, K& rv,
+                                             uint8_t& f)
+{
+    const uint32_t NS = ix.NS;
+    if (op == FLIX_OP_PRED) {
+        // chain nodes other than a bucket's only node are never empty
+        uint32_t pn = NIL, pp = 0;
+        if (pos > 0) {
+            rk = kpos;
+            rv = ix.vals[(uint64_t)node * NS + pos - 1];
+            f = 1;
+            return;
+        }
+        if (prev != NIL && ix.size[prev] > 0) {
+            pn = prev;
+            pp = ix.size[prev] - 1;
+        } else {
+            uint64_t guard = 0;
+            const uint64_t lim = (uint64_t)ix.cap + ix.nb + 1;
+            for (int64_t bb = (int64_t)b - 1; bb >= 0 && pn == NIL && guard < lim; bb--) {
+                uint32_t x = ix.head[bb];
+                uint32_t last = x;
+                while (x != NIL && guard++ < lim) {
+                    last = x;
+                    x = ix.next[x];
+                }
+                const uint32_t ls = ix.size[last];
+                if (ls > 0) {
+                    pn = last;
+                    pp = ls - 1;
+                }
+            }
+        }
+        if (pn != NIL) {
+            rk = ix.keys[(uint64_t)pn * NS + pp];
+            rv = ix.vals[(uint64_t)pn * NS + pp];
+            f = 1;
+        }
+        return;
+    }
+    if (op == FLIX_OP_LOOKUP) {
+        if (pos < sz && kpos == q) {
+            rk = q;
+            rv = ld_node<NC>(ix.vals + (uint64_t)node * NS + pos);
+            f = 1;
+        }
+        return;
+    }
+    if (pos < sz) {
+        rk = kpos;
+        rv = ld_node<NC>(ix.vals + (uint64_t)node * NS + pos);
+        f = 1;
+        return;
+    }
+    // the smallest key >= q is the first key of the next non-empty node in chain order,
+    // continuing into the following buckets
+    uint32_t n2 = nx;
+    uint64_t bb = b;
+    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
+        if (n2 == NIL) {
+            if (++bb >= ix.nb) break;
+            n2 = ix.head[bb];
+            continue;
+        }
+        if (ix.size[n2] > 0) {
+            rk = ix.keys[(uint64_t)n2 * NS];
+            rv = ix.vals[(uint64_t)n2 * NS];
+            f = 1;
+            break;
+        }
+        n2 = ix.next[n2];
+    }
+}
+
 // Read up to 8 device values (4 or 8 bytes each) into h->hpin[word0 + i] and synchronise the stream
 // (flix_capi.cu); returns a FLIX_ status.
 int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
@@ -264,6 +411,11 @@ void preload_sort_kernels();
 void preload_read_kernels();
 void preload_update_kernels();
 void preload_build_kernels();
+void preload_persist_kernels();
+
+// The persistent queue of small mixed batches (flix_persist.cu).
+template <class K>
+int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wait_us, cudaStream_t st);
 
 // Device fills and small copies as kernels on the call's stream (flix_capi.cu): a cudaMemsetAsync
 // or cudaMemcpyAsync may be carried out by a copy engine, where it would wait behind bulk transfers

@@ -140,55 +140,6 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
         for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS) off[a0 + t + 1] = (uint32_t)(b0 + sout[PT_TILE - 1 - t]);
 }
 
-// First position in nk[0..sz) whose key is >= q.
-template <class K>
-__device__ __forceinline__ uint32_t node_lower_bound(const K* __restrict__ nk, uint32_t sz, K q)
-{
-    uint32_t base = 0, len = sz;
-    while (len > 0) {
-        uint32_t half = len >> 1;
-        if (__ldg(nk + base + half) < q) { base += half + 1; len -= half + 1; }
-        else len = half;
-    }
-    return base;
-}
-
-// First position in nk[from..sz) whose key is > q.
-template <class K>
-__device__ __forceinline__ uint32_t node_upper_bound(const K* __restrict__ nk, uint32_t from, uint32_t sz, K q)
-{
-    uint32_t base = from, len = sz - from;
-    while (len > 0) {
-        uint32_t half = len >> 1;
-        if (!(q < __ldg(nk + base + half))) { base += half + 1; len -= half + 1; }
-        else len = half;
-    }
-    return base;
-}
-
-// From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1);
-// prev = the node walked past last (NIL when the walk ends at the first node).
-template <class K>
-__device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, uint32_t& node, uint32_t& sz, K& bd,
-                                          uint32_t& nx, uint32_t& prev)
-{
-    prev = NIL;
-    node = __ldg(ix.head + b);
-    sz = __ldg(ix.size + node);
-    bd = __ldg(ix.bound + node);
-    nx = __ldg(ix.next + node);
-    uint32_t steps = 0;
-    while (q > bd) {
-        if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return false; }
-        prev = node;
-        node = nx;
-        sz = __ldg(ix.size + node);
-        bd = __ldg(ix.bound + node);
-        nx = __ldg(ix.next + node);
-    }
-    return true;
-}
-
 // Windowed result delivery (see read_point): window regions of the results and their offsets,
 // passed by value.
 constexpr uint32_t RP_MAX_WIN = 256;
@@ -201,88 +152,6 @@ struct ReadWin {
     K* rv;
     uint8_t* rf;
 };
-
-// Result of one point read once its node is known (Sec. 4.1 walk done): pos is the first of the
-// node's sz keys >= q (LOOKUP, SUCC) or > q (PRED), and kpos the key at pos (LOOKUP, SUCC, when
-// pos < sz) or at pos - 1 (PRED, when pos > 0).  A successor past the node continues with the
-// first key of the next non-empty node in chain order, into the following buckets (Sec. 6.5: the
-// smallest key >= q); a predecessor before the node's first key takes the last key of the node
-// walked past, else of the nearest earlier bucket whose chain holds a key.
-template <class K>
-__device__ __forceinline__ void point_result(const DevIdx<K>& ix, int op, K q, uint32_t b, uint32_t node, uint32_t sz,
-                                             uint32_t nx, uint32_t prev, uint32_t pos, K kpos, K& rk, K& rv,
-                                             uint8_t& f)
-{
-    const uint32_t NS = ix.NS;
-    if (op == FLIX_OP_PRED) {
-        // chain nodes other than a bucket's only node are never empty
-        uint32_t pn = NIL, pp = 0;
-        if (pos > 0) {
-            rk = kpos;
-            rv = ix.vals[(uint64_t)node * NS + pos - 1];
-            f = 1;
-            return;
-        }
-        if (prev != NIL && ix.size[prev] > 0) {
-            pn = prev;
-            pp = ix.size[prev] - 1;
-        } else {
-            uint64_t guard = 0;
-            const uint64_t lim = (uint64_t)ix.cap + ix.nb + 1;
-            for (int64_t bb = (int64_t)b - 1; bb >= 0 && pn == NIL && guard < lim; bb--) {
-                uint32_t x = ix.head[bb];
-                uint32_t last = x;
-                while (x != NIL && guard++ < lim) {
-                    last = x;
-                    x = ix.next[x];
-                }
-                const uint32_t ls = ix.size[last];
-                if (ls > 0) {
-                    pn = last;
-                    pp = ls - 1;
-                }
-            }
-        }
-        if (pn != NIL) {
-            rk = ix.keys[(uint64_t)pn * NS + pp];
-            rv = ix.vals[(uint64_t)pn * NS + pp];
-            f = 1;
-        }
-        return;
-    }
-    if (op == FLIX_OP_LOOKUP) {
-        if (pos < sz && kpos == q) {
-            rk = q;
-            rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
-            f = 1;
-        }
-        return;
-    }
-    if (pos < sz) {
-        rk = kpos;
-        rv = __ldg(ix.vals + (uint64_t)node * NS + pos);
-        f = 1;
-        return;
-    }
-    // the smallest key >= q is the first key of the next non-empty node in chain order,
-    // continuing into the following buckets
-    uint32_t n2 = nx;
-    uint64_t bb = b;
-    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
-        if (n2 == NIL) {
-            if (++bb >= ix.nb) break;
-            n2 = ix.head[bb];
-            continue;
-        }
-        if (ix.size[n2] > 0) {
-            rk = ix.keys[(uint64_t)n2 * NS];
-            rv = ix.vals[(uint64_t)n2 * NS];
-            f = 1;
-            break;
-        }
-        n2 = ix.next[n2];
-    }
-}
 
 // Delivery of one result: to the query's input position, or (win) tagged with it into the next
 // free place of its window's region (offsets per window and block from a count and a scan).

@@ -56,6 +56,17 @@ def _torch_allocator(device):
     return _ALLOC_FN(alloc), _FREE_FN(free)
 
 
+class Batch(ctypes.Structure):
+    """flix_batch: one batch of a persistent queue (device pointers)."""
+    _fields_ = [("ops", ctypes.c_void_p), ("keys", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("keys_out", ctypes.c_void_p), ("vals_out", ctypes.c_void_p), ("found", ctypes.c_void_p),
+                ("range_off", ctypes.c_void_p), ("range_keys", ctypes.c_void_p), ("range_vals", ctypes.c_void_p),
+                ("range_cap", ctypes.c_uint64), ("status", ctypes.c_void_p), ("ready", ctypes.c_void_p)]
+
+
+QUEUE_BATCH_MAX = 2048
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("buckets", "nodes_used", "nodes_free", "pool_nodes", "live_keys",
                                                "max_chain", "node_bytes", "used_bytes", "reserved_bytes")]
@@ -87,6 +98,7 @@ SIGNATURES = {
     "flix_export": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_dump_layout": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "flix_sort_pairs": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "flix_apply_queue": (_INT, [_VP, _VP, _U32, _U32, _VP]),
     "flix_profile_enable": (_INT, [_VP, _INT]),
     "flix_profile_reset": (_INT, [_VP]),
     "flix_profile_read": (_INT, [_VP, _U32, _VP, _VP, _VP, _VP, _VP]),
@@ -317,6 +329,24 @@ class Index:
                                        _ptr(out["vals"]), _ptr(out["found"]), _ptr(out["range_off"]),
                                        _ptr(out["range_keys"]), _ptr(out["range_vals"]), cap, _ptr(out["status"]),
                                        _stream(stream)), "flix_apply_async", self._h)
+
+    def apply_queue(self, batches, wait_us: int = 2_000_000, stream=None):
+        """Run a queue of small mixed batches in one persistent kernel (flix_apply_queue).  batches:
+        list of dicts with device tensors ops, keys, aux and outputs keys_out, vals_out, found,
+        range_off (n+1), range_keys, range_vals, status (4 x int64), and optionally `ready` (an int32
+        device word the kernel waits on).  Asynchronous: read the outputs once the stream has run."""
+        arr = (Batch * len(batches))()
+        for i, b in enumerate(batches):
+            o = self._dev(b["ops"], torch.uint8)
+            k, a = self._dev(b["keys"]), self._dev(b["aux"])
+            arr[i] = Batch(_ptr(o).value if o.numel() else None, _ptr(k).value if k.numel() else None,
+                           _ptr(a).value if a.numel() else None, k.numel(),
+                           *(_ptr(b[f]).value if b.get(f) is not None else None
+                             for f in ("keys_out", "vals_out", "found", "range_off", "range_keys", "range_vals")),
+                           b["range_keys"].numel() if b.get("range_keys") is not None else 0,
+                           _ptr(b["status"]).value, _ptr(b["ready"]).value if b.get("ready") is not None else None)
+        _check(load().flix_apply_queue(self._h, arr, len(batches), wait_us, _stream(stream)), "flix_apply_queue",
+               self._h)
 
     def reserve(self, batch_max: int, free_nodes_min: int = 0, stream=None):
         _check(load().flix_reserve(self._h, batch_max, free_nodes_min, _stream(stream)), "flix_reserve", self._h)

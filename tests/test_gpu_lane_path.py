@@ -19,10 +19,14 @@ from tests.gpu_util import compare_contents, compare_layout, oracle_pair
 pytestmark = pytest.mark.gpu
 
 
+MASK = (1 << 62) - 1
+
+
 def light_batch(load, NS, rng, nbuckets):
     """Updates for the first nbuckets buckets of a build of `load` (sorted, p = NS/2 keys each):
     bucket i gets 1 + i % 12 updates drawn from its own key range."""
     p = NS // 2
+    nbuckets = min(nbuckets, len(load) // p - 1)
     keys, ops, vals = [], [], []
     for i in range(nbuckets):
         lo = int(load[i * p]) if i > 0 else 0
@@ -31,14 +35,14 @@ def light_batch(load, NS, rng, nbuckets):
         for u in range(1 + i % 12):
             kind = rng.integers(0, 5)
             if kind == 0 or kind == 4:                    # fresh insert inside the bucket's range
-                k = int(rng.integers(lo + 1, hi)) if hi - lo > 2 else lo + 1
-                keys.append(k); ops.append(W.OP_INSERT); vals.append(k * 3 + 1)
+                k = int(rng.integers(lo + 1, hi, dtype=np.uint64)) if hi - lo > 2 else lo + 1
+                keys.append(k); ops.append(W.OP_INSERT); vals.append((k * 3 + 1) & MASK)
             elif kind == 1:                               # delete of a present key
                 k = present[int(rng.integers(0, p))]
                 keys.append(k); ops.append(W.OP_DELETE); vals.append(0)
             elif kind == 2:                               # upsert: delete then insert the same key
                 k = present[int(rng.integers(0, p))]
-                keys += [k, k]; ops += [W.OP_DELETE, W.OP_INSERT]; vals += [0, k * 5 + 2]
+                keys += [k, k]; ops += [W.OP_DELETE, W.OP_INSERT]; vals += [0, (k * 5 + 2) & MASK]
             else:                                         # insert of a present key (no-op)
                 k = present[int(rng.integers(0, p))]
                 keys.append(k); ops.append(W.OP_INSERT); vals.append(7)
