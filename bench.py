@@ -406,7 +406,7 @@ def main():
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "update_heavy", "xy", "light"],
                     help="plain: the read-scale step (default); batched: mixed-batch stream through CUDA "
                          "graphs vs plain launches; served: continuous batching under Poisson arrivals")
-    ap.add_argument("--batches", type=int, default=300, help="batched form: stream length")
+    ap.add_argument("--batches", type=int, default=10000, help="batched form: stream length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
@@ -610,92 +610,155 @@ def main():
 # Batched and served forms (their own JSON lines; the default run is the plain read-scale step)
 # ------------------------------------------------------------------------------------------------
 
-def bench_batched(args):
-    """Uneven mixed batches (sizes 2^8..2^22, 60/15/5/10/10 lookup/successor/range/insert/delete) on a
-    2^27-key uint64 index: plain per-batch flix_apply vs the batched form (CUDA graph per size class,
-    device-side admission).  Node size and sort variant come from the autotuner on a held-out seed."""
-    import torch
-    import paper_2604_16725_gb300 as fx
-    from paper_2604_16725_gb300.batched import BatchedRunner
-    from paper_2604_16725_gb300.tune import autotune
-    torch.cuda.set_device(0)
-    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
-    # autotune on a held-out seed, scaled-down preload
-    held = W.mixed_stream(seed=4999, n_preload=1 << 22, n_batches=40, lo_exp=8, hi_exp=20)
-    hb = [(torch.from_numpy(o).cuda(), torch.from_numpy(k.view(np.int64)).cuda(),
-           torch.from_numpy(a.view(np.int64)).cuda()) for o, k, a in held["batches"]()]
-    tune = autotune(64, held["preload_keys"], held["preload_vals"], hb, range_per_op=64, log=log)
-    NS, sv = tune["node_size"], tune["sort_variant"]
-    log("autotune: NS=%d sort_variant=%d" % (NS, sv))
-    del hb
-    s = W.mixed_stream(seed=4000, n_preload=1 << args.log_load if args.log_load != LOG_LOAD else 1 << 27,
-                       n_batches=args.batches)
-    batches = []
-    for o, k, a in s["batches"]():
-        batches.append((torch.from_numpy(o).cuda(), torch.from_numpy(k.view(np.int64)).cuda(),
-                        torch.from_numpy(a.view(np.int64)).cuda()))
+def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log, queue_depth=32):
+    """One stream through plain per-batch flix_apply, the graph path and the persistent path.
+    Per batch: latency from submission to completion (CUDA events); throughput = ops / wall time."""
     n_ops = sum(int(k.numel()) for _, k, _ in batches)
-    pk = torch.from_numpy(s["preload_keys"].view(np.int64)).cuda()
-    pv = torch.from_numpy(s["preload_vals"].view(np.int64)).cuda()
-    max_b = max(int(k.numel()) for _, k, _ in batches)
+    sizes = np.array([int(k.numel()) for _, k, _ in batches])
+    max_b = int(sizes.max())
+    # free nodes held for the asynchronous paths: new nodes hold at least NS/2 keys, inserts are a
+    # tenth of the ops, and the runner restructures every 50 batches when nodes exceed 2x buckets
+    free_min = min(1 << 24, n_ops // 10 // max(NS // 4, 1) + (1 << 20))
     results = {}
     finals = {}
-    for mode in ("plain", "batched"):
-        idx = fx.Index(key_bits=64, node_size=NS, sort_variant=sv)
-        idx.bulk_load(pk, pv)
+    for mode in ("plain", "graph", "persistent"):
+        idx = fx.Index(key_bits=64, node_size=NS, sort_variant=sv, bucket_threads=bt)
+        idx.bulk_load(pre_k, pre_v)
+        log("%s: device memory free %.1f GB" % (mode, torch.cuda.mem_get_info()[0] / 1e9))
         st = torch.cuda.Stream()
-        per = []
-        if mode == "batched":
-            run = BatchedRunner(idx, max_batch=max_b, min_log=8, range_per_op=64, free_nodes_min=n_ops // 4 + (1 << 20))
+        run = None
+        if mode != "plain":
+            run = BatchedRunner(idx, max_batch=max_b, min_log=8, range_per_op=64,
+                                free_nodes_min=free_min, queue_depth=queue_depth if mode == "persistent" else 0)
             for o, k, a in batches:
-                run.graph_for(run.size_for(int(k.numel())))
+                if mode == "graph" or int(k.numel()) > fx.QUEUE_BATCH_MAX:
+                    run.graph_for(run.size_for(int(k.numel())))
             st = run.stream
         else:
-            idx.reserve(max_b, n_ops // 4 + (1 << 20))
+            idx.reserve(max_b, free_min)
         torch.cuda.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(batches) + 1)]
+        sub = [torch.cuda.Event(enable_timing=True) for _ in batches]
+        done = [None] * len(batches)
+        pend = []
+
+        def flushed():
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(st)
+            for j in pend:
+                done[j] = ev
+            pend.clear()
+
+        if run is not None:
+            run.on_flush = flushed
         t0 = time.perf_counter()
-        evs[0].record(st)
         for i, (o, k, a) in enumerate(batches):
-            if mode == "batched":
-                run.run(o, k, a)
-            else:
-                with torch.cuda.stream(st):
-                    idx.apply(o, k, a, range_capacity=64 * int(k.numel()), stream=st)
-            evs[i + 1].record(st)
+            sub[i].record(st)
+            queued = mode == "persistent" and int(k.numel()) <= fx.QUEUE_BATCH_MAX
+            if queued:
+                pend.append(i)
+            try:
+                if run is None:
+                    with torch.cuda.stream(st):
+                        idx.apply(o, k, a, range_capacity=max(64 * int(k.numel()), 1 << 18), stream=st)
+                else:
+                    run.run(o, k, a)
+            except fx.FlixError:
+                free_b, total_b = torch.cuda.mem_get_info()
+                log("%s: batch %d of %d ops failed; index %s; device memory free %.1f of %.1f GB"
+                    % (mode, i, int(k.numel()), idx.stats(stream=st), free_b / 1e9, total_b / 1e9))
+                raise
+            if not queued:
+                done[i] = torch.cuda.Event(enable_timing=True)
+                done[i].record(st)
             if (i + 1) % 50 == 0:
-                if mode == "batched":
+                if run is not None:
                     run.restructure_if_needed()
                 else:
                     s_ = idx.stats(stream=st)
                     if s_["nodes_used"] > 2 * s_["buckets"] or s_["max_chain"] > 64:
                         idx.restructure(stream=st)
-        if mode == "batched":
+        if run is not None:
             run.synchronize()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(batches))]
-        sizes = np.array([int(k.numel()) for _, k, _ in batches])
-        small = sizes <= 4096
+        lat = np.array([sub[i].elapsed_time(done[i]) for i in range(len(batches))])
+        small = sizes <= fx.QUEUE_BATCH_MAX
         results[mode] = {"mops": n_ops / wall / 1e6, "wall_s": wall,
-                         "batch_ms_p50": float(np.median(per)), "batch_ms_p99": float(np.percentile(per, 99)),
-                         "small_batches_mops": float(sizes[small].sum() / (np.array(per)[small].sum() * 1e-3) / 1e6)
-                         if small.any() else None}
+                         "batch_ms_p50": float(np.median(lat)), "batch_ms_p99": float(np.percentile(lat, 99)),
+                         "small_batch_ms_p50": float(np.median(lat[small])) if small.any() else None,
+                         "small_batch_ms_p99": float(np.percentile(lat[small], 99)) if small.any() else None,
+                         "queues": run.queues if run is not None else 0}
         k_, v_ = idx.export()
         finals[mode] = (k_.cpu(), v_.cpu())
-        log("%s: %.1f Mops/s" % (mode, results[mode]["mops"]))
+        log("%s: %s" % (mode, results[mode]))
+        del run
         idx.close()
         torch.cuda.empty_cache()
-    same_state = bool(torch.equal(finals["plain"][0], finals["batched"][0]) and
-                      torch.equal(finals["plain"][1], finals["batched"][1]))
-    line = {"form": "batched", "metric": METRIC, "value": results["batched"]["mops"], "unit": "Mops/s",
+    results["_finals"] = finals
+    return results
+
+
+def bench_batched(args):
+    """Config 4's stream: a 2^27-key uint64 index and --batches (default 10,000) uneven mixed batches,
+    sizes log-uniform 2^8..2^22 (about 4.3e9 ops), 60/15/5/10/10 lookup/successor/range/insert/
+    delete, generated on the GPU (workload.device: gen.mixed_stream's recipe and key universe).
+    Three paths over the same batches: plain per-batch flix_apply; the batched form with a CUDA
+    graph per size class; and the batched form with the persistent kernel taking queues of up to
+    32 batches of at most 2048 ops (larger batches take the graphs).  Node size, sort variant and
+    bucket threads come from the autotuner on a held-out seed.  Per batch: latency from submission
+    to completion (CUDA events); throughput = all ops / wall time."""
+    import torch
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.batched import BatchedRunner
+    from paper_2604_16725_gb300.tune import autotune
+    from workload import device as WD
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    held = WD.mixed_stream_device(seed=4999, n_preload=1 << 22, n_batches=24, lo_exp=8, hi_exp=20)
+    hb = list(held["batches"]())
+    tune = autotune(64, held["preload_keys"], held["preload_vals"], hb, range_per_op=64, log=log)
+    NS, sv, bt = tune["node_size"], tune["sort_variant"], tune.get("bucket_threads", 0)
+    log("autotune: NS=%d sort_variant=%d bucket_threads=%d" % (NS, sv, bt))
+    del hb, held
+    n_pre = 1 << args.log_load if args.log_load != LOG_LOAD else 1 << 27
+    s = WD.mixed_stream_device(seed=4000, n_preload=n_pre, n_batches=args.batches)
+    batches = list(s["batches"]())
+    torch.cuda.synchronize()
+    n_ops = sum(int(k.numel()) for _, k, _ in batches)
+    sizes = np.array([int(k.numel()) for _, k, _ in batches])
+    max_b = int(sizes.max())
+    log("stream: %d batches, %d ops" % (len(batches), n_ops))
+    results = run_stream(torch, fx, BatchedRunner, batches, s["preload_keys"], s["preload_vals"], NS, sv, bt, log)
+    finals = results.pop("_finals")
+    # a stream of small batches only (2^4..2^11 ops: every batch fits the persistent kernel's queue)
+    ss = WD.mixed_stream_device(seed=4100, n_preload=n_pre, n_batches=min(args.batches, 3000), lo_exp=4, hi_exp=11)
+    sbatches = list(ss["batches"]())
+    small_res = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
+                           queue_depth=8)
+    small_finals = small_res.pop("_finals")
+    small_same = all(bool(torch.equal(small_finals["plain"][0], small_finals[m][0]) and
+                          torch.equal(small_finals["plain"][1], small_finals[m][1])) for m in ("graph", "persistent"))
+    sizes = np.array([int(k.numel()) for _, k, _ in batches])
+    small = sizes <= fx.QUEUE_BATCH_MAX
+    same_state = all(bool(torch.equal(finals["plain"][0], finals[m][0]) and torch.equal(finals["plain"][1], finals[m][1]))
+                     for m in ("graph", "persistent"))
+    best = max(("graph", "persistent"), key=lambda m: results[m]["mops"])
+    line = {"form": "batched", "metric": METRIC, "value": results[best]["mops"], "unit": "Mops/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "batched: 2^27 uint64 keys preloaded; %d mixed batches, sizes log-uniform "
-                                   "2^8..2^22, 60/15/5/10/10 lookup/successor/range(1-1000)/insert/delete" % len(batches),
-                       "node_size": NS, "sort_variant": sv, "ops": n_ops},
-            "plain": results["plain"], "batched": results["batched"],
-            "speedup_vs_plain": results["batched"]["mops"] / results["plain"]["mops"],
-            "final_state_equal": same_state, "autotune": tune["table"]}
+            "config": {"workload": "batched: %d uint64 keys preloaded; %d mixed batches, sizes log-uniform "
+                                   "2^8..2^22, 60/15/5/10/10 lookup/successor/range(1-1000)/insert/delete, "
+                                   "generated on the GPU" % (n_pre, len(batches)),
+                       "node_size": NS, "sort_variant": sv, "bucket_threads": bt, "ops": n_ops,
+                       "small_batches": int(small.sum())},
+            "plain": results["plain"], "graph": results["graph"], "persistent": results["persistent"],
+            "best_batched_path": best, "speedup_vs_plain": results[best]["mops"] / results["plain"]["mops"],
+            "final_state_equal": same_state,
+            "small_batch_stream": {"workload": "%d batches of log-uniform 2^4..2^11 ops, same mix, same index size; "
+                                               "persistent queue depth 8" % len(sbatches),
+                                   "ops": sum(int(k.numel()) for _, k, _ in sbatches),
+                                   "plain": small_res["plain"], "graph": small_res["graph"],
+                                   "persistent": small_res["persistent"], "final_state_equal": small_same},
+            "autotune": tune["table"]}
     print(json.dumps(line))
     return 0
 

@@ -10,6 +10,12 @@ one device word that the runner checks every `check_every` batches.
 
 Graphs hold the index's pool pointers and bucket count, so they are re-captured after a
 restructure, a bulk load or pool growth (`invalidate`; `restructure_if_needed` does both).
+
+With `queue_depth` > 0 (the persistent path), batches of at most QUEUE_BATCH_MAX ops are not
+launched one by one: their inputs go into one of `queue_depth` slots, and a full queue (or a larger
+batch, or a check) runs every queued batch in order through ONE launch of the library's persistent
+kernel (flix_apply_queue).  A queued batch's results are in its slot once that launch has run, and
+stay there until the slot is reused `queue_depth` batches later.
 """
 from __future__ import annotations
 
@@ -17,7 +23,7 @@ import math
 
 import torch
 
-from .flix import OP_NOP, FlixError, Index
+from .flix import OP_NOP, QUEUE_BATCH_MAX, FlixError, Index
 
 
 def class_sizes(min_log: int, max_log: int, per_octave: int = 4, align: int = 256):
@@ -34,7 +40,7 @@ class BatchedRunner:
     """Run mixed batches (device tensors ops/keys/aux) on `idx` through per-size-class CUDA graphs."""
 
     def __init__(self, idx: Index, max_batch: int, min_log: int = 8, range_per_op: int = 64,
-                 free_nodes_min: int = 0, check_every: int = 64, per_octave: int = 4):
+                 free_nodes_min: int = 0, check_every: int = 64, per_octave: int = 4, queue_depth: int = 0):
         self.idx = idx
         self.min_log = min_log
         self.max_log = max(min_log, math.ceil(math.log2(max(max_batch, 2))))
@@ -54,6 +60,23 @@ class BatchedRunner:
                         status=torch.zeros(4, dtype=torch.int64, device=dev))
         self.graphs: dict[int, torch.cuda.CUDAGraph] = {}
         self.batches = 0
+        # persistent path: slots of queued small batches
+        self.queue_depth = queue_depth
+        self.pending = []
+        self.slots = []
+        Q = QUEUE_BATCH_MAX
+        for _ in range(queue_depth):
+            self.slots.append(dict(ops=torch.zeros(Q, dtype=torch.uint8, device=dev), keys=torch.empty(Q, dtype=dt, device=dev),
+                                   aux=torch.empty(Q, dtype=dt, device=dev), keys_out=torch.empty(Q, dtype=dt, device=dev),
+                                   vals_out=torch.empty(Q, dtype=dt, device=dev),
+                                   found=torch.empty(Q, dtype=torch.uint8, device=dev),
+                                   range_off=torch.empty(Q + 1, dtype=torch.int64, device=dev),
+                                   range_keys=torch.empty(max(range_per_op * Q, 1), dtype=dt, device=dev),
+                                   range_vals=torch.empty(max(range_per_op * Q, 1), dtype=dt, device=dev),
+                                   status=torch.zeros(4, dtype=torch.int64, device=dev)))
+        self.next_slot = 0
+        self.queues = 0
+        self.on_flush = None      # called on self.stream right after each queue launch
         self.flags = torch.zeros(1, dtype=torch.int64, device=dev)   # OR of every batch's status flags
         idx.reserve(S, free_nodes_min, stream=self.stream)
         # run the flag accumulation once now: a first use inside the stream of batches would load
@@ -94,10 +117,47 @@ class BatchedRunner:
         """Drop every captured graph (after a restructure, a bulk load or pool growth)."""
         self.graphs.clear()
 
+    def flush(self):
+        """Run every queued small batch through one persistent-kernel launch on `self.stream`."""
+        if not self.pending:
+            return
+        with torch.cuda.stream(self.stream):
+            self.idx.apply_queue(self.pending, stream=self.stream)
+            if self.on_flush is not None:
+                self.on_flush()
+            for b in self.pending:
+                self.flags.bitwise_or_(b["status"][:1])
+        self.pending = []
+        self.queues += 1
+
+    def _enqueue(self, ops, keys, aux, n):
+        slot = self.slots[self.next_slot]
+        self.next_slot = (self.next_slot + 1) % self.queue_depth
+        with torch.cuda.stream(self.stream):
+            slot["ops"][:n].copy_(ops, non_blocking=True)
+            slot["keys"][:n].copy_(keys.view(slot["keys"].dtype), non_blocking=True)
+            slot["aux"][:n].copy_(aux.view(slot["aux"].dtype), non_blocking=True)
+        b = dict(ops=slot["ops"][:n], keys=slot["keys"][:n], aux=slot["aux"][:n], keys_out=slot["keys_out"],
+                 vals_out=slot["vals_out"], found=slot["found"], range_off=slot["range_off"][:n + 1],
+                 range_keys=slot["range_keys"], range_vals=slot["range_vals"], status=slot["status"])
+        self.pending.append(b)
+        self.batches += 1
+        if len(self.pending) == self.queue_depth:
+            self.flush()
+        if self.batches % self.check_every == 0:
+            self.check()
+        return dict(keys=slot["keys_out"][:n], vals=slot["vals_out"][:n], found=slot["found"][:n],
+                    range_off=slot["range_off"][:n + 1], range_keys=slot["range_keys"],
+                    range_vals=slot["range_vals"], status=slot["status"])
+
     def run(self, ops, keys, aux):
         """Enqueue one batch on `self.stream`; returns views of its results (valid once the stream
-        reaches them, until the next batch)."""
+        reaches them, until the next batch; on the persistent path, once its queue has run and until
+        its slot is reused)."""
         n = int(keys.numel())
+        if self.queue_depth and n <= QUEUE_BATCH_MAX:
+            return self._enqueue(ops, keys, aux, n)
+        self.flush()
         s = self.size_for(n)
         g = self.graph_for(s)
         with torch.cuda.stream(self.stream):
@@ -118,7 +178,9 @@ class BatchedRunner:
                     range_keys=o["range_keys"], range_vals=o["range_vals"], status=o["status"])
 
     def check(self):
-        """Synchronise and raise if a batch since the last check was not admitted."""
+        """Run the queued batches, synchronise and raise if a batch since the last check was not
+        admitted."""
+        self.flush()
         self.stream.synchronize()
         f = int(self.flags.item())
         if f:

@@ -122,3 +122,50 @@ def test_async_admission_rejects_without_changes():
     after2 = idx.dump_layout()
     for f in before:
         same(before[f], after2[f], "unchanged " + f)
+
+
+@pytest.mark.parametrize("kw,NS", [(64, 16), (32, 32)])
+def test_batched_persistent_queue_matches_oracle(kw, NS):
+    """The runner's persistent path: batches of at most 2048 ops queue up and run by one launch of the
+    persistent kernel per 8 batches; larger ones flush the queue and take the graph path.  Every
+    output of every batch and the final contents against the oracle, across a restructure."""
+    import paper_2604_16725_gb300 as fx
+    from paper_2604_16725_gb300.batched import BatchedRunner
+    depth = 8
+    s = W.mixed_stream(seed=4700 + kw, kw=kw, n_preload=1 << 15, n_batches=48, lo_exp=3, hi_exp=12.5, max_len=100)
+    idx = fx.Index(key_bits=kw, node_size=NS)
+    idx.bulk_load(s["preload_keys"], s["preload_vals"])
+    mp = oracle.Map(kw)
+    mp.bulk_load(s["preload_keys"], s["preload_vals"])
+    run = BatchedRunner(idx, max_batch=1 << 13, min_log=4, range_per_op=128, free_nodes_min=1 << 15,
+                        queue_depth=depth)
+    batches = list(s["batches"]())
+    assert any(k.size > 2048 for _, k, _ in batches) and any(k.size <= 2048 for _, k, _ in batches)
+    for g0 in range(0, len(batches), depth):
+        group = batches[g0:g0 + depth]
+        views = []
+        for ops, keys, aux in group:
+            r = run.run(idx._dev(ops, torch.uint8), idx._dev(keys), idx._dev(aux))
+            if keys.size > 2048:            # graph path: its views are reused by the next graph batch
+                with torch.cuda.stream(run.stream):
+                    r = {k: v.clone() for k, v in r.items()}
+            views.append(r)
+        run.check()
+        for b, ((ops, keys, aux), got) in enumerate(zip(group, views)):
+            e, st = mp.apply(ops, keys, aux)
+            assert st == 0 and int(got["status"][0]) == 0
+            tag = "batch %d" % (g0 + b)
+            same(np_of(got["keys"], kw), e["keys"], tag + " keys")
+            same(np_of(got["vals"], kw), e["vals"], tag + " vals")
+            same(got["found"].cpu().numpy(), e["found"], tag + " found")
+            off = got["range_off"].cpu().numpy().view(np.uint64)
+            same(off, e["range_off"], tag + " range_off")
+            t = int(off[-1])
+            same(np_of(got["range_keys"][:t], kw), e["range_keys"], tag + " range_keys")
+        if g0 == 24:
+            run.restructure_if_needed(max_nodes_per_bucket=0.0)        # forces a restructure
+    assert run.queues > 0
+    k, v = idx.export()
+    ek, ev = mp.export()
+    same(np_of(k, kw), ek, "final keys")
+    same(np_of(v, kw), ev, "final vals")

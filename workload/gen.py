@@ -306,13 +306,14 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
 
     Hits and deletes draw from the preload plus inserts generated earlier in the stream (stale keys
     are allowed: deleting an absent key is a no-op).  Range queries take lo from the universe and
-    hi = lo + span where span is a multiple of the mean key gap, so they cover about 1..max_len keys.
+    hi = lo + span where span is 1..max_len times the mean gap between the keys generated so far
+    (preload and earlier inserts), so they cover at most about max_len stored keys however far the
+    stream has grown the index.
     Yields (ops, keys, aux) per batch; preload arrays come first via the 'preload' entry.
     """
     dt = _kdt(kw)
     pre = universe(kw, seed, 0, n_preload)
     sizes = log_uniform_sizes(seed, 1, n_batches, lo_exp, hi_exp)
-    gap = (1 << kw) // max(n_preload, 1)
     cum = np.cumsum(np.array(mix) / np.sum(mix))
 
     def batches():
@@ -341,6 +342,7 @@ def mixed_stream(seed: int = 4000, kw: int = 64, n_preload: int = 1 << 27, n_bat
             keys = kk.astype(dt)
             aux[is_ins] = values_for(kw, fresh, salt=b + 7)
             is_rng = ops == OP_RANGE
+            gap = (1 << kw) // max(n_preload + n_ins, 1)
             span = ((w[2 * m:] % np.uint64(max_len)).astype(np.uint64) + np.uint64(1)) * np.uint64(gap)
             with np.errstate(over="ignore"):
                 hi = kk + span
