@@ -610,7 +610,8 @@ def main():
 # Batched and served forms (their own JSON lines; the default run is the plain read-scale step)
 # ------------------------------------------------------------------------------------------------
 
-def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log, queue_depth=32):
+def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log, queue_depth=32,
+               modes=("plain", "graph", "persistent")):
     """One stream through plain per-batch flix_apply, the graph path and the persistent path.
     Per batch: latency from submission to completion (CUDA events); throughput = ops / wall time."""
     n_ops = sum(int(k.numel()) for _, k, _ in batches)
@@ -621,7 +622,7 @@ def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log,
     free_min = min(1 << 24, n_ops // 10 // max(NS // 4, 1) + (1 << 20))
     results = {}
     finals = {}
-    for mode in ("plain", "graph", "persistent"):
+    for mode in modes:
         idx = fx.Index(key_bits=64, node_size=NS, sort_variant=sv, bucket_threads=bt)
         idx.bulk_load(pre_k, pre_v)
         log("%s: device memory free %.1f GB" % (mode, torch.cuda.mem_get_info()[0] / 1e9))
@@ -734,10 +735,16 @@ def bench_batched(args):
     ss = WD.mixed_stream_device(seed=4100, n_preload=n_pre, n_batches=min(args.batches, 3000), lo_exp=4, hi_exp=11)
     sbatches = list(ss["batches"]())
     small_res = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
-                           queue_depth=8)
+                           queue_depth=2)
     small_finals = small_res.pop("_finals")
+    deep = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
+                      queue_depth=16, modes=("persistent",))
+    deep_finals = deep.pop("_finals")
+    small_res["persistent_queue16"] = deep["persistent"]
+    small_finals["persistent_queue16"] = deep_finals["persistent"]
     small_same = all(bool(torch.equal(small_finals["plain"][0], small_finals[m][0]) and
-                          torch.equal(small_finals["plain"][1], small_finals[m][1])) for m in ("graph", "persistent"))
+                          torch.equal(small_finals["plain"][1], small_finals[m][1]))
+                     for m in ("graph", "persistent", "persistent_queue16"))
     sizes = np.array([int(k.numel()) for _, k, _ in batches])
     small = sizes <= fx.QUEUE_BATCH_MAX
     same_state = all(bool(torch.equal(finals["plain"][0], finals[m][0]) and torch.equal(finals["plain"][1], finals[m][1]))
@@ -754,10 +761,12 @@ def bench_batched(args):
             "best_batched_path": best, "speedup_vs_plain": results[best]["mops"] / results["plain"]["mops"],
             "final_state_equal": same_state,
             "small_batch_stream": {"workload": "%d batches of log-uniform 2^4..2^11 ops, same mix, same index size; "
-                                               "persistent queue depth 8" % len(sbatches),
+                                               "persistent queue depth 2 (and 16)" % len(sbatches),
                                    "ops": sum(int(k.numel()) for _, k, _ in sbatches),
                                    "plain": small_res["plain"], "graph": small_res["graph"],
-                                   "persistent": small_res["persistent"], "final_state_equal": small_same},
+                                   "persistent": small_res["persistent"],
+                                   "persistent_queue16": small_res["persistent_queue16"],
+                                   "final_state_equal": small_same},
             "autotune": tune["table"]}
     print(json.dumps(line))
     return 0

@@ -271,8 +271,10 @@ typedef struct {
  * returns FLIX_ETIMEDOUT.  h_batches is a HOST array of count descriptors (copied before the
  * launch).  Asynchronous; not for stream capture.  The chain split and underfull merge policies
  * are not applied on this path (FLIX_ENOTIMPL when one is configured).  Returns FLIX_EINVAL for a
- * batch larger than FLIX_QUEUE_BATCH_MAX. */
-int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us, void* stream);
+ * batch larger than FLIX_QUEUE_BATCH_MAX.  d_flags_or (optional DEVICE word): every batch's status
+ * flags are OR-ed into it. */
+int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us,
+                     uint64_t* d_flags_or, void* stream);
 
 /* Reserve scratch for batches of up to batch_max ops and grow the pool (if needed) so that at least
  * free_nodes_min nodes are free.  Synchronises.  FLIX_ENOMEM if the device cannot hold it. */

@@ -66,8 +66,7 @@ class BatchedRunner:
         self.slots = []
         Q = QUEUE_BATCH_MAX
         for _ in range(queue_depth):
-            self.slots.append(dict(ops=torch.zeros(Q, dtype=torch.uint8, device=dev), keys=torch.empty(Q, dtype=dt, device=dev),
-                                   aux=torch.empty(Q, dtype=dt, device=dev), keys_out=torch.empty(Q, dtype=dt, device=dev),
+            self.slots.append(dict(keys=torch.empty(0, dtype=dt, device=dev), keys_out=torch.empty(Q, dtype=dt, device=dev),
                                    vals_out=torch.empty(Q, dtype=dt, device=dev),
                                    found=torch.empty(Q, dtype=torch.uint8, device=dev),
                                    range_off=torch.empty(Q + 1, dtype=torch.int64, device=dev),
@@ -122,22 +121,21 @@ class BatchedRunner:
         if not self.pending:
             return
         with torch.cuda.stream(self.stream):
-            self.idx.apply_queue(self.pending, stream=self.stream)
+            self.idx.apply_queue(self.pending, flags_or=self.flags, stream=self.stream)
             if self.on_flush is not None:
                 self.on_flush()
-            for b in self.pending:
-                self.flags.bitwise_or_(b["status"][:1])
         self.pending = []
         self.queues += 1
 
     def _enqueue(self, ops, keys, aux, n):
         slot = self.slots[self.next_slot]
         self.next_slot = (self.next_slot + 1) % self.queue_depth
-        with torch.cuda.stream(self.stream):
-            slot["ops"][:n].copy_(ops, non_blocking=True)
-            slot["keys"][:n].copy_(keys.view(slot["keys"].dtype), non_blocking=True)
-            slot["aux"][:n].copy_(aux.view(slot["aux"].dtype), non_blocking=True)
-        b = dict(ops=slot["ops"][:n], keys=slot["keys"][:n], aux=slot["aux"][:n], keys_out=slot["keys_out"],
+        # the batch's own input tensors go into the queue (held until its launch): no copies
+        dt = slot["keys"].dtype
+        ops, keys, aux = ops.contiguous(), keys.view(dt).contiguous(), aux.view(dt).contiguous()
+        for t in (ops, keys, aux):
+            t.record_stream(self.stream)     # not reused by the allocator before the queue has run
+        b = dict(ops=ops, keys=keys, aux=aux, keys_out=slot["keys_out"],
                  vals_out=slot["vals_out"], found=slot["found"], range_off=slot["range_off"][:n + 1],
                  range_keys=slot["range_keys"], range_vals=slot["range_vals"], status=slot["status"])
         self.pending.append(b)
@@ -156,6 +154,7 @@ class BatchedRunner:
         its slot is reused)."""
         n = int(keys.numel())
         if self.queue_depth and n <= QUEUE_BATCH_MAX:
+            self.stream.wait_stream(torch.cuda.current_stream(self.idx.device))
             return self._enqueue(ops, keys, aux, n)
         self.flush()
         s = self.size_for(n)

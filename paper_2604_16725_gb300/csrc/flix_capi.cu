@@ -1072,11 +1072,12 @@ int flix_apply_async(flix_t h, const uint8_t* d_ops, const void* d_keys, const v
                            (uint64_t*)d_range_vals, range_cap, nullptr, d_status, false, S(stream)));
 }
 
-int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us, void* stream)
+int flix_apply_queue(flix_t h, const flix_batch* h_batches, uint32_t count, uint32_t wait_us, uint64_t* d_flags_or,
+                     void* stream)
 {
     if (!h || (count && !h_batches)) return FLIX_EINVAL;
-    return DISPATCH(apply_queue<uint32_t>(h, h_batches, count, wait_us, S(stream)),
-                    apply_queue<uint64_t>(h, h_batches, count, wait_us, S(stream)));
+    return DISPATCH(apply_queue<uint32_t>(h, h_batches, count, wait_us, d_flags_or, S(stream)),
+                    apply_queue<uint64_t>(h, h_batches, count, wait_us, d_flags_or, S(stream)));
 }
 
 int flix_reserve(flix_t h, uint64_t batch_max, uint64_t free_nodes_min, void* stream)

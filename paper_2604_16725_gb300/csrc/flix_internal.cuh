@@ -398,6 +398,154 @@ __device__ __forceinline__ void point_result(const DevIdx<K>& ix, int op, K q, u
     }
 }
 
+// Range count by one warp (all 32 lanes call it with the same arguments): the stored keys <= hi
+// from slot pos of `node` in bucket bb onwards.  Like the fill, the warp takes the next nodes in
+// chain order 32 at a time (lane 0 the current node, lane l > 0 the first node of bucket bb + l,
+// a batch ending at the first node whose chain continues); a node whose maxKey is <= hi counts
+// its size from its position; the first node whose maxKey is > hi counts its keys <= hi by a binary
+// search and ends the count.
+template <class K, bool NC = true>
+__device__ __forceinline__ uint64_t range_count_warp(const DevIdx<K>& ix, uint64_t bb, uint32_t node, uint32_t pos, K hi)
+{
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t NS = ix.NS;
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t c = 0;
+    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
+        uint32_t n_l = NIL, p_l = 0, sz_l = 0, nx_l = NIL;
+        K bd_l = K(0);
+        if (lane == 0) {
+            n_l = node;
+            p_l = pos;
+        } else if (bb + lane < ix.nb) {
+            n_l = ld_node<NC>(ix.head + bb + lane);
+        }
+        if (n_l != NIL) {
+            sz_l = ld_node<NC>(ix.size + n_l);
+            nx_l = ld_node<NC>(ix.next + n_l);
+            bd_l = ld_node<NC>(ix.bound + n_l);
+        }
+        const uint32_t cont = __ballot_sync(FULL, n_l != NIL && nx_l != NIL);
+        const uint32_t past = __ballot_sync(FULL, n_l != NIL && bd_l > hi);
+        const uint32_t none = __ballot_sync(FULL, n_l == NIL);
+        // the batch: lanes up to the first that continues its chain, ends the count or has no node
+        const uint32_t stop = cont | past | none;
+        const uint32_t last = stop ? __ffs(stop) - 1 : 31;
+        uint32_t mine = 0;
+        if (lane <= last && n_l != NIL && sz_l > p_l) {
+            if (bd_l <= hi) mine = sz_l - p_l;
+            else mine = node_upper_bound<K, NC>(ix.keys + (uint64_t)n_l * NS, p_l, sz_l, hi) - p_l;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(FULL, mine, d);
+        c += mine;
+        if ((past | none) & (0xFFFFFFFFu >> (31 - last))) break;   // a node past hi, or no node left
+        // continue after the batch's last node: along its link, or at the next bucket's first node
+        const uint32_t lnx = __shfl_sync(FULL, nx_l, last);
+        if (lnx != NIL) {
+            bb += last;
+            node = lnx;
+        } else {
+            bb += last + 1;
+            if (bb >= ix.nb) break;
+            node = ld_node<NC>(ix.head + bb);
+        }
+        pos = 0;
+    }
+    return c;
+}
+
+// Range fill by one warp (all 32 lanes call it with the same arguments): c pairs starting at slot
+// pos of `node` in bucket bb, written to rkeys/rvals[o..o+c) in key order.  The warp takes the
+// next nodes in chain order 32 at a time: lane 0 the current node (from the current position), lane
+// l > 0 the first node of bucket bb + l; their sizes and node-links load in parallel, and a batch
+// ends at the first node whose chain continues (the walk goes on from its link).  A warp scan of
+// the nodes' available counts gives each node's output offset, and the pairs are copied with one
+// independent load per pair (each lane finds its pair's node by a shuffle search over the offsets).
+template <class K, bool NC = true, uint32_t R = 1>
+__device__ __forceinline__ void range_fill_warp(const DevIdx<K>& ix, uint64_t bb, uint32_t node, uint32_t pos,
+                                                uint64_t o, uint64_t c, K* __restrict__ rkeys, K* __restrict__ rvals)
+{
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t NS = ix.NS;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim && c > 0; guard++) {
+        // lane 0: the current node; lane l > 0: the first node of bucket bb + l
+        uint32_t n_l = NIL, p_l = 0, sz_l = 0, nx_l = NIL;
+        if (lane == 0) {
+            n_l = node;
+            p_l = pos;
+        } else if (bb + lane < ix.nb) {
+            n_l = ld_node<NC>(ix.head + bb + lane);
+        }
+        if (n_l != NIL) {
+            sz_l = ld_node<NC>(ix.size + n_l);
+            nx_l = ld_node<NC>(ix.next + n_l);
+        }
+        // the batch ends at the first node whose chain continues
+        const uint32_t cont = __ballot_sync(FULL, nx_l != NIL);
+        const uint32_t last = cont ? __ffs(cont) - 1 : 31;
+        const uint32_t avail = (lane <= last && sz_l > p_l) ? sz_l - p_l : 0u;
+        uint32_t incl = avail;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, incl, 31);
+        const uint32_t take = (uint64_t)total < c ? total : (uint32_t)c;
+        // R pairs per lane in flight: every load of a round is issued before its stores (a warp on
+        // its own, as in the persistent queue kernel, wants several; a full grid of warps, one)
+        for (uint32_t t0 = 0; t0 < take; t0 += 32 * R) {
+            K kr[R], vr[R];
+#pragma unroll
+            for (uint32_t r = 0; r < R; r++) {
+                const uint32_t t = t0 + r * 32 + lane;
+                // the pair's node: the first lane whose inclusive count exceeds t
+                uint32_t src = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t probe = src + step - 1;
+                    if (__shfl_sync(FULL, incl, probe) <= t) src += step;
+                }
+                const uint32_t base = __shfl_sync(FULL, incl - avail, src);
+                const uint32_t sn = __shfl_sync(FULL, n_l, src);
+                const uint32_t sp = __shfl_sync(FULL, p_l, src);
+                if (t < take) {
+                    const uint64_t slot = (uint64_t)sn * NS + sp + (t - base);
+                    kr[r] = ix.keys[slot];
+                    vr[r] = ix.vals[slot];
+                }
+            }
+#pragma unroll
+            for (uint32_t r = 0; r < R; r++) {
+                const uint32_t t = t0 + r * 32 + lane;
+                if (t < take) {
+                    rkeys[o + t] = kr[r];
+                    rvals[o + t] = vr[r];
+                }
+            }
+        }
+        o += take;
+        c -= take;
+        if (c == 0) break;
+        // continue after the batch's last node: along its link, or at the next bucket's first node
+        const uint32_t lnx = __shfl_sync(FULL, nx_l, last);
+        if (lnx != NIL) {
+            bb += last;
+            node = lnx;
+        } else {
+            bb += last + 1;
+            if (bb >= ix.nb) {
+                if (lane == 0) atomicOr(ix.err, ERR_RANGE);
+                return;
+            }
+            node = ix.head[bb];
+        }
+        pos = 0;
+    }
+}
+
 // Read up to 8 device values (4 or 8 bytes each) into h->hpin[word0 + i] and synchronise the stream
 // (flix_capi.cu); returns a FLIX_ status.
 int readback_at(flix_index* h, cudaStream_t st, uint32_t word0,
@@ -415,7 +563,8 @@ void preload_persist_kernels();
 
 // The persistent queue of small mixed batches (flix_persist.cu).
 template <class K>
-int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wait_us, cudaStream_t st);
+int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wait_us, uint64_t* d_flags_or,
+                cudaStream_t st);
 
 // Device fills and small copies as kernels on the call's stream (flix_capi.cu): a cudaMemsetAsync
 // or cudaMemcpyAsync may be carried out by a copy engine, where it would wait behind bulk transfers

@@ -186,7 +186,7 @@ __device__ uint32_t merged_size(const DevIdx<K>& ix, uint32_t x, const K* ukey, 
 template <class K>
 __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatch* __restrict__ q, uint32_t count,
                                                       PQScratch<K> S, DevState* __restrict__ ds, uint32_t* free_ids,
-                                                      uint64_t limit_ns)
+                                                      uint64_t limit_ns, unsigned long long* flags_or)
 {
     grid_dep_enter();
     __shared__ K s_k[PQ_MAX];
@@ -330,44 +330,33 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
                     }
                     point_result<K, false>(ix, op, key, b, node, sz, nx, prev, p, kp, rk, rv, f);
                 }
-            } else if (op == FLIX_OP_RANGE) {
-                const K hi = aux[pos];
-                uint64_t c = 0;
-                uint32_t bb = bucket_of(ix, key);
-                uint32_t node, sz, nx, prev;
-                K bd;
-                S.rb[pos] = bb;
-                S.rn[pos] = NIL;
-                S.rp[pos] = 0;
-                if (key <= hi && find_node<K, false>(ix, bb, key, node, sz, bd, nx, prev)) {
-                    uint32_t p = node_lower_bound<K, false>(ix.keys + (uint64_t)node * NS, sz, key);
-                    S.rn[pos] = node;
-                    S.rp[pos] = p;
-                    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim; guard++) {
-                        if (bd <= hi) {
-                            c += sz - p;
-                        } else {
-                            c += node_upper_bound<K, false>(ix.keys + (uint64_t)node * NS, p, sz, hi) - p;
-                            break;
-                        }
-                        node = nx;
-                        while (node == NIL) {
-                            if (++bb >= ix.nb) break;
-                            node = ix.head[bb];
-                        }
-                        if (node == NIL) break;
-                        sz = ix.size[node];
-                        bd = ix.bound[node];
-                        nx = ix.next[node];
-                        p = 0;
-                    }
-                }
-                S.cnt[pos] = c;
             }
-            if (op != FLIX_OP_RANGE) S.cnt[pos] = 0;
+            if (op != FLIX_OP_RANGE) S.cnt[pos] = 0;       // a range op's count comes from its warp below
             if (B.keys_out) static_cast<K*>(B.keys_out)[pos] = rk;
             if (B.vals_out) static_cast<K*>(B.vals_out)[pos] = rv;
             if (B.found) B.found[pos] = f;
+        }
+        // range counts, one warp per range op (the pairs follow on the snapshot in phase E1)
+        for (uint32_t i = gtid >> 5; i < n; i += gstride >> 5) {
+            const uint32_t pos = S.si[i];
+            if (B.ops[pos] != FLIX_OP_RANGE) continue;          // warp-uniform
+            const K lo = S.sk[i], hi = aux[pos];
+            const uint32_t bb = bucket_of(ix, lo);
+            uint32_t node, sz, nx, prev;
+            K bd;
+            uint64_t c = 0;
+            uint32_t rn = NIL, rp = 0;
+            if (lo <= hi && find_node<K, false>(ix, bb, lo, node, sz, bd, nx, prev)) {
+                rn = node;
+                rp = node_lower_bound<K, false>(ix.keys + (uint64_t)node * NS, sz, lo);
+                c = range_count_warp<K, false>(ix, bb, node, rp, hi);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                S.rb[pos] = bb;
+                S.rn[pos] = rn;
+                S.rp[pos] = rp;
+                S.cnt[pos] = c;
+            }
         }
         for (uint32_t u = gtid; u < U; u += gstride) S.ub[u] = bucket_of(ix, S.ukey[u]);
         if (!grid_barrier(S.word, limit_ns)) break;
@@ -453,6 +442,7 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
                 S.word[2] = tn;
                 S.word[3] = tf;
                 S.wide[0] = top;
+                if (flags_or && flags) atomicOr(flags_or, (unsigned long long)flags);
                 if (B.status) {
                     B.status[0] = flags;
                     B.status[1] = S.wide[1];
@@ -463,27 +453,15 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
         }
         if (!grid_barrier(S.word, limit_ns)) break;
         const bool admitted = S.word[1] != 0;
-        // ---- E1: range pairs on the pre-batch state ------------------------------------------------
+        // ---- E1: range pairs on the pre-batch state, one warp per range op --------------------
         if (admitted) {
-            for (uint32_t pos = gtid; pos < n; pos += gstride) {
-                if (B.ops[pos] != FLIX_OP_RANGE) continue;
-                uint64_t c = S.cnt[pos];
+            const uint32_t gw = gtid >> 5, nwarps = gstride >> 5;
+            for (uint32_t pos = gw; pos < n; pos += nwarps) {
+                if (B.ops[pos] != FLIX_OP_RANGE) continue;      // warp-uniform: pos is the warp's
+                const uint64_t c = S.cnt[pos];
                 if (c == 0) continue;
-                uint64_t o = B.range_off[pos];
-                uint32_t bb = S.rb[pos], node = S.rn[pos], p = S.rp[pos];
-                K* rk = static_cast<K*>(B.range_keys);
-                K* rv = static_cast<K*>(B.range_vals);
-                for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim && c > 0 && node != NIL;
-                     guard++) {
-                    const uint32_t sz = ix.size[node];
-                    for (; p < sz && c > 0; p++, c--, o++) {
-                        rk[o] = ix.keys[(uint64_t)node * NS + p];
-                        rv[o] = ix.vals[(uint64_t)node * NS + p];
-                    }
-                    node = ix.next[node];
-                    p = 0;
-                    while (node == NIL && ++bb < ix.nb) node = ix.head[bb];
-                }
+                range_fill_warp<K, false, 4>(ix, (uint64_t)S.rb[pos], S.rn[pos], S.rp[pos], B.range_off[pos], c,
+                                          static_cast<K*>(B.range_keys), static_cast<K*>(B.range_vals));
             }
         }
         if (!grid_barrier(S.word, limit_ns)) break;
@@ -594,6 +572,7 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
         atomicOr(ix.err, ERR_TIMEOUT);
         for (uint32_t r = bi; r < count; r++)
             if (q[r].status) q[r].status[0] = PQ_NOT_RUN;
+        if (flags_or) atomicOr(flags_or, (unsigned long long)PQ_NOT_RUN);
     }
 }
 
@@ -607,7 +586,8 @@ void preload_persist_kernels()
 }
 
 template <class K>
-int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wait_us, cudaStream_t st)
+int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wait_us, uint64_t* d_flags_or,
+                cudaStream_t st)
 {
     if (count == 0) return FLIX_OK;
     if (h->cfg.merge_underfull || h->cfg.split_chains_over) return FLIX_ENOTIMPL;
@@ -698,7 +678,8 @@ int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wa
     uint64_t limit_ns = (uint64_t)wait_us * 1000ull;
     DevState* ds = h->dstate;
     uint32_t* fid = h->free_ids;
-    void* args[] = {&ix, &dqc, &count, &S, &ds, &fid, &limit_ns};
+    unsigned long long* fo = reinterpret_cast<unsigned long long*>(d_flags_or);
+    void* args[] = {&ix, &dqc, &count, &S, &ds, &fid, &limit_ns, &fo};
     cudaEvent_t pa = nullptr, pb = nullptr;
     if (h->prof_on) {
         pa = prof_event(h);
@@ -715,7 +696,7 @@ int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wa
     return FLIX_OK;
 }
 
-template int apply_queue<uint32_t>(flix_index*, const flix_batch*, uint32_t, uint32_t, cudaStream_t);
-template int apply_queue<uint64_t>(flix_index*, const flix_batch*, uint32_t, uint32_t, cudaStream_t);
+template int apply_queue<uint32_t>(flix_index*, const flix_batch*, uint32_t, uint32_t, uint64_t*, cudaStream_t);
+template int apply_queue<uint64_t>(flix_index*, const flix_batch*, uint32_t, uint32_t, uint64_t*, cudaStream_t);
 
 }  // namespace flix

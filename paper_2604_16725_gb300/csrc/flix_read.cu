@@ -253,7 +253,9 @@ __global__ void __launch_bounds__(RP_THREADS) k_win_scatter(const uint32_t* __re
 }
 
 // Range count: per range query, the start (bucket, node, position) and the number of stored keys
-// in [lo, hi].  Nodes whose maxKey <= hi are counted from their size alone.
+// in [lo, hi].  Nodes whose maxKey <= hi are counted from their size alone.  (One thread per query:
+// a batch holds enough queries to keep every SM busy; the persistent queue kernel, with few queries
+// per batch, counts each by a warp instead.)
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const K* __restrict__ skeys,
                                                             const uint32_t* __restrict__ sidx, uint64_t m,
@@ -313,12 +315,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const 
     cnt[idx] = c;
 }
 
-// Range fill: one warp per sorted query.  The warp takes the next nodes in chain order 32 at a
-// time: lane 0 the current node (from the current position), lane l > 0 the first node of bucket
-// bb + l; their sizes and node-links load in parallel, and the batch ends at the first node whose
-// chain continues (the walk goes on from its link).  A warp scan of the nodes' available counts
-// gives each node's output offset, and the batch's pairs are copied with one independent load per
-// pair (each lane finds its pair's node by a shuffle search over the offsets).
+// Range fill: one warp per sorted query (range_fill_warp).
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const uint32_t* __restrict__ sidx,
                                                            uint64_t m, const uint8_t* __restrict__ ops,
@@ -330,7 +327,6 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
 {
     grid_dep_enter();
     if (ds && !ds->admitted) return;
-    const uint32_t lane = threadIdx.x & 31;
     const uint64_t j = ((uint64_t)blockIdx.x * RP_THREADS + threadIdx.x) >> 5;
     if (j >= m) return;
     const uint32_t idx = sidx[j];
@@ -338,71 +334,7 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_fill(DevIdx<K> ix, const u
     uint64_t o = roff[idx];
     uint64_t c = roff[idx + 1] - o;
     if (c == 0) return;
-    const uint32_t NS = ix.NS;
-    uint64_t bb = start_bucket[j];
-    uint32_t node = start_node[j];
-    uint32_t pos = start_pos[j];
-    for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim && c > 0; guard++) {
-        // lane 0: the current node; lane l > 0: the first node of bucket bb + l
-        uint32_t n_l = NIL, p_l = 0, sz_l = 0, nx_l = NIL;
-        if (lane == 0) {
-            n_l = node;
-            p_l = pos;
-        } else if (bb + lane < ix.nb) {
-            n_l = ix.head[bb + lane];
-        }
-        if (n_l != NIL) {
-            sz_l = ix.size[n_l];
-            nx_l = ix.next[n_l];
-        }
-        // the batch ends at the first node whose chain continues
-        const uint32_t cont = __ballot_sync(FULL, nx_l != NIL);
-        const uint32_t last = cont ? __ffs(cont) - 1 : 31;
-        const uint32_t avail = (lane <= last && sz_l > p_l) ? sz_l - p_l : 0u;
-        uint32_t incl = avail;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, incl, d);
-            if (lane >= (uint32_t)d) incl += y;
-        }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        const uint32_t take = (uint64_t)total < c ? total : (uint32_t)c;
-        for (uint32_t t0 = 0; t0 < take; t0 += 32) {
-            const uint32_t t = t0 + lane;
-            // the pair's node: the first lane whose inclusive count exceeds t
-            uint32_t src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t probe = src + step - 1;
-                if (__shfl_sync(FULL, incl, probe) <= t) src += step;
-            }
-            const uint32_t base = __shfl_sync(FULL, incl - avail, src);
-            const uint32_t sn = __shfl_sync(FULL, n_l, src);
-            const uint32_t sp = __shfl_sync(FULL, p_l, src);
-            if (t < take) {
-                const uint64_t slot = (uint64_t)sn * NS + sp + (t - base);
-                rkeys[o + t] = ix.keys[slot];
-                rvals[o + t] = ix.vals[slot];
-            }
-        }
-        o += take;
-        c -= take;
-        if (c == 0) break;
-        // continue after the batch's last node: along its link, or at the next bucket's first node
-        const uint32_t lnx = __shfl_sync(FULL, nx_l, last);
-        if (lnx != NIL) {
-            bb += last;
-            node = lnx;
-        } else {
-            bb += last + 1;
-            if (bb >= ix.nb) {
-                if (lane == 0) atomicOr(ix.err, ERR_RANGE);
-                return;
-            }
-            node = ix.head[bb];
-        }
-        pos = 0;
-    }
+    range_fill_warp(ix, (uint64_t)start_bucket[j], start_node[j], start_pos[j], o, c, rkeys, rvals);
 }
 
 }  // namespace

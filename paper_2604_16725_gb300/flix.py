@@ -98,7 +98,7 @@ SIGNATURES = {
     "flix_export": (_INT, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "flix_dump_layout": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "flix_sort_pairs": (_INT, [_VP, _VP, _U64, _VP, _VP, _VP]),
-    "flix_apply_queue": (_INT, [_VP, _VP, _U32, _U32, _VP]),
+    "flix_apply_queue": (_INT, [_VP, _VP, _U32, _U32, _VP, _VP]),
     "flix_profile_enable": (_INT, [_VP, _INT]),
     "flix_profile_reset": (_INT, [_VP]),
     "flix_profile_read": (_INT, [_VP, _U32, _VP, _VP, _VP, _VP, _VP]),
@@ -330,11 +330,12 @@ class Index:
                                        _ptr(out["range_keys"]), _ptr(out["range_vals"]), cap, _ptr(out["status"]),
                                        _stream(stream)), "flix_apply_async", self._h)
 
-    def apply_queue(self, batches, wait_us: int = 2_000_000, stream=None):
+    def apply_queue(self, batches, wait_us: int = 2_000_000, flags_or=None, stream=None):
         """Run a queue of small mixed batches in one persistent kernel (flix_apply_queue).  batches:
         list of dicts with device tensors ops, keys, aux and outputs keys_out, vals_out, found,
         range_off (n+1), range_keys, range_vals, status (4 x int64), and optionally `ready` (an int32
-        device word the kernel waits on).  Asynchronous: read the outputs once the stream has run."""
+        device word the kernel waits on).  flags_or: optional int64 device word that every batch's
+        status flags are OR-ed into.  Asynchronous: read the outputs once the stream has run."""
         arr = (Batch * len(batches))()
         for i, b in enumerate(batches):
             o = self._dev(b["ops"], torch.uint8)
@@ -345,8 +346,8 @@ class Index:
                              for f in ("keys_out", "vals_out", "found", "range_off", "range_keys", "range_vals")),
                            b["range_keys"].numel() if b.get("range_keys") is not None else 0,
                            _ptr(b["status"]).value, _ptr(b["ready"]).value if b.get("ready") is not None else None)
-        _check(load().flix_apply_queue(self._h, arr, len(batches), wait_us, _stream(stream)), "flix_apply_queue",
-               self._h)
+        _check(load().flix_apply_queue(self._h, arr, len(batches), wait_us, _ptr(flags_or), _stream(stream)),
+               "flix_apply_queue", self._h)
 
     def reserve(self, batch_max: int, free_nodes_min: int = 0, stream=None):
         _check(load().flix_reserve(self._h, batch_max, free_nodes_min, _stream(stream)), "flix_reserve", self._h)
