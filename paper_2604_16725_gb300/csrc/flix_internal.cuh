@@ -228,6 +228,37 @@ cudaError_t launch_b(Ctx& c, int kid, double bytes, dim3 grid, dim3 block, size_
     return e;
 }
 
+// A cooperative launch (every block resident at once, for kernels with a grid barrier); it waits
+// for the previous launch on the stream to complete, like a launch without dependent-launch overlap.
+template <class Kern, class... Args>
+cudaError_t launch_coop(Ctx& c, int kid, double bytes, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
+{
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c.h->prof_on) {
+        a = prof_event(c.h);
+        b = prof_event(c.h);
+        cudaEventRecord(a, c.st);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (c.h->prof_on) {
+        cudaEventRecord(b, c.st);
+        c.h->prof.push_back(ProfRec{kid, bytes, a, b});
+    }
+    c.h->launches++;
+    return e;
+}
+
 template <class Kern, class... Args>
 cudaError_t launch(Ctx& c, int kid, dim3 grid, dim3 block, size_t smem, Kern kern, Args... args)
 {

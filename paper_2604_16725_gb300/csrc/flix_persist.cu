@@ -2,9 +2,9 @@
 // cooperative launch (no launch per batch).  A grid of one wave of blocks takes the batches one
 // after another; each batch goes through the method's steps as phases separated by grid barriers:
 //
-//   A  (block 0)   wait for the batch's ready word; sort the batch's (key, position) pairs in shared
-//                  memory (Sec. 3.3: the batch is sorted before buckets pull their operations);
-//                  fold each key's inserts and deletes into one net update (submission order)
+//   A  (block 0)   wait for the batch's ready word; sort the batch's inserts and deletes by (key,
+//                  position) in shared memory (Sec. 3.3: updates are sorted before buckets pull
+//                  them); fold each key's inserts and deletes into one net update (submission order)
 //   B  (all)       snapshot reads (lookup, successor, predecessor, range count): bucket = number of
 //                  maxBucket values below the key (Sec. 3.3), walk to the node (Sec. 4.1), search it;
 //                  the bucket of every net update
@@ -51,8 +51,6 @@ struct PQBatch {
 // Scratch of the queue (one batch at a time), from the handle's arena.
 template <class K>
 struct PQScratch {
-    K* sk;              // sorted keys
-    uint32_t* si;       // their input positions
     uint64_t* cnt;      // range pair count per input position
     uint32_t* rb;       // range start per input position: bucket, node, slot
     uint32_t* rn;
@@ -224,18 +222,34 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
             }
             __syncthreads();
             if (s_flag) {
-                uint32_t P2 = 2;
-                while (P2 < n) P2 <<= 1;
-                uint32_t bad = 0;
-                for (uint32_t i = threadIdx.x; i < P2; i += PQ_THREADS) {
+                // only the inserts and deletes are sorted: reads look their keys up one by one
+                constexpr uint32_t PER = PQ_MAX / PQ_THREADS;
+                uint32_t mine = 0, bad = 0;
+#pragma unroll
+                for (uint32_t r = 0; r < PER; r++) {
+                    const uint32_t i = threadIdx.x * PER + r;
                     if (i < n) {
-                        s_k[i] = keys[i];
-                        s_p[i] = i;
-                        bad |= B.ops[i] == FLIX_OP_INSERT && keys[i] == KM;
-                    } else {
-                        s_k[i] = KM;
-                        s_p[i] = 0xFFFFFFFFu;
+                        const uint8_t op = B.ops[i];
+                        mine += op == FLIX_OP_INSERT || op == FLIX_OP_DELETE;
+                        bad |= op == FLIX_OP_INSERT && keys[i] == KM;
                     }
+                }
+                uint32_t m;
+                uint32_t o = block_scan<uint32_t>(mine, s_sw, m);
+#pragma unroll
+                for (uint32_t r = 0; r < PER; r++) {
+                    const uint32_t i = threadIdx.x * PER + r;
+                    if (i < n && (B.ops[i] == FLIX_OP_INSERT || B.ops[i] == FLIX_OP_DELETE)) {
+                        s_k[o] = keys[i];
+                        s_p[o] = i;
+                        o++;
+                    }
+                }
+                uint32_t P2 = 2;
+                while (P2 < m) P2 <<= 1;
+                for (uint32_t i = m + threadIdx.x; i < P2; i += PQ_THREADS) {
+                    s_k[i] = KM;
+                    s_p[i] = 0xFFFFFFFFu;
                 }
                 if (__syncthreads_or(bad) && threadIdx.x == 0) S.word[5] = 1;
                 for (uint32_t k = 2; k <= P2; k <<= 1) {
@@ -257,41 +271,32 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
                     }
                 }
                 // net update of each key's run (submission order: positions ascend in a run)
-                constexpr uint32_t PER = PQ_MAX / PQ_THREADS;
                 uint32_t has[PER];
                 K nkv[PER];
                 uint32_t nop[PER];
-                uint32_t mine = 0;
+                mine = 0;
 #pragma unroll
                 for (uint32_t r = 0; r < PER; r++) {
                     const uint32_t i = threadIdx.x * PER + r;
                     has[r] = 0;
-                    if (i < n) {
-                        S.sk[i] = s_k[i];
-                        S.si[i] = s_p[i];
-                    }
-                    if (i >= n || (i > 0 && s_k[i - 1] == s_k[i])) continue;
-                    bool present = false, deleted = false, any = false;
+                    if (i >= m || (i > 0 && s_k[i - 1] == s_k[i])) continue;
+                    bool present = false, deleted = false;
                     K v = K(0);
-                    for (uint32_t e = i; e < n && s_k[e] == s_k[i]; e++) {
-                        const uint8_t op = B.ops[s_p[e]];
-                        if (op == FLIX_OP_INSERT) {
-                            any = true;
+                    for (uint32_t e = i; e < m && s_k[e] == s_k[i]; e++) {
+                        if (B.ops[s_p[e]] == FLIX_OP_INSERT) {
                             if (!present) { present = true; v = aux[s_p[e]]; }
-                        } else if (op == FLIX_OP_DELETE) {
-                            any = true;
+                        } else {
                             present = false;
                             deleted = true;
                         }
                     }
-                    if (!any) continue;
                     has[r] = 1;
                     nop[r] = !present ? EFF_DEL : (deleted ? EFF_UPS : EFF_INS);
                     nkv[r] = v;
                     mine++;
                 }
                 uint32_t tot;
-                uint32_t o = block_scan<uint32_t>(mine, s_sw, tot);
+                o = block_scan<uint32_t>(mine, s_sw, tot);
 #pragma unroll
                 for (uint32_t r = 0; r < PER; r++) {
                     if (!has[r]) continue;
@@ -307,10 +312,9 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
         if (!grid_barrier(S.word, limit_ns)) break;
         const uint32_t U = S.word[0];
         // ---- B: snapshot reads, buckets of the net updates -------------------------------------
-        for (uint32_t i = gtid; i < n; i += gstride) {
-            const uint32_t pos = S.si[i];
+        for (uint32_t pos = gtid; pos < n; pos += gstride) {
             const uint8_t op = B.ops[pos];
-            const K key = S.sk[i];
+            const K key = keys[pos];
             K rk = KM, rv = KM;
             uint8_t f = 0;
             if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC || op == FLIX_OP_PRED) {
@@ -337,10 +341,9 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
             if (B.found) B.found[pos] = f;
         }
         // range counts, one warp per range op (the pairs follow on the snapshot in phase E1)
-        for (uint32_t i = gtid >> 5; i < n; i += gstride >> 5) {
-            const uint32_t pos = S.si[i];
+        for (uint32_t pos = gtid >> 5; pos < n; pos += gstride >> 5) {
             if (B.ops[pos] != FLIX_OP_RANGE) continue;          // warp-uniform
-            const K lo = S.sk[i], hi = aux[pos];
+            const K lo = keys[pos], hi = aux[pos];
             const uint32_t bb = bucket_of(ix, lo);
             uint32_t node, sz, nx, prev;
             K bd;
@@ -605,8 +608,6 @@ int apply_queue(flix_index* h, const flix_batch* hb, uint32_t count, uint32_t wa
     Arena& A = h->arena;
     PQBatch* dq = A.take<PQBatch>(count);
     PQScratch<K> S;
-    S.sk = A.take<K>(PQ_MAX);
-    S.si = A.take<uint32_t>(PQ_MAX);
     S.cnt = A.take<uint64_t>(PQ_MAX);
     S.rb = A.take<uint32_t>(PQ_MAX);
     S.rn = A.take<uint32_t>(PQ_MAX);

@@ -197,22 +197,16 @@ __global__ void __launch_bounds__(256) k_scan_digits(const uint32_t* __restrict_
     }
 }
 
-// One digit pass of the plan.  LOOKBACK selects one-sweep (status, tile_ctr) or reduce-then-scan
-// (offsets).  A pass beyond the plan's count returns at once.  PERSIST (one-sweep only): the grid is
-// one wave of blocks that take tiles from the counter until none is left, which makes a launch
-// that finds its pass beyond the plan cheap (the passes the plan may leave out run this way; a
-// grid of one block per tile is faster when the pass runs).
-template <class K, bool LOOKBACK, bool PERSIST = false>
-__global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv,
-                                                         uint64_t n, int pass, const SortPlan* __restrict__ plan,
-                                                         const uint32_t* __restrict__ bases,
-                                                         const uint32_t* __restrict__ offsets, uint32_t T,
-                                                         uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
-                                                         uint32_t* __restrict__ err)
+// One digit pass of the plan (np passes in all).  LOOKBACK selects one-sweep (status, tile_ctr) or
+// reduce-then-scan (offsets).  PERSIST (one-sweep only): the grid is one wave of blocks that take
+// tiles from the counter until none is left.
+template <class K, bool LOOKBACK, bool PERSIST>
+__device__ __forceinline__ void sweep_pass(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv, uint64_t n,
+                                           int pass, uint32_t np, const SortPlan* __restrict__ plan,
+                                           const uint32_t* __restrict__ bases, const uint32_t* __restrict__ offsets,
+                                           uint32_t T, uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
+                                           uint32_t* __restrict__ err)
 {
-    grid_dep_enter();
-    const uint32_t np = plan->npass;
-    if ((uint32_t)pass >= np) return;
     const int shift = plan->shift[pass];
     const PassBufs<K> io = pass_bufs<K>(pass, np, kin, kout, vout, tk, tv);
     bases += (shift >> 3) * RADIX;
@@ -243,8 +237,9 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, 
         for (int i = 0; i < OS_ITEMS; i++) {
             const uint64_t pos = wbase + (uint64_t)i * 32 + lane;
             const bool ok = full_tile || pos < n;
-            key[i] = ok ? io.kin[pos] : K(0);
-            val[i] = ok ? (io.vin ? io.vin[pos] : static_cast<uint32_t>(pos)) : 0u;
+            // the tail kernel reads what other blocks wrote in its previous pass: past L1
+            key[i] = ok ? (PERSIST ? __ldcg(io.kin + pos) : io.kin[pos]) : K(0);
+            val[i] = ok ? (io.vin ? (PERSIST ? __ldcg(io.vin + pos) : io.vin[pos]) : static_cast<uint32_t>(pos)) : 0u;
         }
         if (full_tile) rank_warp<K, true>(key, rank, whist + warp * RADIX, wbase, n, shift);
         else rank_warp<K, false>(key, rank, whist + warp * RADIX, wbase, n, shift);
@@ -323,6 +318,72 @@ __global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, 
         }
         if (!PERSIST) break;
         __syncthreads();   // the tile's shared memory is reused by the next one
+    }
+}
+
+// One digit pass as its own launch; a pass beyond the plan's count returns at once.
+template <class K, bool LOOKBACK>
+__global__ void __launch_bounds__(OS_THREADS, 2) k_sweep(const K* kin, K* kout, uint32_t* vout, K* tk, uint32_t* tv,
+                                                         uint64_t n, int pass, const SortPlan* __restrict__ plan,
+                                                         const uint32_t* __restrict__ bases,
+                                                         const uint32_t* __restrict__ offsets, uint32_t T,
+                                                         uint32_t* __restrict__ status, uint32_t* __restrict__ tile_ctr,
+                                                         uint32_t* __restrict__ err)
+{
+    grid_dep_enter();
+    const uint32_t np = plan->npass;
+    if ((uint32_t)pass >= np) return;
+    sweep_pass<K, LOOKBACK, false>(kin, kout, vout, tk, tv, n, pass, np, plan, bases, offsets, T, status, tile_ctr,
+                                   err);
+}
+
+// Every pass from p0 on that the plan takes, in one cooperative launch of one wave of blocks: each
+// pass takes tiles from its own counter, and a grid barrier separates the passes.  The plan takes
+// these passes only for dense or skewed keys, so the usual launch reads the pass count and returns;
+// as separate launches each of them would cost a launch of its own.  The barrier counts arrivals
+// in bar[0] (zero at the sort's start: barrier j waits for j * gridDim.x arrivals); a wait past
+// about a second sets ERR_SPIN and the block returns, and blocks that see the bit stop waiting.
+template <class K>
+__global__ void __launch_bounds__(OS_THREADS, 2) k_sweep_tail(const K* kin, K* kout, uint32_t* vout, K* tk,
+                                                              uint32_t* tv, uint64_t n, int p0,
+                                                              const SortPlan* __restrict__ plan,
+                                                              const uint32_t* __restrict__ bases, uint32_t T,
+                                                              uint32_t* __restrict__ status,
+                                                              uint32_t* __restrict__ tile_ctr, uint32_t* bar,
+                                                              uint32_t* __restrict__ err)
+{
+    grid_dep_enter();
+    const uint32_t np = plan->npass;
+    __shared__ int s_stop;
+    for (int p = p0; (uint32_t)p < np && p < (int)sizeof(K); p++) {
+        sweep_pass<K, true, true>(kin, kout, vout, tk, tv, n, p, np, plan, bases, nullptr, T,
+                                  status + (size_t)p * T * RADIX, tile_ctr + p, err);
+        if ((uint32_t)p + 1 >= np) break;
+        // grid barrier: every tile of pass p is written before any block reads for pass p + 1
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint32_t target = (uint32_t)(p - p0 + 1) * gridDim.x;
+            atomicAdd(bar, 1u);
+            int stop = 0;
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (ld_volatile(bar) < target) {
+                if (ld_volatile(err) & ERR_SPIN) { stop = 1; break; }
+                uint64_t t1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if (t1 - t0 > 1000000000ull) {
+                    atomicOr(err, ERR_SPIN);
+                    stop = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            __threadfence();
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) return;
     }
 }
 
@@ -825,7 +886,7 @@ void preload_sort_kernels()
     FLIX_TOUCH(k_sort_plan<K>);              \
     FLIX_TOUCH(k_upsweep<K>);                \
     FLIX_TOUCH(k_sweep<K, true>);            \
-    FLIX_TOUCH((k_sweep<K, true, true>));    \
+    FLIX_TOUCH(k_sweep_tail<K>);             \
     FLIX_TOUCH(k_sweep<K, false>);           \
     FLIX_TOUCH(k_sort_finish<K>);            \
     FLIX_TOUCH(k_sort_finish_big<K>)
@@ -864,7 +925,7 @@ size_t sort_scratch_bytes(uint64_t n)
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t pingpong = al(n * sizeof(K)) + al(n * 4);
     const size_t rts = 2 * al(T * RADIX * 4);                      // counts, offsets
-    const size_t one = al(P * T * RADIX * 4) + al(P * 4);          // tile states, tile counters
+    const size_t one = al(P * T * RADIX * 4) + al((P + 1) * 4);    // tile states, tile counters, barrier
     const size_t fin = al(sizeof(SortPlan)) + al((n / (SMALL_SEG + 1) + 1) * 8);   // plan, long-group list
     return pingpong + al(P * RADIX * 4) + (rts > one ? rts : one) + fin + 1024;
 }
@@ -892,7 +953,7 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     const uint32_t T = div_up(n, OS_TILE);
     uint32_t* bases = A.take<uint32_t>(P * RADIX);
     uint32_t* status = onesweep ? A.take<uint32_t>((size_t)P * T * RADIX) : nullptr;
-    uint32_t* tile_ctr = onesweep ? A.take<uint32_t>(P) : nullptr;
+    uint32_t* tile_ctr = onesweep ? A.take<uint32_t>(P + 1) : nullptr;   // + the tail's barrier word
     uint32_t* counts = onesweep ? nullptr : A.take<uint32_t>((size_t)T * RADIX);
     uint32_t* offsets = onesweep ? nullptr : A.take<uint32_t>((size_t)T * RADIX);
     K* tk = A.take<K>(n);
@@ -906,7 +967,7 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     if (e) return e;
     if (onesweep) {
         if ((e = fill_bytes(c, status, 0, (size_t)P * T * RADIX * 4))) return e;
-        if ((e = fill_bytes(c, tile_ctr, 0, P * 4))) return e;
+        if ((e = fill_bytes(c, tile_ctr, 0, (P + 1) * 4))) return e;
     }
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.h->device);
@@ -929,33 +990,18 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     e = onesweep ? cudaFuncSetAttribute(k_sweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                  : cudaFuncSetAttribute(k_sweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    // the plan takes at least the h prefix digits unless fewer digits vary; the passes after those
-    // run as one wave of blocks taking tiles from the counter, cheap when the plan leaves them out
-    const uint32_t h_min = prefix_digits<K>(n);
-    uint32_t wave = T;
-    if (onesweep) {
-        if ((e = cudaFuncSetAttribute(k_sweep<K, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-            return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep<K, true, true>, OS_THREADS, smem)))
-            return e;
-        wave = std::min<uint32_t>(T, (uint32_t)std::max(per_sm, 1) * (uint32_t)nsm);
-    }
-    for (int p = 0; p < P; p++) {
+    // the plan takes at least the h prefix digits unless fewer digits vary; one-sweep runs the passes
+    // after those in one cooperative launch, which returns at once when the plan leaves them out
+    const uint32_t h_min = onesweep ? std::min<uint32_t>(prefix_digits<K>(n), P) : P;
+    for (int p = 0; p < (int)h_min; p++) {
         const bool on = (uint32_t)p < active;
         // algorithmic bytes: the first pass reads keys only (payload = position)
         const double bytes = on ? (double)n * ((p == 0 ? sizeof(K) : sizeof(K) + 4) + sizeof(K) + 4) : 0.0;
         if (onesweep) {
-            if ((uint32_t)p < h_min)
-                e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem,
-                             k_sweep<K, true>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
-                             (const uint32_t*)bases, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX,
-                             tile_ctr + p, c.h->err);
-            else
-                e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(wave), dim3(OS_THREADS), smem,
-                             k_sweep<K, true, true>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
-                             (const uint32_t*)bases, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX,
-                             tile_ctr + p, c.h->err);
+            e = launch_b(c, on ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(T), dim3(OS_THREADS), smem,
+                         k_sweep<K, true>, kin, kout, vout, tk, tv, n, p, (const SortPlan*)plan,
+                         (const uint32_t*)bases, (const uint32_t*)nullptr, T, status + (size_t)p * T * RADIX,
+                         tile_ctr + p, c.h->err);
         } else {
             e = launch(c, on ? K_SORT_UP : K_SORT_IDLE, dim3(T), dim3(UP_THREADS_S), 0, k_upsweep<K>, kin, kout, vout,
                        tk, tv, n, p, (const SortPlan*)plan, counts, T);
@@ -968,6 +1014,20 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
                              (const uint32_t*)bases, (const uint32_t*)offsets, T, (uint32_t*)nullptr,
                              (uint32_t*)nullptr, c.h->err);
         }
+        if (e) return e;
+    }
+    if (h_min < (uint32_t)P) {
+        if ((e = cudaFuncSetAttribute(k_sweep_tail<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+            return e;
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_tail<K>, OS_THREADS, smem))) return e;
+        // every block of a cooperative launch is resident at once, which the grid barrier needs
+        const uint32_t wave = std::min<uint32_t>(T, (uint32_t)std::max(per_sm, 1) * (uint32_t)nsm);
+        double bytes = 0.0;
+        for (uint32_t p = h_min; p < active && p < (uint32_t)P; p++) bytes += (double)n * 2.0 * (sizeof(K) + 4);
+        e = launch_coop(c, active > h_min ? K_SORT_ONESWEEP : K_SORT_IDLE, bytes, dim3(wave), dim3(OS_THREADS), smem,
+                        k_sweep_tail<K>, kin, kout, vout, tk, tv, n, (int)h_min, (const SortPlan*)plan,
+                        (const uint32_t*)bases, T, status, tile_ctr, tile_ctr + P, c.h->err);
         if (e) return e;
     }
     if ((e = launch(c, K_SORT_FINISH, dim3(div_up(n, FIN_TILE)), dim3(FIN_THREADS), 0, k_sort_finish<K>, kout, vout, n,

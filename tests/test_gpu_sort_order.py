@@ -83,3 +83,20 @@ def test_constant_and_dense_digits(fx):
     check_sort(fx, (np.uint64(0xABCD) << np.uint64(48)) | r.integers(0, 1 << 16, n, dtype=np.uint64), 64)
     check_sort(fx, np.full(n, 42, np.uint64), 64)                                    # one key repeated
     check_sort(fx, np.arange(n, 0, -1, dtype=np.uint64) * np.uint64(1 << 30), 64)    # descending, distinct
+
+
+def test_passes_past_the_prefix(fx):
+    """Plans with more passes than the prefix digits, which run in one cooperative launch with a grid
+    barrier between passes: one extra pass (three top digits of 64 values each: not heavy, but a
+    random item would share its 3-digit prefix with about 4 others, so a fourth digit is taken), and
+    every digit sorted (Zipf keys make every prefix digit heavy), both with ragged last tiles."""
+    r = np.random.default_rng(21)
+    n = (1 << 20) + 123
+    top = [r.integers(0, 64, n, dtype=np.uint64) for _ in range(3)]
+    keys = (top[0] << np.uint64(56)) | (top[1] << np.uint64(48)) | (top[2] << np.uint64(40)) | \
+        r.integers(0, 1 << 40, n, dtype=np.uint64)
+    check_sort(fx, keys, 64)
+    z = W.zipf(11, 1, (1 << 21) + 1001, 0.99, 1 << 20).astype(np.uint64)
+    keys = W.mix64(z) >> np.uint64(1)
+    check_sort(fx, keys, 64)
+    check_sort(fx, (keys & np.uint64(0xFFFFFFF0)).astype(np.uint32), 32)

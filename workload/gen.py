@@ -140,7 +140,9 @@ def zipf(seed: int, stream: int, n: int, s: float, N: int) -> np.ndarray:
 
     Density h(x) = x^-s on [1, N]; H is its antiderivative, written in the numerically stable
     helper form so that s close to 1 is exact enough.  Accept k = round(x) when k - x <= c
-    (the squeeze) or when u >= H(k + 1/2) - h(k).
+    (the squeeze) or when u >= H(k + 1/2) - h(k).  The two helper functions with their series
+    fallbacks and the squeeze constant c follow the form of this method in Apache Commons Math's
+    RejectionInversionZipfSampler.
     """
     assert s > 0 and N >= 1
     one_m_s = 1.0 - s
