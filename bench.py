@@ -737,14 +737,15 @@ def bench_batched(args):
     small_res = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
                            queue_depth=2)
     small_finals = small_res.pop("_finals")
-    deep = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
-                      queue_depth=16, modes=("persistent",))
-    deep_finals = deep.pop("_finals")
-    small_res["persistent_queue16"] = deep["persistent"]
-    small_finals["persistent_queue16"] = deep_finals["persistent"]
+    for dq in (1, 16):
+        deep = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
+                          queue_depth=dq, modes=("persistent",))
+        deep_finals = deep.pop("_finals")
+        small_res["persistent_queue%d" % dq] = deep["persistent"]
+        small_finals["persistent_queue%d" % dq] = deep_finals["persistent"]
     small_same = all(bool(torch.equal(small_finals["plain"][0], small_finals[m][0]) and
                           torch.equal(small_finals["plain"][1], small_finals[m][1]))
-                     for m in ("graph", "persistent", "persistent_queue16"))
+                     for m in ("graph", "persistent", "persistent_queue1", "persistent_queue16"))
     sizes = np.array([int(k.numel()) for _, k, _ in batches])
     small = sizes <= fx.QUEUE_BATCH_MAX
     same_state = all(bool(torch.equal(finals["plain"][0], finals[m][0]) and torch.equal(finals["plain"][1], finals[m][1]))
@@ -761,10 +762,12 @@ def bench_batched(args):
             "best_batched_path": best, "speedup_vs_plain": results[best]["mops"] / results["plain"]["mops"],
             "final_state_equal": same_state,
             "small_batch_stream": {"workload": "%d batches of log-uniform 2^4..2^11 ops, same mix, same index size; "
-                                               "persistent queue depth 2 (and 16)" % len(sbatches),
+                                               "persistent queue depth 2 (and 1, 16); a queued batch completes "
+                                               "when its queue's launch has run" % len(sbatches),
                                    "ops": sum(int(k.numel()) for _, k, _ in sbatches),
                                    "plain": small_res["plain"], "graph": small_res["graph"],
                                    "persistent": small_res["persistent"],
+                                   "persistent_queue1": small_res["persistent_queue1"],
                                    "persistent_queue16": small_res["persistent_queue16"],
                                    "final_state_equal": small_same},
             "autotune": tune["table"]}
@@ -939,7 +942,7 @@ def bench_xy(args):
 
     Rounds: build 2^24 uniform keys; 8 insert rounds of 3 * 2^21 keys (300% growth), Y = 90% of each
     round inside a hot interval covering X of the key range, X from 90% (uniform) down to 2%; after
-    every insert round a batch of 2^25 lookups of stored keys (the skew experiment of Sec. 6.4); then
+    every insert round a batch of 2^25 lookups of stored keys (the skew experiment of Sec. 6.3); then
     8 delete rounds removing the inserted keys.  Restructure accounting (Sec. 6.6, Tab. 4): each
     printed row (builds of 1M, 33M and 100M keys, 8 insert rounds to the printed final size at
     X25Y90 and X90Y90), 8 delete rounds removing the share of the inserted keys that the row
