@@ -195,7 +195,8 @@ def step_bytes(rcap, log_load=None, log_q=None, log_r=LOG_R, log_u=LOG_U):
         # sorted key, position and bucket; touched node prefixes; value sectors; results
         "read_point": (B * (ks + 8) + T(B) * node + hits * 32 + B * vs)
                       + (B * (ks + 8) + T(B) * node + B * 32 + B * (ks + vs)),
-        # windowed delivery: positions read for the counts, then (position, result) read and result written
+        # windowed delivery: the position tag the read kernel writes beside each result, then
+        # (position, result) read and the result written to its position
         "read_unsort": (B * 4 + B * (4 + vs) + B * vs) + (B * 4 + B * (4 + ks + vs) + B * (ks + vs)),
         # lower bound, position, bucket, upper bound; first node's prefix; start (3 words) and count out
         "range_count": R * (ks + 8) + R * ks + T(R) * node + R * (12 + 8),

@@ -140,43 +140,25 @@ __global__ void __launch_bounds__(PT_THREADS) k_partition(const K* __restrict__ 
         for (uint32_t t = threadIdx.x; t < la; t += PT_THREADS) off[a0 + t + 1] = (uint32_t)(b0 + sout[PT_TILE - 1 - t]);
 }
 
-// Windowed result delivery (see read_point): window regions of the results and their offsets,
-// passed by value.
+// Windowed result delivery (see read_point), passed by value.  Window w holds input positions
+// [w << shift, (w + 1) << shift); the reads of a batch deliver every input position exactly once, so
+// window w's region of the tagged arrays is that same range, and a block reserves its place in it
+// from the window's cursor.
 constexpr uint32_t RP_MAX_WIN = 256;
 template <class K>
 struct ReadWin {
-    int shift;               // window w holds input positions [w << shift, (w + 1) << shift)
-    const uint64_t* off;     // off[w * nblocks + b]: where block b's results of window w start
+    int shift;
+    uint32_t* cur;           // per window: results placed so far (zero before the read kernel)
     uint32_t* idx;           // input position of each windowed result
     K* rk;
     K* rv;
     uint8_t* rf;
 };
 
-// Delivery of one result: to the query's input position, or (win) tagged with it into the next
-// free place of its window's region (offsets per window and block from a count and a scan).
-template <class K>
-__device__ __forceinline__ void deliver(uint32_t idx, K rk, K rv, uint8_t f, K* __restrict__ keys_out,
-                                        K* __restrict__ vals_out, uint8_t* __restrict__ found_out,
-                                        const ReadWin<K>& win, uint32_t nwin, uint32_t* s_wcnt)
-{
-    if (!nwin) {
-        if (keys_out) keys_out[idx] = rk;
-        if (vals_out) vals_out[idx] = rv;
-        if (found_out) found_out[idx] = f;
-        return;
-    }
-    const uint32_t w = idx >> win.shift;
-    const uint32_t r = atomicAdd(&s_wcnt[w], 1u);
-    const uint64_t at = win.off[(uint64_t)w * gridDim.x + blockIdx.x] + r;
-    win.idx[at] = idx;
-    if (keys_out) win.rk[at] = rk;
-    if (vals_out) win.rv[at] = rv;
-    if (found_out) win.rf[at] = f;
-}
-
 // Point reads, one thread per sorted query (bucket bk from the partition).  Results go to the
-// query's input position, or, with win, to its window's region for k_win_scatter.
+// query's input position, or, with win, tagged with it into its window's region for k_win_scatter:
+// a block counts its results per window in shared memory, then reserves one run per window with
+// one atomic on the window's cursor.
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mode, const K* __restrict__ skeys,
                                                            const uint32_t* __restrict__ sidx, uint64_t m,
@@ -187,56 +169,68 @@ __global__ void __launch_bounds__(RP_THREADS) k_read_point(DevIdx<K> ix, int mod
 {
     grid_dep_enter();
     __shared__ uint32_t s_wcnt[RP_MAX_WIN];
+    __shared__ uint32_t s_wbase[RP_MAX_WIN];
     if (nwin) {
         for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) s_wcnt[w] = 0;
         __syncthreads();
     }
     const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
-    if (j >= m) return;
-    const uint32_t idx = sidx[j];
-    const int op = mode ? mode : ops[idx];
+    const bool active = j < m;              // every thread stays for the block's barriers
     const K KM = key_max<K>();
+    uint32_t idx = 0;
     K rk = KM, rv = KM;
     uint8_t f = 0;
-    if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC || op == FLIX_OP_PRED) {
-        const K q = skeys[j];
-        const uint32_t b = bk[j];
-        uint32_t node, sz, nx, prev;
-        K bd;
-        if (find_node(ix, b, q, node, sz, bd, nx, prev)) {   // else: chain error flagged, default results
-            const K* nk = ix.keys + (uint64_t)node * ix.NS;
-            uint32_t pos;
-            K kpos = K(0);
-            if (op == FLIX_OP_PRED) {
-                pos = node_upper_bound(nk, 0, sz, q);
-                if (pos > 0) kpos = __ldg(nk + pos - 1);
-            } else {
-                pos = node_lower_bound(nk, sz, q);
-                if (pos < sz) kpos = __ldg(nk + pos);
+    if (active) {
+        idx = sidx[j];
+        const int op = mode ? mode : ops[idx];
+        if (op == FLIX_OP_LOOKUP || op == FLIX_OP_SUCC || op == FLIX_OP_PRED) {
+            const K q = skeys[j];
+            const uint32_t b = bk[j];
+            uint32_t node, sz, nx, prev;
+            K bd;
+            if (find_node(ix, b, q, node, sz, bd, nx, prev)) {   // else: chain error flagged, default results
+                const K* nk = ix.keys + (uint64_t)node * ix.NS;
+                uint32_t pos;
+                K kpos = K(0);
+                if (op == FLIX_OP_PRED) {
+                    pos = node_upper_bound(nk, 0, sz, q);
+                    if (pos > 0) kpos = __ldg(nk + pos - 1);
+                } else {
+                    pos = node_lower_bound(nk, sz, q);
+                    if (pos < sz) kpos = __ldg(nk + pos);
+                }
+                point_result(ix, op, q, b, node, sz, nx, prev, pos, kpos, rk, rv, f);
             }
-            point_result(ix, op, q, b, node, sz, nx, prev, pos, kpos, rk, rv, f);
         }
     }
-    deliver(idx, rk, rv, f, keys_out, vals_out, found_out, win, nwin, s_wcnt);
-}
-
-// Windowed result delivery: counts[w * nblocks + b] = results of read block b whose input position
-// lies in window w (positions [w << shift, (w + 1) << shift)).
-__global__ void __launch_bounds__(RP_THREADS) k_win_count(const uint32_t* __restrict__ sidx, uint64_t m, int shift,
-                                                          uint32_t nwin, uint32_t* __restrict__ counts)
-{
-    grid_dep_enter();
-    __shared__ uint32_t c[RP_MAX_WIN];
-    for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) c[w] = 0;
+    if (!nwin) {
+        if (active) {
+            if (keys_out) keys_out[idx] = rk;
+            if (vals_out) vals_out[idx] = rv;
+            if (found_out) found_out[idx] = f;
+        }
+        return;
+    }
+    const uint32_t w = idx >> win.shift;
+    const uint32_t r = active ? atomicAdd(&s_wcnt[w], 1u) : 0u;
     __syncthreads();
-    const uint64_t j = (uint64_t)blockIdx.x * RP_THREADS + threadIdx.x;
-    if (j < m) atomicAdd(&c[sidx[j] >> shift], 1u);
+    for (uint32_t t = threadIdx.x; t < nwin; t += RP_THREADS) {
+        const uint32_t c = s_wcnt[t];
+        s_wbase[t] = c ? (t << win.shift) + atomicAdd(win.cur + t, c) : 0u;
+    }
     __syncthreads();
-    for (uint32_t w = threadIdx.x; w < nwin; w += RP_THREADS) counts[(uint64_t)w * gridDim.x + blockIdx.x] = c[w];
+    if (active) {
+        const uint64_t at = (uint64_t)s_wbase[w] + r;
+        win.idx[at] = idx;
+        if (keys_out) win.rk[at] = rk;
+        if (vals_out) win.rv[at] = rv;
+        if (found_out) win.rf[at] = f;
+    }
 }
 
 // Second half of the windowed delivery: results are read in window order, so the scattered
-// writes of the blocks in flight fall in a few windows' worth of output and merge in L2.
+// writes of the blocks in flight fall in a few windows' worth of output and merge in L2.  (One
+// result per thread: four per thread, loads first, measured slower.)
 template <class K>
 __global__ void __launch_bounds__(RP_THREADS) k_win_scatter(const uint32_t* __restrict__ widx, uint64_t m,
                                                             const K* __restrict__ rk, const K* __restrict__ rv,
@@ -344,7 +338,6 @@ void preload_read_kernels()
 {
     cudaFuncAttributes a;
 #define FLIX_TOUCH(...) cudaFuncGetAttributes(&a, __VA_ARGS__)
-    FLIX_TOUCH(k_win_count);
 #define FLIX_TOUCH_K(K)                      \
     FLIX_TOUCH(k_corank<K>);                 \
     FLIX_TOUCH(k_partition<K>);              \
@@ -380,9 +373,8 @@ cudaError_t partition(Ctx& c, const K* mkba, uint64_t nb, const K* skeys, uint64
 // Results scattered to random input positions cost a read-modify-write of a DRAM sector each once
 // they no longer fit in L2.  Above RP_WIN_BYTES of results, homogeneous reads deliver them in two
 // steps instead: the read kernel writes each result, tagged with its input position, into the
-// region of its window of input positions (about RP_WIN_TARGET bytes of output per window; the
-// regions' per-block offsets come from a count and a scan), and k_win_scatter reads the regions in
-// order and writes the results to their positions.
+// region of its window of input positions (about RP_WIN_TARGET bytes of output per window), and
+// k_win_scatter reads the regions in order and writes the results to their positions.
 constexpr uint64_t RP_WIN_BYTES = 96ull << 20;
 constexpr uint64_t RP_WIN_TARGET = 4ull << 20;
 
@@ -390,9 +382,7 @@ template <class K>
 size_t read_point_scratch_bytes(uint64_t m)
 {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t nblk = div_up(m ? m : 1, RP_THREADS);
-    return al(m * sizeof(K)) * 2 + al(m) + al(m * 4) + al(nblk * RP_MAX_WIN * 4) + al((nblk * RP_MAX_WIN + 1) * 8) +
-           scan_scratch_bytes<uint64_t>(nblk * RP_MAX_WIN) + 1024;
+    return al(m * sizeof(K)) * 2 + al(m) + al(m * 4) + al(RP_MAX_WIN * 4) + 1024;
 }
 
 template <class K>
@@ -411,17 +401,13 @@ cudaError_t read_point(Ctx& c, int mode, const K* skeys, const uint32_t* sidx, u
         const size_t mark = A.used;
         ReadWin<K> hw;
         hw.shift = shift;
-        uint32_t* counts = A.take<uint32_t>((size_t)nwin * nblk);
-        uint64_t* off = A.take<uint64_t>((size_t)nwin * nblk + 1);
-        hw.off = off;
+        hw.cur = A.take<uint32_t>(nwin);
         hw.idx = A.take<uint32_t>(m);
         hw.rk = keys_out ? A.take<K>(m) : nullptr;
         hw.rv = vals_out ? A.take<K>(m) : nullptr;
         hw.rf = found_out ? A.take<uint8_t>(m) : nullptr;
-        if (counts && off && hw.idx && (!keys_out || hw.rk) && (!vals_out || hw.rv) && (!found_out || hw.rf)) {
-            cudaError_t e =
-                launch(c, K_UNSORT, dim3(nblk), dim3(RP_THREADS), 0, k_win_count, sidx, m, shift, nwin, counts);
-            if (!e) e = scan_exclusive<uint32_t, uint64_t>(c, counts, off, (uint64_t)nwin * nblk);
+        if (hw.cur && hw.idx && (!keys_out || hw.rk) && (!vals_out || hw.rv) && (!found_out || hw.rf)) {
+            cudaError_t e = fill_bytes(c, hw.cur, 0, (size_t)nwin * 4);
             if (!e)
                 e = launch(c, K_READ_POINT, dim3(nblk), dim3(RP_THREADS), 0, k_read_point<K>, dev_view<K>(c.h), mode,
                            skeys, sidx, m, bk, ops, keys_out, vals_out, found_out, hw, nwin);
