@@ -405,7 +405,7 @@ constexpr int FIND_GROUPS = 8;                 // groups of 32 buckets per warp 
 // Every kernel reads the snapshot, because placing writes into the node itself.
 
 template <class K>
-__global__ void __launch_bounds__(UP_THREADS) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
+__global__ void __launch_bounds__(UP_THREADS, 10) k_update_count(DevIdx<K> ix, const K* __restrict__ ukey,
                                                              const uint32_t* __restrict__ uop,
                                                              const uint32_t* __restrict__ uoff,
                                                              uint32_t* __restrict__ tnode, uint64_t* __restrict__ nf,
