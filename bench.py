@@ -611,7 +611,7 @@ def main():
 # Batched and served forms (their own JSON lines; the default run is the plain read-scale step)
 # ------------------------------------------------------------------------------------------------
 
-def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log, queue_depth=32,
+def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log, queue_depth=1,
                modes=("plain", "graph", "persistent")):
     """One stream through plain per-batch flix_apply, the graph path and the persistent path.
     Per batch: latency from submission to completion (CUDA events); throughput = ops / wall time."""
@@ -705,8 +705,8 @@ def bench_batched(args):
     sizes log-uniform 2^8..2^22 (about 4.3e9 ops), 60/15/5/10/10 lookup/successor/range/insert/
     delete, generated on the GPU (workload.device: gen.mixed_stream's recipe and key universe).
     Three paths over the same batches: plain per-batch flix_apply; the batched form with a CUDA
-    graph per size class; and the batched form with the persistent kernel taking queues of up to
-    32 batches of at most 2048 ops (larger batches take the graphs).  Node size, sort variant and
+    graph per size class; and the batched form with the persistent kernel taking each batch of at
+    most 2048 ops as it comes (queue depth 1; larger batches take the graphs).  Node size, sort variant and
     bucket threads come from the autotuner on a held-out seed.  Per batch: latency from submission
     to completion (CUDA events); throughput = all ops / wall time."""
     import torch
@@ -730,15 +730,16 @@ def bench_batched(args):
     sizes = np.array([int(k.numel()) for _, k, _ in batches])
     max_b = int(sizes.max())
     log("stream: %d batches, %d ops" % (len(batches), n_ops))
-    results = run_stream(torch, fx, BatchedRunner, batches, s["preload_keys"], s["preload_vals"], NS, sv, bt, log)
+    results = run_stream(torch, fx, BatchedRunner, batches, s["preload_keys"], s["preload_vals"], NS, sv, bt, log,
+                         queue_depth=1)
     finals = results.pop("_finals")
     # a stream of small batches only (2^4..2^11 ops: every batch fits the persistent kernel's queue)
     ss = WD.mixed_stream_device(seed=4100, n_preload=n_pre, n_batches=min(args.batches, 3000), lo_exp=4, hi_exp=11)
     sbatches = list(ss["batches"]())
     small_res = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
-                           queue_depth=2)
+                           queue_depth=1)
     small_finals = small_res.pop("_finals")
-    for dq in (1, 16):
+    for dq in (2, 16):
         deep = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
                           queue_depth=dq, modes=("persistent",))
         deep_finals = deep.pop("_finals")
@@ -746,7 +747,7 @@ def bench_batched(args):
         small_finals["persistent_queue%d" % dq] = deep_finals["persistent"]
     small_same = all(bool(torch.equal(small_finals["plain"][0], small_finals[m][0]) and
                           torch.equal(small_finals["plain"][1], small_finals[m][1]))
-                     for m in ("graph", "persistent", "persistent_queue1", "persistent_queue16"))
+                     for m in ("graph", "persistent", "persistent_queue2", "persistent_queue16"))
     sizes = np.array([int(k.numel()) for _, k, _ in batches])
     small = sizes <= fx.QUEUE_BATCH_MAX
     same_state = all(bool(torch.equal(finals["plain"][0], finals[m][0]) and torch.equal(finals["plain"][1], finals[m][1]))
@@ -763,12 +764,12 @@ def bench_batched(args):
             "best_batched_path": best, "speedup_vs_plain": results[best]["mops"] / results["plain"]["mops"],
             "final_state_equal": same_state,
             "small_batch_stream": {"workload": "%d batches of log-uniform 2^4..2^11 ops, same mix, same index size; "
-                                               "persistent queue depth 2 (and 1, 16); a queued batch completes "
+                                               "persistent queue depth 1 (and 2, 16); a queued batch completes "
                                                "when its queue's launch has run" % len(sbatches),
                                    "ops": sum(int(k.numel()) for _, k, _ in sbatches),
                                    "plain": small_res["plain"], "graph": small_res["graph"],
                                    "persistent": small_res["persistent"],
-                                   "persistent_queue1": small_res["persistent_queue1"],
+                                   "persistent_queue2": small_res["persistent_queue2"],
                                    "persistent_queue16": small_res["persistent_queue16"],
                                    "final_state_equal": small_same},
             "autotune": tune["table"]}
