@@ -407,7 +407,9 @@ def main():
     ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "update_heavy", "xy", "light"],
                     help="plain: the read-scale step (default); batched: mixed-batch stream through CUDA "
                          "graphs vs plain launches; served: continuous batching under Poisson arrivals")
-    ap.add_argument("--batches", type=int, default=10000, help="batched form: stream length")
+    ap.add_argument("--batches", type=int, default=None,
+                    help="batched form: stream length (default 10000); update_heavy form: insert batches per "
+                         "distribution (default 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
@@ -723,7 +725,8 @@ def bench_batched(args):
     log("autotune: NS=%d sort_variant=%d bucket_threads=%d" % (NS, sv, bt))
     del hb, held
     n_pre = 1 << args.log_load if args.log_load != LOG_LOAD else 1 << 27
-    s = WD.mixed_stream_device(seed=4000, n_preload=n_pre, n_batches=args.batches)
+    n_stream = args.batches or 10000
+    s = WD.mixed_stream_device(seed=4000, n_preload=n_pre, n_batches=n_stream)
     batches = list(s["batches"]())
     torch.cuda.synchronize()
     n_ops = sum(int(k.numel()) for _, k, _ in batches)
@@ -734,7 +737,7 @@ def bench_batched(args):
                          queue_depth=1)
     finals = results.pop("_finals")
     # a stream of small batches only (2^4..2^11 ops: every batch fits the persistent kernel's queue)
-    ss = WD.mixed_stream_device(seed=4100, n_preload=n_pre, n_batches=min(args.batches, 3000), lo_exp=4, hi_exp=11)
+    ss = WD.mixed_stream_device(seed=4100, n_preload=n_pre, n_batches=min(n_stream, 3000), lo_exp=4, hi_exp=11)
     sbatches = list(ss["batches"]())
     small_res = run_stream(torch, fx, BatchedRunner, sbatches, ss["preload_keys"], ss["preload_vals"], NS, sv, bt, log,
                            queue_depth=1)
@@ -836,7 +839,7 @@ def bench_update_heavy(args):
     torch.cuda.set_device(0)
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
     out = {}
-    n_batches = args.batches if args.batches != 300 else 64
+    n_batches = args.batches or 64
     for dist in ("uniform", "zipf", "zipf_dense", "sequential"):
         ins, deletes = W.update_heavy(dist, seed=3000, n_batches=n_batches, batch=1 << 20)
         idx = fx.Index(key_bits=32, node_size=32)

@@ -426,6 +426,14 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     CK(fill_bytes(c, status, 0, 64));
     CK(validate_inserts<K>(c, mixed ? ops : nullptr, keys, mixed || hom_op == FLIX_OP_INSERT ? n : 0, status));
     CK(sort_pairs<K>(c, keys, nullptr, sk, si, n));
+    // A mixed batch's reads (on st) and the preparation of its updates (fold, partition, count pass,
+    // on the handle's side stream) both only read the pre-batch state, so they run side by side; the
+    // side stream joins st before admission.  Scratch for both is taken here, on the host, in order.
+    Ctx cu{h, mixed ? h->side_st : st};
+    if (mixed) {
+        CK(cudaEventRecord(h->fork_ev, st));
+        CK(cudaStreamWaitEvent(h->side_st, h->fork_ev, 0));
+    }
     uint64_t* roff = roff_user;
     uint32_t *sb = nullptr, *sn = nullptr, *sp = nullptr;
     if (mixed) {
@@ -452,12 +460,16 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     const uint64_t alloc_cap = 2 * n + 16;   // a batch of U distinct updates allocates at most 2U nodes
     uint32_t* alloc_ids = A.take<uint32_t>(alloc_cap);
     if (!ukey || !uop || !uval || !uoff || !nf || !nf_off || !allgone || !alloc_ids) return FLIX_ENOMEM;
-    CK(fold_updates<K>(c, sk, si, n, ops, hom_op, aux, ukey, uop, uval, udev));
-    CK(partition<K>(c, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff, nullptr));
-    const HeavyList hl = heavy_list(c, n);
+    CK(fold_updates<K>(cu, sk, si, n, ops, hom_op, aux, ukey, uop, uval, udev));
+    CK(partition<K>(cu, static_cast<const K*>(h->mkba), nb, ukey, n, udev, uoff, nullptr));
+    const HeavyList hl = heavy_list(cu, n);
     if (!hl.list || !hl.n) return FLIX_ENOMEM;
-    CK(update_count<K>(c, ukey, uop, uval, uoff, nf, allgone, hl));
-    CK(scan_exclusive<uint64_t, uint64_t>(c, nf, nf_off, nb));
+    CK(update_count<K>(cu, ukey, uop, uval, uoff, nf, allgone, hl));
+    CK(scan_exclusive<uint64_t, uint64_t>(cu, nf, nf_off, nb));
+    if (mixed) {
+        CK(cudaEventRecord(h->join_ev, h->side_st));
+        CK(cudaStreamWaitEvent(st, h->join_ev, 0));
+    }
     const uint64_t* nf_total = nf_off + nb;
     const uint64_t* rtot_dev = (mixed && roff) ? roff + n : nullptr;
     uint64_t need = 0, freed = 0, rtotal = 0, heavy_nodes = 1;   // async: the heavy kernel always runs
@@ -935,7 +947,10 @@ int flix_create(const flix_config* cfg, flix_t* out)
         (e = cudaMemset(h->dstate, 0, sizeof(DevState))) ||
         (e = cudaHostAlloc(&h->hpin, 64 * sizeof(uint64_t), cudaHostAllocMapped)) ||
         (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->hpin_dev), h->hpin, 0)) ||
-        (e = cudaEventCreateWithFlags(&h->qstage_ev, cudaEventDisableTiming))) {
+        (e = cudaEventCreateWithFlags(&h->qstage_ev, cudaEventDisableTiming)) ||
+        (e = cudaStreamCreateWithFlags(&h->side_st, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming))) {
         int r = fail(h, e);
         flix_destroy(h);
         return r;
@@ -963,6 +978,9 @@ int flix_destroy(flix_t h)
     if (h->qstage_ev) cudaEventSynchronize(h->qstage_ev);
     if (h->qstage) cudaFreeHost(h->qstage);
     if (h->qstage_ev) cudaEventDestroy(h->qstage_ev);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->side_st) cudaStreamDestroy(h->side_st);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return FLIX_OK;

@@ -181,6 +181,10 @@ struct flix_index {
     void* qstage = nullptr;        // pinned staging of a persistent queue's batch descriptors
     size_t qstage_bytes = 0;
     cudaEvent_t qstage_ev = nullptr;   // recorded after the staging copy was issued
+
+    // a mixed batch's update preparation runs on side_st beside its reads (fork and join events)
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace flix {
