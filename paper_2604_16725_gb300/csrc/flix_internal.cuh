@@ -329,16 +329,24 @@ __device__ __forceinline__ uint32_t node_upper_bound(const K* __restrict__ nk, u
 }
 
 // From bucket b's first node, walk node-links to the first node whose maxKey >= q (Sec. 4.1);
-// prev = the node walked past last (NIL when the walk ends at the first node).
+// prev = the node walked past last (NIL when the walk ends at the first node).  Node b is bucket
+// b's first node after every bulk load and restructure (until an elastic split renumbers the
+// buckets or the node leaves its chain), so its metadata is read beside the bucket's head (b < nb
+// <= cap) and kept when the head confirms it: one dependent load less on the usual walk.
 template <class K, bool NC = true>
 __device__ __forceinline__ bool find_node(const DevIdx<K>& ix, uint32_t b, K q, uint32_t& node, uint32_t& sz, K& bd,
                                           uint32_t& nx, uint32_t& prev)
 {
     prev = NIL;
     node = ld_node<NC>(ix.head + b);
-    sz = ld_node<NC>(ix.size + node);
-    bd = ld_node<NC>(ix.bound + node);
-    nx = ld_node<NC>(ix.next + node);
+    sz = ld_node<NC>(ix.size + b);
+    bd = ld_node<NC>(ix.bound + b);
+    nx = ld_node<NC>(ix.next + b);
+    if (node != b) {
+        sz = ld_node<NC>(ix.size + node);
+        bd = ld_node<NC>(ix.bound + node);
+        nx = ld_node<NC>(ix.next + node);
+    }
     uint32_t steps = 0;
     while (q > bd) {
         if (nx == NIL || ++steps > ix.cap) { atomicOr(ix.err, ERR_CHAIN); return false; }

@@ -214,10 +214,17 @@ __device__ __forceinline__ uint32_t load_ugroup(const DevIdx<K>& ix, const uint3
     g.nx = NIL;
     g.bd = K(0);
     if (touched) {
+        // node b is usually bucket b's first node (see find_node): its metadata is read beside the
+        // head and replaced when the head names another node
         g.node = ix.head[b];
-        g.sz = ix.size[g.node];
-        g.bd = ix.bound[g.node];
-        g.nx = ix.next[g.node];
+        g.sz = ix.size[b];
+        g.bd = ix.bound[b];
+        g.nx = ix.next[b];
+        if (g.node != (uint32_t)b) {
+            g.sz = ix.size[g.node];
+            g.bd = ix.bound[g.node];
+            g.nx = ix.next[g.node];
+        }
     }
     return __ballot_sync(FULL, touched);
 }
