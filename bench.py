@@ -517,6 +517,30 @@ def main():
         if i >= args.warmup:
             pred_ms.append(a.elapsed_time(b))
 
+    # config 2's smaller read batches (2^20 and 2^22: the first queries of the step's batches), each
+    # timed alone, 10 repetitions after warm-up, median
+    sizes_ms = {}
+    sk_buf = torch.empty(1 << LOG_Q, dtype=torch.int64, device="cuda")
+    sv_buf = torch.empty(1 << LOG_Q, dtype=torch.int64, device="cuda")
+    for lg in sorted({lg_ for lg_ in (20, 22, LOG_Q) if lg_ <= LOG_Q}):
+        m = 1 << lg
+        for name, fn in (("lookup", lambda m=m: idx.lookup(bufs["q"][:m], stream=stream, out=bufs["lv"][:m],
+                                                            found=False)),
+                         ("successor", lambda m=m: idx.successor(bufs["sq"][:m], stream=stream,
+                                                                 out=(sk_buf[:m], sv_buf[:m])))):
+            t = []
+            for i in range(args.warmup + 10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                if i >= args.warmup:
+                    t.append(a.elapsed_time(b))
+            med = statistics.median(t)
+            sizes_ms["%s_2e%d" % (name, lg)] = {"ms_p50": round(med, 4), "mops": round(m / (med * 1e-3) / 1e6, 1)}
+    del sk_buf, sv_buf
+
     # roofline of the dominant kernel: the radix-sort scatter pass
     peak, peak_kind = measured_peaks()
     down = prof.get("sort_onesweep", {"launches": 0, "ms": 0.0, "bytes": 0.0})
@@ -551,7 +575,8 @@ def main():
                            "ms_p50": statistics.median(per_phase[p]),
                            "ms_p99": float(np.percentile(per_phase[p], 99))} for p in phases},
             "outside_step": {"predecessor": {"mops": (1 << LOG_Q) / (statistics.median(pred_ms) * 1e-3) / 1e6,
-                                             "ms_p50": statistics.median(pred_ms), "queries": 1 << LOG_Q}},
+                                             "ms_p50": statistics.median(pred_ms), "queries": 1 << LOG_Q},
+                             "read_batches": sizes_ms},
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
             "roofline": roofline, "apply_roofline": apply_roofline,
             # every kernel's CUDA-event time per step (profiled pass): apply-only times are the
