@@ -618,6 +618,27 @@ def main():
         d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
         line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+    if rank == 0 and world == 1:
+        # the batched form beside the plain path on a short stream of small mixed batches (the full
+        # config-4 stream is `--form batched`): 600 batches of log-uniform 2^4..2^11 ops on a 2^24-key
+        # index, plain per-batch flix_apply against the persistent kernel taking each batch as it comes
+        from paper_2604_16725_gb300.batched import BatchedRunner
+        from workload import device as WD
+        ss = WD.mixed_stream_device(seed=4100, n_preload=1 << 24, n_batches=600, lo_exp=4, hi_exp=11)
+        sb = list(ss["batches"]())
+        res = run_stream(torch, fx, BatchedRunner, sb, ss["preload_keys"], ss["preload_vals"], NODE_SIZE, 0, 0,
+                         lambda m: None, queue_depth=1, modes=("plain", "persistent"))
+        fin = res.pop("_finals")
+        line["small_batch_stream"] = {
+            "workload": "600 mixed batches of log-uniform 2^4..2^11 ops (60/15/5/10/10 lookup/successor/range/"
+                        "insert/delete) on 2^24 preloaded uint64 keys; persistent = flix_apply_queue, one batch "
+                        "per launch",
+            "plain": {k: round(v, 4) if isinstance(v, float) else v for k, v in res["plain"].items()},
+            "persistent": {k: round(v, 4) if isinstance(v, float) else v for k, v in res["persistent"].items()},
+            "final_state_equal": bool(torch.equal(fin["plain"][0], fin["persistent"][0]) and
+                                      torch.equal(fin["plain"][1], fin["persistent"][1]))}
+        del ss, sb, fin
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         mops_mt, dt_mt, cores, desc_mt = cpu_oracle_sample_mt(c)
         mops, dt, desc = cpu_oracle_sample(c)
