@@ -214,7 +214,10 @@ int flix_delete(flix_t h, const void* d_keys, uint64_t n, void* stream);
  * d_range_off[n+1]: exclusive prefix of range result counts (0 for non-range ops); the pairs go to
  * d_range_keys/d_range_vals (capacity range_cap).  Any output pointer may be NULL if the batch has
  * no op that writes it.  Synchronises (range total and node admission).  Errors as for
- * flix_insert and flix_range; on FLIX_ENOMEM for the range capacity the updates are not applied. */
+ * flix_insert and flix_range; on FLIX_ENOMEM for the range capacity the updates are not applied.
+ * After its sort the batch's reads run on `stream` and the preparation of its updates on a stream
+ * the handle owns; that stream rejoins `stream` (an event wait) before anything else is enqueued,
+ * so all of the call's work is ordered before later work on `stream`, also when captured. */
 int flix_apply(flix_t h, const uint8_t* d_ops, const void* d_keys, const void* d_aux, uint64_t n,
                void* d_keys_out, void* d_vals_out, uint8_t* d_found, uint64_t* d_range_off,
                void* d_range_keys, void* d_range_vals, uint64_t range_cap, uint64_t* h_range_total,
