@@ -639,6 +639,7 @@ def main():
                                       torch.equal(fin["plain"][1], fin["persistent"][1]))}
         del ss, sb, fin
         torch.cuda.empty_cache()
+        line["short_forms"] = mini_forms(torch, fx)
     if rank == 0 and not args.no_cpu_baseline:
         mops_mt, dt_mt, cores, desc_mt = cpu_oracle_sample_mt(c)
         mops, dt, desc = cpu_oracle_sample(c)
@@ -746,6 +747,71 @@ def run_stream(torch, fx, BatchedRunner, batches, pre_k, pre_v, NS, sv, bt, log,
         torch.cuda.empty_cache()
     results["_finals"] = finals
     return results
+
+
+def mini_forms(torch, fx):
+    """Short versions of the update-heavy and serving forms for the default line (the full forms are
+    `--form update_heavy` and `--form served`): 16 uniform insert batches of 2^20 uint32 keys into an
+    empty node-size-32 index with the full form's restructure policy, then 8 delete batches of a
+    seeded half; and requests offered at 1e6
+    ops/s (2000 requests of floor(2^U(0,12)) ops, 80/10/10 lookup/insert/delete over Zipf(0.9)) on
+    2^24 preloaded uint64 keys (universe 2^25), through the server and through the plain path."""
+    from paper_2604_16725_gb300.serve import Server, plain_serve
+    out = {}
+    ins, deletes = W.update_heavy("uniform", seed=3000, n_batches=16, batch=1 << 20, n_del_batches=8)
+    idx = fx.Index(key_bits=32, node_size=32)
+    st = torch.cuda.Stream()
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()  # noqa: E731
+    dev = [(td(k), td(v)) for k, v in ins]
+    torch.cuda.synchronize()
+    # the full form's restructure policy (nodes > 2 * buckets or a chain > 64) after every insert batch,
+    # timed apart from the inserts as there
+    t_ins = 0.0
+    for k, v in dev:
+        t0 = time.perf_counter()
+        idx.insert(k, v, stream=st)
+        st.synchronize()
+        t_ins += time.perf_counter() - t0
+        s_ = idx.stats(stream=st)
+        if s_["nodes_used"] > 2 * s_["buckets"] or s_["max_chain"] > 64:
+            idx.restructure(stream=st)
+            st.synchronize()
+    stored, _ = idx.export(stream=st)
+    dels = [td(d) for d in deletes(stored.cpu().numpy().view(np.uint32))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d in dels:
+        idx.delete(d, stream=st)
+    st.synchronize()
+    t_del = time.perf_counter() - t0
+    out["update_heavy_uniform"] = {"insert_mops": round(16 * (1 << 20) / t_ins / 1e6, 1),
+                                   "delete_mops": round(sum(int(d.numel()) for d in dels) / t_del / 1e6, 1),
+                                   "live_keys": idx.stats(stream=st)["live_keys"]}
+    idx.close()
+    del dev, dels, stored
+    ubits, pbits, seed = 25, 24, 5000
+    pk = W.universe(64, seed, 0, 1 << pbits)
+    pv = W.values_for(64, pk)
+    idx = fx.Index(key_bits=64, node_size=64)
+    idx.bulk_load(torch.from_numpy(pk.view(np.int64)).cuda(), torch.from_numpy(pv.view(np.int64)).cuda())
+    srv = Server(idx, max_batch=1 << 18, depth=2, min_log=8, free_nodes_min=1 << 20)
+    req = W.serving_requests(seed=seed + 6, universe_bits=ubits, preload_bits=pbits, offered_ops_per_s=1e6,
+                             n_requests=2000)
+    sv = srv.serve(req["arrival_s"], req["req_off"], req["ops"], req["keys"], req["aux"])
+    lat = sv["latency_s"] * 1e3
+    req = W.serving_requests(seed=seed + 7, universe_bits=ubits, preload_bits=pbits, offered_ops_per_s=1e6,
+                             n_requests=300)
+    pl = plain_serve(idx, req["arrival_s"], req["req_off"], req["ops"], req["keys"], req["aux"])
+    plat = pl["latency_s"] * 1e3
+    out["served_1e6"] = {"served": {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                    "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                                    "sustained_mops": round(sv["ops"] / sv["wall_s"] / 1e6, 3), "requests": 2000},
+                         "plain_per_request": {"p50_ms": round(float(np.percentile(plat, 50)), 3),
+                                               "p99_ms": round(float(np.percentile(plat, 99)), 3), "requests": 300}}
+    del srv
+    idx.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(args):
