@@ -412,36 +412,48 @@ __global__ void __launch_bounds__(RADIX) k_sort_plan(uint32_t* __restrict__ hist
 {
     grid_dep_enter();
     constexpr int P = sizeof(K);
-    __shared__ uint32_t sw[RADIX / 32];
-    __shared__ float sq[RADIX / 32];
     __shared__ uint32_t s_const[P], s_max[P];
     __shared__ float s_p2[P];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int p = 0; p < P; p++) {
-        uint32_t* hp = hist + (size_t)p * RADIX;
-        const uint32_t c = hp[threadIdx.x];
-        const int all_one_bin = __syncthreads_or((uint64_t)c == n);
-        uint32_t m = c;
-        float q = (float)c * (float)c;
+    static_assert(P <= RADIX / 32, "one warp per digit position");
+    // one warp per digit position: lane l holds bins 8l..8l+7
+    if (warp < (uint32_t)P) {
+        uint32_t* hp = hist + (size_t)warp * RADIX + lane * 8;
+        uint32_t c[8], m = 0, run = 0;
+        float q = 0.0f;
+        bool one = false;
+#pragma unroll
+        for (int t = 0; t < 8; t++) {
+            c[t] = hp[t];
+            one |= (uint64_t)c[t] == n;
+            m = max(m, c[t]);
+            q += (float)c[t] * (float)c[t];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             m = max(m, __shfl_xor_sync(FULL, m, o));
             q += __shfl_xor_sync(FULL, q, o);
         }
-        if (lane == 0) { sw[warp] = m; sq[warp] = q; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t mm = 0;
-            float qq = 0.0f;
-            for (int w = 0; w < RADIX / 32; w++) { mm = max(mm, sw[w]); qq += sq[w]; }
-            s_max[p] = mm;
-            s_const[p] = all_one_bin;
-            s_p2[p] = qq / ((float)n * (float)n);   // chance that two items share this digit
+        const bool all_one_bin = __any_sync(FULL, one);
+        // exclusive scan of the 256 bins: within the lane, then over the lanes
+#pragma unroll
+        for (int t = 0; t < 8; t++) { const uint32_t x = c[t]; c[t] = run; run += x; }
+        uint32_t x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= (uint32_t)o) x += y;
         }
-        __syncthreads();
-        uint32_t tot;
-        hp[threadIdx.x] = block_excl_scan<uint32_t, RADIX / 32>(c, sw, tot);
+        const uint32_t before = x - run;
+#pragma unroll
+        for (int t = 0; t < 8; t++) hp[t] = before + c[t];
+        if (lane == 0) {
+            s_max[warp] = m;
+            s_const[warp] = all_one_bin;
+            s_p2[warp] = q / ((float)n * (float)n);   // chance that two items share this digit
+        }
     }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     int nc[P];
     int m = 0;
