@@ -975,12 +975,13 @@ cudaError_t sort_pairs(Ctx& c, const K* kin, const uint32_t* vin, K* kout, uint3
     uint64_t* list = A.take<uint64_t>(list_cap);
     if (!bases || !tk || !tv || !plan || !list || (onesweep ? (!status || !tile_ctr) : (!counts || !offsets)))
         return cudaErrorMemoryAllocation;
-    cudaError_t e = fill_bytes(c, bases, 0, P * RADIX * 4);
+    // the digit counts, the tile states and the tile counters were taken one after another from the
+    // arena: one fill zeroes them all
+    cudaError_t e = onesweep ? fill_bytes(c, bases, 0,
+                                          (size_t)(reinterpret_cast<char*>(tile_ctr + P + 1) -
+                                                   reinterpret_cast<char*>(bases)))
+                             : fill_bytes(c, bases, 0, P * RADIX * 4);
     if (e) return e;
-    if (onesweep) {
-        if ((e = fill_bytes(c, status, 0, (size_t)P * T * RADIX * 4))) return e;
-        if ((e = fill_bytes(c, tile_ctr, 0, (P + 1) * 4))) return e;
-    }
     int nsm = 148;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.h->device);
     uint32_t hg = div_up(n, 256);
