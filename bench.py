@@ -595,6 +595,21 @@ def main():
                              ("rk", bufs["rcap"], torch.int64), ("rv", bufs["rcap"], torch.int64)):
             host[k] = torch.empty(shape, dtype=dt).pin_memory()
         h2d_st, d2h_st = torch.cuda.Stream(), torch.cuda.Stream()
+        # this box's device-to-host link: one 1 GiB copy into pinned memory, the best of three (the
+        # e2e step moves 2.5 GB of results down, so its time is bounded by this rate)
+        lk_d = torch.empty(1 << 27, dtype=torch.int64, device="cuda")
+        lk_h = torch.empty(1 << 27, dtype=torch.int64).pin_memory()
+        lk = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(d2h_st)
+            with torch.cuda.stream(d2h_st):
+                lk_h.copy_(lk_d, non_blocking=True)
+            b.record(d2h_st)
+            b.synchronize()
+            lk.append(a.elapsed_time(b))
+        link_gbs = (1 << 30) / (min(lk) * 1e-3) / 1e9
+        del lk_d, lk_h
         outs = [dict(lv=torch.empty(n, dtype=torch.int64, device="cuda"),
                      sk=torch.empty(n, dtype=torch.int64, device="cuda"),
                      sv=torch.empty(n, dtype=torch.int64, device="cuda"),
@@ -617,7 +632,9 @@ def main():
         h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv"))
         d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
         line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+                       "d2h_link_gbs": round(link_gbs, 1),
+                       "d2h_link_bound_ms_per_step": round(d2h / (link_gbs * 1e9) * 1e3, 2)}
     if rank == 0 and world == 1:
         # the batched form beside the plain path on a short stream of small mixed batches (the full
         # config-4 stream is `--form batched`): 600 batches of log-uniform 2^4..2^11 ops on a 2^24-key

@@ -515,15 +515,25 @@ __device__ __forceinline__ void range_fill_warp(const DevIdx<K>& ix, uint64_t bb
     for (uint64_t guard = 0, lim = (uint64_t)ix.cap + ix.nb + 1; guard < lim && c > 0; guard++) {
         // lane 0: the current node; lane l > 0: the first node of bucket bb + l
         uint32_t n_l = NIL, p_l = 0, sz_l = 0, nx_l = NIL;
+        bool have = false;
         if (lane == 0) {
             n_l = node;
             p_l = pos;
         } else if (bb + lane < ix.nb) {
-            n_l = ld_node<NC>(ix.head + bb + lane);
+            // node b is usually bucket b's first node (see find_node): its metadata is read beside
+            // the head and kept when the head confirms it
+            const uint32_t b_l = (uint32_t)(bb + lane);
+            n_l = ld_node<NC>(ix.head + b_l);
+            sz_l = ld_node<NC>(ix.size + b_l);
+            nx_l = ld_node<NC>(ix.next + b_l);
+            have = n_l == b_l;
         }
-        if (n_l != NIL) {
+        if (n_l != NIL && !have) {
             sz_l = ld_node<NC>(ix.size + n_l);
             nx_l = ld_node<NC>(ix.next + n_l);
+        } else if (n_l == NIL) {
+            sz_l = 0;
+            nx_l = NIL;
         }
         // the batch ends at the first node whose chain continues
         const uint32_t cont = __ballot_sync(FULL, nx_l != NIL);

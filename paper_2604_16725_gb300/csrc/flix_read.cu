@@ -295,14 +295,29 @@ __global__ void __launch_bounds__(RP_THREADS) k_range_count(DevIdx<K> ix, const 
                 break;
             }
             node = nx;
+            // entering the next bucket: node bb is usually its first node (see find_node), so its
+            // metadata is read beside the head and kept when the head confirms it
+            bool spec = false;
+            uint32_t s_sz = 0, s_nx = NIL;
+            K s_bd = K(0);
             while (node == NIL) {
                 if (++bb >= ix.nb) break;
                 node = ix.head[bb];
+                s_sz = ix.size[bb];
+                s_bd = ix.bound[bb];
+                s_nx = ix.next[bb];
+                spec = true;
             }
             if (node == NIL) break;
-            sz = ix.size[node];
-            bd = ix.bound[node];
-            nx = ix.next[node];
+            if (spec && node == bb) {
+                sz = s_sz;
+                bd = s_bd;
+                nx = s_nx;
+            } else {
+                sz = ix.size[node];
+                bd = ix.bound[node];
+                nx = ix.next[node];
+            }
             pos = 0;
         }
     }
