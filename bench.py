@@ -412,6 +412,8 @@ def main():
                          "distribution (default 64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="plain form: leave out the short batched, update-heavy and serving forms after the step")
     ap.add_argument("--log-load", type=int, default=LOG_LOAD, help="log2 of the keys loaded (smaller cases)")
     ap.add_argument("--log-q", type=int, default=LOG_Q, help="log2 of the lookup/successor batch")
     ap.add_argument("--sort-variant", type=int, default=0, help="0 auto, 1 one-sweep, 2 reduce-then-scan")
@@ -635,7 +637,7 @@ def main():
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                        "d2h_link_gbs": round(link_gbs, 1),
                        "d2h_link_bound_ms_per_step": round(d2h / (link_gbs * 1e9) * 1e3, 2)}
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_forms:
         # the batched form beside the plain path on a short stream of small mixed batches (the full
         # config-4 stream is `--form batched`): 600 batches of log-uniform 2^4..2^11 ops on a 2^24-key
         # index, plain per-batch flix_apply against the persistent kernel taking each batch as it comes
