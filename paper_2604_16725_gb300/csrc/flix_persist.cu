@@ -30,6 +30,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr int PQ_THREADS = 256;
 constexpr uint32_t PQ_MAX = FLIX_QUEUE_BATCH_MAX;
 constexpr uint64_t PQ_NOT_RUN = 8;      // status[0] flag of a batch the queue did not reach
+constexpr int PQ_CHUNK = 8;             // node pairs a merging thread has in flight
 
 // Device copy of one flix_batch.
 struct PQBatch {
@@ -496,12 +497,26 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
                         const K* nv = ix.vals + (uint64_t)x * NS;
                         const uint32_t sz = ix.size[x];
                         uint32_t a = 0, c = j, t = 0;
+                        // the node's pairs come in chunks of PQ_CHUNK, every load of a chunk issued
+                        // before the merge uses it (the merge's stores could alias the loads, so
+                        // one pair at a time would wait for each load)
+                        K kb[PQ_CHUNK], vb[PQ_CHUNK];
+                        uint32_t a0 = 0;
+                        bool have = false;
                         while (a < sz || c < k) {
-                            if (c >= k || (a < sz && nk[a] < S.ukey[c])) {
-                                mk[t] = nk[a]; mv[t] = nv[a]; t++; a++;
-                            } else if (a < sz && nk[a] == S.ukey[c]) {
-                                if (S.uop[c] == EFF_UPS) { mk[t] = nk[a]; mv[t] = S.uval[c]; t++; }
-                                else if (S.uop[c] == EFF_INS) { mk[t] = nk[a]; mv[t] = nv[a]; t++; }
+                            if (a < sz && (!have || a - a0 >= (uint32_t)PQ_CHUNK)) {
+                                a0 = a;
+                                have = true;
+#pragma unroll
+                                for (int i = 0; i < PQ_CHUNK; i++)
+                                    if (a0 + i < sz) { kb[i] = nk[a0 + i]; vb[i] = nv[a0 + i]; }
+                            }
+                            const K ka = a < sz ? kb[a - a0] : K(0);
+                            if (c >= k || (a < sz && ka < S.ukey[c])) {
+                                mk[t] = ka; mv[t] = vb[a - a0]; t++; a++;
+                            } else if (a < sz && ka == S.ukey[c]) {
+                                if (S.uop[c] == EFF_UPS) { mk[t] = ka; mv[t] = S.uval[c]; t++; }
+                                else if (S.uop[c] == EFF_INS) { mk[t] = ka; mv[t] = vb[a - a0]; t++; }
                                 a++; c++;
                             } else {
                                 if (S.uop[c] != EFF_DEL) { mk[t] = S.ukey[c]; mv[t] = S.uval[c]; t++; }
@@ -527,10 +542,20 @@ __global__ void __launch_bounds__(PQ_THREADS) k_queue(DevIdx<K> ix, const PQBatc
                                 node = nn;
                             }
                             const uint32_t ps = piece_size(t, NS, qn, r);
-                            for (uint32_t s2 = 0; s2 < ps; s2++, o++) {
-                                ix.keys[(uint64_t)node * NS + s2] = mk[o];
-                                ix.vals[(uint64_t)node * NS + s2] = mv[o];
+                            // the merged run goes out in chunks: its loads first, then its stores
+                            for (uint32_t s0 = 0; s0 < ps; s0 += PQ_CHUNK) {
+                                K ck[PQ_CHUNK], cv[PQ_CHUNK];
+#pragma unroll
+                                for (int i = 0; i < PQ_CHUNK; i++)
+                                    if (s0 + i < ps) { ck[i] = mk[o + s0 + i]; cv[i] = mv[o + s0 + i]; }
+#pragma unroll
+                                for (int i = 0; i < PQ_CHUNK; i++)
+                                    if (s0 + i < ps) {
+                                        ix.keys[(uint64_t)node * NS + s0 + i] = ck[i];
+                                        ix.vals[(uint64_t)node * NS + s0 + i] = cv[i];
+                                    }
                             }
+                            o += ps;
                             ix.size[node] = ps;
                             ix.bound[node] = r + 1 < qn ? mk[o - 1] : obound;
                         }
