@@ -255,16 +255,29 @@ def run_step(torch, idx, bufs, stream, events=None):
     ev("restructure", 1)
 
 
-def upload_inputs(torch, host, h2d):
+def timed_span(torch, st, spans, fn):
+    """Run fn() enqueueing work on stream st; with a list `spans`, bracket it by timing events."""
+    if spans is None:
+        return fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    r = fn()
+    b.record(st)
+    spans.append((a, b))
+    return r
+
+
+def upload_inputs(torch, host, h2d, spans=None):
     """One step's inputs, host -> device on the h2d stream; returns (tensors, ready event)."""
     with torch.cuda.stream(h2d):
-        dev = {k: host[k].to("cuda", non_blocking=True) for k in ("q", "sq", "lo", "hi", "ik", "iv")}
+        dev = timed_span(torch, h2d, spans, lambda: {k: host[k].to("cuda", non_blocking=True)
+                                                      for k in ("q", "sq", "lo", "hi", "ik", "iv")})
         ready = torch.cuda.Event()
         ready.record(h2d)
     return dev, ready
 
 
-def run_step_e2e(torch, idx, host, stream, h2d, d2h, outs, step, pending):
+def run_step_e2e(torch, idx, host, stream, h2d, d2h, outs, step, pending, spans=None):
     """The same step through the public API from pinned host buffers, results read back to host.
     Each step copies its own inputs host -> device, one step ahead on the h2d stream (`pending`
     holds this step's upload); each phase's results go device -> host on the d2h stream as soon as
@@ -273,7 +286,7 @@ def run_step_e2e(torch, idx, host, stream, h2d, d2h, outs, step, pending):
     Returns the next step's upload."""
     o = outs[step % 2]
     dev, ready = pending
-    nxt = upload_inputs(torch, host, h2d)
+    nxt = upload_inputs(torch, host, h2d, None if spans is None else spans["h2d"])
     for t in dev.values():
         t.record_stream(stream)
     stream.wait_event(ready)
@@ -285,8 +298,8 @@ def run_step_e2e(torch, idx, host, stream, h2d, d2h, outs, step, pending):
         done.record(stream)
         d2h.wait_event(done)
         with torch.cuda.stream(d2h):
-            for dst, src in pairs:
-                dst.copy_(src, non_blocking=True)
+            timed_span(torch, d2h, None if spans is None else spans["d2h"],
+                       lambda: [dst.copy_(src, non_blocking=True) for dst, src in pairs])
 
     with torch.cuda.stream(stream):
         v, _ = idx.lookup(dev["q"], stream=stream, out=o["lv"], found=False)
@@ -624,19 +637,23 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        pending = upload_inputs(torch, host, h2d_st)     # the first timed step's inputs
+        spans = {"h2d": [], "d2h": []}
+        pending = upload_inputs(torch, host, h2d_st, spans["h2d"])     # the first timed step's inputs
         for s in range(args.steps):
-            pending = run_step_e2e(torch, idx, host, stream, h2d_st, d2h_st, outs, s, pending)
+            pending = run_step_e2e(torch, idx, host, stream, h2d_st, d2h_st, outs, s, pending, spans)
         torch.cuda.synchronize()
         barrier()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        # time each copy engine direction was busy per step (the copies' own durations)
+        busy = {k: sum(a.elapsed_time(b) for a, b in v) / args.steps for k, v in spans.items()}
         e2e_ms = max_over_ranks(e2e_ms, world)
         h2d = sum(host[k].numel() * host[k].element_size() for k in ("q", "sq", "lo", "hi", "ik", "iv"))
         d2h = sum(host[k].numel() * host[k].element_size() for k in ("lv", "sk", "sv", "roff", "rk", "rv"))
         line["e2e"] = {"value": n_ops * world / (e2e_ms * 1e-3) / 1e6, "unit": "Mops/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                        "d2h_link_gbs": round(link_gbs, 1),
-                       "d2h_link_bound_ms_per_step": round(d2h / (link_gbs * 1e9) * 1e3, 2)}
+                       "d2h_link_bound_ms_per_step": round(d2h / (link_gbs * 1e9) * 1e3, 2),
+                       "d2h_busy_ms_per_step": round(busy["d2h"], 2), "h2d_busy_ms_per_step": round(busy["h2d"], 2)}
     if rank == 0 and world == 1 and not args.no_forms:
         # the batched form beside the plain path on a short stream of small mixed batches (the full
         # config-4 stream is `--form batched`): 600 batches of log-uniform 2^4..2^11 ops on a 2^24-key
