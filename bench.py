@@ -959,6 +959,18 @@ def bench_served(args):
                       "p99_ms": float(np.percentile(lat, 99)), "batches": out["batches"],
                       "mean_batch_ops": out["ops"] / max(out["batches"], 1)})
         log("offered %.0e: %s" % (rate, loads[-1]))
+    # the same server with every batch through the size-class graphs (no persistent kernel), at the
+    # lowest offered load
+    del srv
+    srv_g = Server(idx, max_batch=1 << 22, depth=2, min_log=8, free_nodes_min=1 << 22, queue_depth=0)
+    req = W.serving_requests(seed=seed + 6, universe_bits=ubits, preload_bits=pbits, offered_ops_per_s=1e6,
+                             n_requests=2000)
+    og = srv_g.serve(req["arrival_s"], req["req_off"], req["ops"], req["keys"], req["aux"])
+    lat = og["latency_s"] * 1e3
+    graphs_only = {"offered_mops": 1.0, "requests": 2000, "sustained_mops": og["ops"] / og["wall_s"] / 1e6,
+                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    log("graphs only, offered 1e+06: %s" % graphs_only)
+    del srv_g
     # plain per-request path at the lowest offered load (bounded number of requests)
     req = W.serving_requests(seed=seed + 6, universe_bits=ubits, preload_bits=pbits, offered_ops_per_s=1e6,
                              n_requests=600)
@@ -970,8 +982,9 @@ def bench_served(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "served: 2^%d uint64 keys preloaded (universe 2^%d); Poisson requests of "
                                    "floor(2^U(0,12)) ops, 80/10/10 lookup/insert/delete over Zipf(0.9)" % (pbits, ubits),
-                       "node_size": 64, "depth": 2},
-            "loads": loads, "plain_per_request": plain}
+                       "node_size": 64, "depth": 2,
+                       "small_batches": "batches of at most 2048 ops through the persistent kernel, one per launch"},
+            "loads": loads, "graphs_only_1e6": graphs_only, "plain_per_request": plain}
     print(json.dumps(line))
     return 0
 

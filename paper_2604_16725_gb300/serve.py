@@ -4,7 +4,8 @@ Requests (runs of lookup/insert/delete/... ops, in CSR order in a pinned host re
 a schedule.  Whenever fewer than `depth` batches are in flight, the loop coalesces every request that
 has arrived (up to `max_batch` ops, and only as many inserts as the free-node budget admits) into one
 device batch: the batch's ops are copied host-to-device on a copy stream while earlier batches
-compute, the batch runs through the batched runner's CUDA graph on the compute stream, and its
+compute, the batch runs on the compute stream through the batched runner (a batch of at most 2048
+ops through the persistent kernel, a larger one through its size class's CUDA graph), and its
 results are copied back on the copy stream.  A request completes when its batch's results are on
 the host; its latency is that time minus its scheduled arrival.
 
@@ -30,13 +31,16 @@ from .flix import OP_INSERT, Index
 
 
 class Server:
+    """queue_depth: batches of at most QUEUE_BATCH_MAX ops go through the persistent kernel, that many
+    per launch (1: each as it is dispatched; 0: every batch through the size-class graphs)."""
+
     def __init__(self, idx: Index, max_batch: int = 1 << 22, depth: int = 2, min_log: int = 8,
-                 free_nodes_min: int = 1 << 20):
+                 free_nodes_min: int = 1 << 20, queue_depth: int = 1):
         self.idx = idx
         self.max_batch = max_batch
         self.depth = depth
         self.runner = BatchedRunner(idx, max_batch=max_batch, min_log=min_log, range_per_op=1,
-                                    free_nodes_min=free_nodes_min, check_every=1 << 30)
+                                    free_nodes_min=free_nodes_min, check_every=1 << 30, queue_depth=queue_depth)
         self.compute = self.runner.stream
         self.copy = torch.cuda.Stream(device=idx.device)
         dev, dt = idx.device, idx.tdtype
