@@ -63,3 +63,23 @@ def test_traffic_record_follows_the_marked_source(tmp_path, monkeypatch):
     (src_dir / "flix_sort.cu").write_text(head + body.replace("pass_kernel", "pass_kernel2") + tail)
     assert bench.traffic_record("sort_onesweep") is None
     assert bench.traffic_record("no_such_kernel") is None
+
+
+def test_algorithmic_bytes_and_fractions():
+    """The bench line's algorithmic bytes per step follow the kernel table's formulas (uint64 keys
+    and values, node size 64, half-full nodes), and a kernel's fraction is bytes / time / peak."""
+    by = bench.step_bytes(rcap=1000, log_load=12, log_q=10, log_r=4, log_u=6)
+    n, B, R, U, ks, h = 1 << 12, 1 << 10, 1 << 4, 1 << 6, 8, 32
+    nb = n // h
+    assert by["gather"] == n * 2 * (ks + ks)
+    assert by["sort_hist"] == (2 * B + R + 2 * U) * ks
+    # windowed delivery: tag written with the result, then (tag, result) read and the result written,
+    # for lookups (8-byte values) and successors (8-byte keys and values)
+    assert by["read_unsort"] == (B * 4 + B * (4 + 8) + B * 8) + (B * 4 + B * (4 + 16) + B * 16)
+    assert by["range_fill"] == 1000 * 2 * (ks + ks) + R * (4 + 12 + 16)
+    assert by["partition"] == 2 * (nb * ks + B * ks + 4 * B) + (nb * ks + R * ks + 4 * R) + 2 * (nb * ks + U * ks + 4 * nb)
+    prof = {"gather": {"ms": 2.0, "launches": 2, "bytes": 0.0}}
+    out = bench.apply_rooflines(prof, 2, 1000.0, "measured", rcap=1000)
+    g = out["gather"]
+    assert g["ms_per_step"] == 1.0 and g["frac"] == pytest.approx(g["achieved"] / 1000.0)
+    assert g["achieved"] == pytest.approx(bench.step_bytes(1000)["gather"] / 1e-3 / 1e9, abs=0.1)   # rounded to 0.1
