@@ -430,9 +430,23 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     // on the handle's side stream) both only read the pre-batch state, so they run side by side; the
     // side stream joins st before admission.  Scratch for both is taken here, on the host, in order.
     Ctx cu{h, mixed ? h->side_st : st};
+    // on every return between the fork and the join (an error), the side stream still rejoins st, so
+    // that no work of this call runs past it into the next call's use of the scratch
+    struct Rejoin {
+        flix_index* h;
+        cudaStream_t st;
+        bool armed = false;
+        ~Rejoin()
+        {
+            if (!armed) return;
+            cudaEventRecord(h->join_ev, h->side_st);
+            cudaStreamWaitEvent(st, h->join_ev, 0);
+        }
+    } rejoin{h, st};
     if (mixed) {
         CK(cudaEventRecord(h->fork_ev, st));
         CK(cudaStreamWaitEvent(h->side_st, h->fork_ev, 0));
+        rejoin.armed = true;
     }
     uint64_t* roff = roff_user;
     uint32_t *sb = nullptr, *sn = nullptr, *sp = nullptr;
@@ -467,6 +481,7 @@ int do_batch(flix_index* h, const uint8_t* ops, int hom_op, const K* keys, const
     CK(update_count<K>(cu, ukey, uop, uval, uoff, nf, allgone, hl));
     CK(scan_exclusive<uint64_t, uint64_t>(cu, nf, nf_off, nb));
     if (mixed) {
+        rejoin.armed = false;
         CK(cudaEventRecord(h->join_ev, h->side_st));
         CK(cudaStreamWaitEvent(st, h->join_ev, 0));
     }
